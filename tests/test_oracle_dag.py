@@ -1,0 +1,111 @@
+"""Pins of the task-DAG oracle against the values the paper prints.
+
+Golden values: tests/golden/dag_paper_values.txt (each with its citation).
+"""
+import os
+from itertools import permutations
+
+import pytest
+
+from oracle import dag
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "dag_paper_values.txt")
+
+
+def golden():
+    out = {}
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        name, value = line.split()[:2]
+        out[name] = value
+    return out
+
+
+G = golden()
+D2 = tuple(int(v) for v in G["domain_2d"].split("x"))
+D3 = tuple(int(v) for v in G["domain_3d"].split("x"))
+
+
+def near(x, ref, rel=0.05):
+    return abs(x - ref) <= rel * ref
+
+
+def test_fig1_program_dag_edges():
+    """Fig. 2 drawn for the program of Fig. 1.  The figure numbers its two
+    middle vertices in the opposite order of the calls (its vertex 4 has
+    parents 1 and 2, i.e. vec_add(a,b,d)); the edge set is compared by task."""
+    assert dag.starss_example_edges() == {
+        ("unit_vec(a)", "vec_add(a,b,d)"), ("unit_vec(b)", "vec_add(a,b,d)"),
+        ("unit_vec(b)", "vec_add(c,b,c)"), ("unit_vec(c)", "vec_add(c,b,c)"),
+        ("vec_add(c,b,c)", "scalar_product(c,d,s)"), ("vec_add(a,b,d)", "scalar_product(c,d,s)"),
+    }
+
+
+@pytest.mark.parametrize("name,order", [("s_max_2d_naive", dag.ORDER_2D_NAIVE),
+                                        ("s_max_2d_bad", dag.ORDER_2D_BAD),
+                                        ("s_max_2d_opt", dag.ORDER_2D_OPT)])
+def test_fig5_orderings(name, order):
+    s = dag.speedup(dag.build_dag(dag.basic_order_tasks(D2, order)))
+    assert near(s, float(G[name]))
+
+
+def test_2d_intra_first_permutations_span_delta_2_to_5():
+    """Sec. V: for the basic order Delta lies in [2, 5]; 5 when the x
+    neighbour is last; the best basic order reaches S_max(2, 5) = 2.5."""
+    n = int(G["n_2d"])
+    allowed = [n / d for d in range(int(G["delta_2d_min"]), int(G["delta_2d_max"]) + 1)]
+    best = 0.0
+    for perm in permutations(dag.STENCIL_2D[1:]):
+        order = [(0, 0)] + list(perm)
+        s = dag.speedup(dag.build_dag(dag.basic_order_tasks(D2, order)))
+        assert any(near(s, a) for a in allowed), (order, s)
+        if order[-1] == (1, 0):
+            assert near(s, n / int(G["delta_2d_max"]))
+        best = max(best, s)
+    assert near(best, float(G["s_max_2d_best_basic"]))
+
+
+def test_eq2_against_dag_for_opt_and_bad():
+    k = D2[0] * D2[1]
+    n = int(G["n_2d"])
+    s_opt = dag.speedup(dag.build_dag(dag.basic_order_tasks(D2, dag.ORDER_2D_OPT)))
+    s_bad = dag.speedup(dag.build_dag(dag.basic_order_tasks(D2, dag.ORDER_2D_BAD)))
+    assert near(s_opt, dag.eq2(1, k, n))      # Eq. 4 is Eq. 2 with Delta = 1
+    assert near(s_bad, dag.eq2(n, k, n))
+
+
+def test_3d_x_neighbour_last_serialises():
+    hs = dag.half_shell_3d()
+    xn = (1, 0, 0)
+    order = [(0, 0, 0)] + [o for o in hs if o != xn] + [xn]
+    s = dag.speedup(dag.build_dag(dag.basic_order_tasks(D3, order)))
+    assert near(s, 1.0)
+
+
+def test_3d_best_basic_order_reaches_seven():
+    """Sec. V: S_max(2, 14) = 7 for the best intra-first 3D order."""
+    hs = dag.half_shell_3d()
+    best = 0.0
+    # x neighbour right after the intra task; the remaining 12 in a few orders
+    rest = [o for o in hs if o != (1, 0, 0)]
+    for order_rest in (rest, rest[::-1], sorted(rest, key=lambda o: (o[0], o[1], o[2])),
+                       sorted(rest, key=lambda o: (-o[0], o[2], o[1]))):
+        order = [(0, 0, 0), (1, 0, 0)] + list(order_rest)
+        s = dag.speedup(dag.build_dag(dag.basic_order_tasks(D3, order)))
+        best = max(best, s)
+    assert best <= float(G["s_max_3d_best_basic"]) * 1.05
+    assert near(best, float(G["s_max_3d_best_basic"]), rel=0.05)
+
+
+def test_loop_exchange_with_colouring_is_not_limited():
+    """Sec. VI/VIII: loop exchange + colouring has a critical path that does
+    not grow with the domain, so S grows with the number of tasks."""
+    s_small = dag.speedup(dag.build_dag(dag.loopex_tasks((20, 20), dag.STENCIL_2D)))
+    s_large = dag.speedup(dag.build_dag(dag.loopex_tasks(D2, dag.STENCIL_2D)))
+    cp = dag.critical_path(dag.build_dag(dag.loopex_tasks(D2, dag.STENCIL_2D)))
+    assert cp == len(dag.STENCIL_2D) * 2 - 1
+    assert s_large > 5 * s_small / 1.01 and s_large > 100
+    cp3 = dag.critical_path(dag.build_dag(dag.loopex_tasks(D3, [(0, 0, 0)] + dag.half_shell_3d())))
+    assert cp3 < 40
