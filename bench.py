@@ -1,0 +1,403 @@
+"""Benchmark: link-cell LJ velocity-Verlet steps on one GB300 per rank.
+
+Workload (default): homogeneous liquid start, N = 1,048,576 particles on an
+FCC lattice jittered by U[-0.05, 0.05) per coordinate, density 0.8442,
+T = 0.72, r_c = 2.5, cubic periodic box, mixed precision (FP32 pair math,
+FP64 cutoff decisions near r_c, Kahan / FP64 cross-cell sums, FP64 state).
+A step is one full velocity-Verlet step: kick + drift, counting-sort
+binning, force sweep, kick.  Metric: unique pair interactions (pairs with
+r < r_c, each counted once) per second, whole job.
+
+Arms:
+  --impl gb300       the CUDA library through its C ABI (default)
+  --impl reference   the FP64 CPU oracle (single host core), same workload
+
+Multi-GPU (torchrun): every rank runs an independent replica of the box
+(no data-path collective); value = pairs of all ranks / max rank time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1401_4441_gb300 import inputs  # noqa: E402
+
+METRIC = "LJ pair interactions/s (link-cell, Newton-3, velocity-Verlet steps)"
+UNIT = "pairs/s"
+DT = 0.005
+RC = 2.5
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Dist:
+    def __init__(self):
+        self.rank, self.world, self.local = dist_env()
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as td
+            td.init_process_group("gloo", init_method="env://")
+            self.pg = td
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x):
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x):
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def half_shell_candidates(counts, nc):
+    """Candidate pairs of the half-shell sweep: intra n(n-1)/2 plus n_A n_B
+    over the 13 forward neighbour cells (periodic)."""
+    c = counts.reshape(nc[2], nc[1], nc[0]).astype(np.int64)
+    total = int((c * (c - 1) // 2).sum())
+    for oz in (-1, 0, 1):
+        for oy in (-1, 0, 1):
+            for ox in (-1, 0, 1):
+                if not (oz > 0 or (oz == 0 and oy > 0) or (oz == 0 and oy == 0 and ox > 0)):
+                    continue
+                nb = np.roll(c, shift=(-oz, -oy, -ox), axis=(0, 1, 2))
+                total += int((c * nb).sum())
+    return total
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_baseline(pos, box, budget_s=12.0):
+    """The FP64 oracle (as it stands) on this host: repeated link-cell force
+    evaluations of the same box for about budget_s seconds, one core."""
+    import oracle
+    x, y, z = (np.ascontiguousarray(pos[:, d]) for d in range(3))
+    t0 = time.perf_counter()
+    evals, pairs = 0, 0
+    while True:
+        _, _, _, npairs = oracle.lc_forces(x, y, z, box, RC)
+        evals += 1
+        pairs += npairs
+        if time.perf_counter() - t0 > budget_s or evals >= 8:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{evals} FP64 link-cell force evaluations of the full {pos.shape[0]}-particle box "
+                      f"({dt:.1f} s, single thread)"}
+
+
+def run_reference(args, dist):
+    """Reference arm: the FP64 CPU oracle, same workload, rank 0 only."""
+    if dist.rank != 0:
+        return
+    import oracle
+    w = inputs.workload(args.workload)
+    pos, vel, box = w["pos"], w["vel"], w["box"]
+    f0, U, W, npairs0 = oracle.lc_forces(pos[:, 0], pos[:, 1], pos[:, 2], box, RC)
+    x, v, f = pos, vel, f0
+    for _ in range(args.warmup):
+        x, v, f, e = oracle.verlet(x, v, box, RC, DT, 1, f=f)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x, v, f, e = oracle.verlet(x, v, box, RC, DT, 1, f=f)
+    elapsed = time.perf_counter() - t0
+    _, _, _, npairs1 = oracle.lc_forces(x[:, 0], x[:, 1], x[:, 2], box, RC)
+    pairs = 0.5 * (npairs0 + npairs1) * args.steps
+    value = pairs / elapsed
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} FP64 velocity-Verlet steps of the full box, one host core"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, w):
+    nc = [int(math.floor(L / RC)) for L in w["box"]]
+    return {"workload": f"{args.workload}: N={w['pos'].shape[0]} FCC+jitter {inputs.WORKLOADS[args.workload]['jitter']}, "
+                        f"rho={w['rho']}, T={w['T']}, rc={RC}, cubic periodic L={w['box'][0]:.4f}, "
+                        f"cells {nc[0]}^3, dt={DT}",
+            "particles": int(w["pos"].shape[0]), "cells": nc,
+            "precision": args.precision if args.impl == "gb300" else "fp64 (oracle)",
+            "schedule": args.schedule, "l2": "flushed (512 MiB memset) between timed iterations",
+            "seed": inputs.DEFAULT_SEED}
+
+
+def run_profile(args, dist):
+    """Only W warm-up and K timed steps of one schedule (for ncu captures)."""
+    import torch
+    from paper_1401_4441_gb300 import build
+    torch.cuda.set_device(dist.local)
+    build.build()
+    from paper_1401_4441_gb300 import lc
+    w = inputs.workload(args.workload)
+    g = lc.Box(w["box"], RC, w["pos"].shape[0], args.precision)
+    g.set_state(torch.from_numpy(w["pos"]).cuda(), torch.from_numpy(w["vel"]).cuda())
+    sched = "atomic" if args.schedule == "auto" else args.schedule
+    g.forces(sched)
+    g.verlet(DT, args.warmup, sched)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.verlet(DT, args.steps, sched)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    u, k, wv, npairs = g.energy()
+    print(json.dumps({"profile": sched, "precision": args.precision, "steps": args.steps,
+                      "ms_per_step": 1e3 * dt / max(1, args.steps), "pairs": npairs, "U": u, "K": k}))
+    g.close()
+
+
+def run_gb300(args, dist):
+    import torch
+    from paper_1401_4441_gb300 import build
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    if dist.rank == 0:
+        build.build()
+    dist.barrier()
+    from paper_1401_4441_gb300 import lc
+    lc.lib()
+
+    w = inputs.workload(args.workload, seed=inputs.DEFAULT_SEED + dist.rank)
+    pos, vel, box = w["pos"], w["vel"], w["box"]
+    n = pos.shape[0]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    g = lc.Box(box, RC, n, args.precision)
+    dpos = torch.from_numpy(pos).to(dev)
+    dvel = torch.from_numpy(vel).to(dev)
+    g.set_state(dpos, dvel)
+
+    # schedule: measured, unless fixed on the command line
+    sched_ms = {}
+    for s in ("colour", "atomic", "fullshell"):
+        g.set_state(dpos, dvel)
+        g.bin()
+        g.forces(s)
+        ts = []
+        for _ in range(3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.forces(s)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        sched_ms[s] = min(ts)
+    sched = min(sched_ms, key=sched_ms.get) if args.schedule == "auto" else args.schedule
+
+    g.set_state(dpos, dvel)
+    g.forces(sched)
+    _, _, _, npairs0 = g.energy()
+    for _ in range((args.warmup + 1) // 2):
+        g.verlet(DT, 2, sched)
+    torch.cuda.synchronize(dev)
+
+    # timed region: K steps in graph replays of two steps, L2 flushed between
+    calls = [2] * (args.steps // 2) + ([1] if args.steps % 2 else [])
+    clocks = ClockSampler(dist.local)
+    dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    time.sleep(0.3)
+    evs = []
+    for k in calls:
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.verlet(DT, k, sched)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = sum(a.elapsed_time(b) for a, b in evs)
+    _, _, _, npairs1 = g.energy()
+    per_force, per_step = g.launch_counts()
+    elapsed_ms = dist.max(elapsed_ms)
+    pairs = 0.5 * (npairs0 + npairs1) * args.steps
+    total_pairs = dist.sum(pairs)
+    value = total_pairs / (elapsed_ms * 1e-3)
+
+    # dominant kernel: the force sweep of one evaluation (binned state, L2 flushed)
+    counts = g.get("cell_count")
+    nc, _, _ = g.grid()
+    cand = half_shell_candidates(counts, nc)
+    _, _, _, npairs_now = g.energy()
+    flops = 8.0 * cand + 21.0 * npairs_now
+    fts = []
+    for _ in range(5):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.forces(sched)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        fts.append(e0.elapsed_time(e1))
+    t_force = statistics.median(fts) * 1e-3
+    achieved = flops / t_force / 1e12
+    sm_clock = 2070.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_clock * 1e6 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": f"k_force ({sched}, {args.precision}): one force evaluation",
+                "flops_per_eval": flops, "candidates": cand, "pairs": npairs_now,
+                "eval_ms": t_force * 1e3,
+                "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"}
+
+    # end to end through the public API with host buffers (pinned)
+    hpos = torch.from_numpy(pos).pin_memory()
+    hvel = torch.from_numpy(vel).pin_memory()
+    e2e_iters = 5
+    g.set_state(hpos, hvel)
+    g.forces(sched)
+    g.energy()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e2e_pairs = 0
+    for _ in range(e2e_iters):
+        g.set_state(hpos, hvel)          # H2D positions + velocities
+        g.forces(sched)                   # bin + force sweep
+        _, _, _, npp = g.energy()        # D2H energies + pair count
+        e2e_pairs += npp
+    e2e_s = time.perf_counter() - t0
+    e2e_s = dist.max(e2e_s)
+    e2e = {"value": dist.sum(e2e_pairs) / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(hpos.numel() * 8 + hvel.numel() * 8),
+           "d2h_bytes_per_step": 8 * 4 + 4,
+           "step": "lc_set_state(host) + lc_forces + lc_energy_virial"}
+    g.close()
+
+    if dist.rank == 0:
+        cpu = cpu_baseline(pos, box) if (dist.world == 1 and not args.no_cpu_baseline) else None
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
+                "data": "synthetic", "config": workload_config(args, w),
+                "steps_per_s": args.steps / (elapsed_ms * 1e-3) * dist.world,
+                "schedule": sched, "schedule_force_ms": sched_ms,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": per_step * args.steps}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--schedule", default="auto", choices=["auto", "colour", "atomic", "fullshell"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="liquid1m", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only warm-up + timed steps of one schedule (for ncu captures)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        elif args.profile:
+            run_profile(args, dist)
+        else:
+            run_gb300(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * lc.h -- C ABI of liblc.so: the link-cell Lennard-Jones force sweep with
+ * Newton's third law on one NVIDIA GB300 (sm_103a).
+ *
+ * The method (Niethammer, Glass, Gracia, "Avoiding Serialization Effects in
+ * Data / Dependency aware Task Parallel Algorithms for Spatial
+ * Decomposition"):
+ *   - Sec. IV: the box is divided into cells whose side is at least the
+ *     cutoff r_c, so all partners of a particle lie in its own cell or the 26
+ *     neighbouring cells (link-cell method).
+ *   - Sec. IV, Fig. 3b: with Newton's third law each pair is computed once;
+ *     only the centre cell and 13 of its neighbours (a half-shell) are
+ *     visited, and the result is written to both cells.  A cell-cell
+ *     interaction (intra- or inter-cell) is the unit of work.
+ *   - Sec. IV-V: two cell-cell interactions that share a cell write the same
+ *     force accumulators; this write sharing is the race the paper analyses.
+ *   - Sec. VI, Strategy 1, Fig. 6: loop exchange plus 2-strided colouring
+ *     makes the writes of one phase disjoint (LC_SCHED_COLOUR).
+ *   - Sec. VIII: commutative updates only need mutual exclusion, not an
+ *     order (LC_SCHED_ATOMIC resolves the sharing with atomic adds).
+ * Units are reduced Lennard-Jones units, sigma = epsilon = m = 1:
+ *   U(r) = 4 (r^-12 - r^-6) for r < r_c (truncated, not shifted),
+ *   F_i  = sum_j 24 (2 r^-12 - r^-6) / r^2 (r_i - r_j),
+ *   virial W = sum over pairs r_ij . F_ij, kinetic K = 1/2 sum v^2.
+ *
+ * Conventions for every call:
+ *   - Each call returns an lc_status; no call aborts or prints.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     queued on it; calls that hand results to the host synchronise it.
+ *   - Pointers passed in stay owned by the caller; the library reads or
+ *     writes them only during the call (host buffers) or, for device
+ *     buffers, in stream order before the call's work on `stream` ends.
+ *   - Arrays of 3-vectors are [n][3] doubles (x, y, z interleaved), indexed
+ *     by particle ID (0 .. n-1) unless stated otherwise.
+ *   - A context owns all of its device memory (allocated in lc_create or
+ *     lc_batch_create, freed in lc_destroy) and is used from one host thread
+ *     at a time.
+ */
+#ifndef LC_H
+#define LC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lc_ctx lc_ctx;
+
+typedef enum {
+    LC_OK = 0,
+    LC_ERR_INVALID_ARG = 1,   /* NULL pointer, n < 0, rc <= 0, unknown enum   */
+    LC_ERR_BOX_TOO_SMALL = 2, /* some L_d / r_c < 3: fewer than 3 cells        */
+    LC_ERR_CUDA = 3,          /* a CUDA runtime call failed                    */
+    LC_ERR_OOM = 4,           /* device allocation failed                      */
+    LC_ERR_NONFINITE = 5,     /* a position or velocity was NaN or infinite    */
+    LC_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up            */
+    LC_ERR_STATE = 7,         /* call order violated (e.g. no state set)       */
+    LC_ERR_RACE = 8,          /* a colour phase wrote one cell twice           */
+    LC_ERR_TOO_LARGE = 9      /* size beyond a stated maximum                  */
+} lc_status;
+
+/* How the write sharing between cell pairs is resolved (Sec. IV-VI). */
+typedef enum {
+    LC_SCHED_COLOUR = 0,    /* phases (offset group, colour), disjoint writes   */
+    LC_SCHED_ATOMIC = 1,    /* one pass, both cells updated by atomic adds      */
+    LC_SCHED_FULLSHELL = 2  /* all 27 cells, own cell written only, no Newton-3 */
+} lc_schedule;
+
+typedef enum {
+    LC_PREC_FP64 = 0,  /* FP64 positions, pair math and accumulation           */
+    LC_PREC_MIXED = 1  /* FP32 pair math on cell-local coordinates; FP64 cutoff
+                          decision near r_c; Kahan / FP64 cross-cell sums;
+                          FP64 positions, velocities, energy and virial        */
+} lc_precision;
+
+typedef enum {
+    LC_GET_CELL_COUNT = 0, /* int32[ncell]  particles per cell                 */
+    LC_GET_CELL_START = 1, /* int32[ncell]  exclusive prefix sum of the counts  */
+    LC_GET_PERM = 2,       /* int32[n]      slot -> particle ID (cell-sorted)   */
+    LC_GET_COLOUR = 3,     /* int8[ncell]   colour of each cell                 */
+    LC_GET_FORCES = 4,     /* double[n][3]  forces of the last evaluation       */
+    LC_GET_POS = 5,        /* double[n][3]  positions, wrapped into [0, L)      */
+    LC_GET_VEL = 6         /* double[n][3]  velocities                          */
+} lc_get_what;
+
+/* Create a context for one periodic orthorhombic box.
+ *   box[3]  edge lengths L_x, L_y, L_z (> 0)
+ *   rc      cutoff (> 0); cells per dimension nc_d = floor(L_d / rc) (Sec. IV)
+ *   n       number of particles (>= 0, < 2^26)
+ *   prec    arithmetic of the force sweep
+ * Allocates every device buffer the context needs on the current device.
+ * Errors: LC_ERR_INVALID_ARG, LC_ERR_BOX_TOO_SMALL, LC_ERR_TOO_LARGE,
+ * LC_ERR_OOM, LC_ERR_CUDA.  *out is NULL on error. */
+lc_status lc_create(const double box[3], double rc, int64_t n, lc_precision prec, lc_ctx **out);
+
+/* Copy the particle state in.  pos, vel: [n][3]; vel may be NULL (zero
+ * velocities).  id: reserved, must be NULL (IDs are 0 .. n-1, the row index).
+ * on_device != 0: the pointers are device memory, else host memory.
+ * Positions may lie outside the box; they are wrapped when binned.
+ * Marks the binning and the forces stale. */
+lc_status lc_set_state(lc_ctx *ctx, const double *pos, const double *vel, const int32_t *id,
+                       int on_device, void *stream);
+
+/* Counting-sort binning (link-cell construction, Sec. IV): wrap the
+ * positions, compute each particle's cell, count, scan and scatter so that
+ * every cell's particles are contiguous, ascending by ID inside a cell.  The
+ * particle state is stored in that order afterwards.  LC_ERR_NONFINITE if a
+ * position is not finite (reported by lc_energy_virial / lc_get, which read
+ * the device flag). */
+lc_status lc_bin(lc_ctx *ctx, void *stream);
+
+/* One force evaluation with the given schedule (bins first if the positions
+ * changed since the last binning).  Also produces the potential energy,
+ * the virial and the number of pairs inside r_c. */
+lc_status lc_forces(lc_ctx *ctx, lc_schedule sched, void *stream);
+
+/* nsteps velocity-Verlet steps of size dt (m = 1): v += dt/2 F; x += dt v;
+ * bin; F = F(x); v += dt/2 F.  Computes the forces first if they are stale.
+ * The step's kernels are captured once into a CUDA graph per (schedule, dt)
+ * and replayed. */
+lc_status lc_verlet_step(lc_ctx *ctx, double dt, int nsteps, lc_schedule sched, void *stream);
+
+/* Energies of the current state, FP64: potential U and virial W of the last
+ * force evaluation, kinetic K = 1/2 sum v^2 of the current velocities, and the
+ * number of pairs with r < r_c.  Any output pointer may be NULL.  Synchronises
+ * the stream; returns LC_ERR_NONFINITE / LC_ERR_TIMEOUT if a device flag
+ * was raised. */
+lc_status lc_energy_virial(lc_ctx *ctx, double *u_pot, double *k_kin, double *virial,
+                           int64_t *npairs, void *stream);
+
+/* Copy one array out (layouts under lc_get_what).  on_device != 0: dst is
+ * device memory.  Host copies synchronise the stream. */
+lc_status lc_get(lc_ctx *ctx, lc_get_what what, void *dst, int on_device, void *stream);
+
+/* Grid of the context: cells per dimension, number of colours, number of
+ * colour phases (4 offset groups x colours).  Any output may be NULL. */
+lc_status lc_grid(const lc_ctx *ctx, int32_t nc[3], int32_t *ncolours, int32_t *nphases);
+
+/* Race and coverage check of a schedule's work decomposition on the device
+ * (Sec. IV-VI: the write sharing between cell pairs).  Runs the schedule's
+ * own task enumeration without the force arithmetic.  For LC_SCHED_COLOUR
+ * every task stamps the cells it writes with its phase and counts cells
+ * stamped twice within one phase (*conflicts).  For every schedule each
+ * cell pair of the half-shell (the full shell for LC_SCHED_FULLSHELL) must be
+ * visited exactly once; *coverage_errors counts the pairs that are not.
+ * Synchronises the stream. */
+lc_status lc_schedule_check(lc_ctx *ctx, lc_schedule sched, int64_t *conflicts,
+                            int64_t *coverage_errors, void *stream);
+
+/* Tile shape of the force kernels: ni = particles of the centre cell held
+ * per warp (8, 16 or 32), warps = warps per thread block (1 .. 16).  0 keeps
+ * the current value.  Used by the autotuner. */
+lc_status lc_set_tile(lc_ctx *ctx, int ni, int warps);
+
+/* Number of kernels launched by the last lc_forces / lc_verlet_step call
+ * per force evaluation and per step (for accounting). */
+lc_status lc_launch_counts(const lc_ctx *ctx, int32_t *per_force, int32_t *per_step);
+
+void lc_destroy(lc_ctx *ctx);
+
+/* Static string naming a status code. */
+const char *lc_status_str(lc_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LC_H */

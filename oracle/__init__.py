@@ -155,15 +155,17 @@ def forces_sample(x, y, z, L, rc, ids):
     return f, nn
 
 
-def verlet(xyz, v, L, rc, dt, nsteps):
-    """Velocity Verlet in FP64; returns (xyz, v, f, energies[nsteps+1, (U, K, W)])."""
+def verlet(xyz, v, L, rc, dt, nsteps, f=None):
+    """Velocity Verlet in FP64; returns (xyz, v, f, energies[nsteps+1, (U, K, W)]).
+    If f (forces of xyz) is given the initial force evaluation is skipped."""
     lib = _load()
     xyz = np.ascontiguousarray(xyz, dtype=np.float64).copy()
     v = np.ascontiguousarray(v, dtype=np.float64).copy()
     n = xyz.shape[0]
-    f = np.zeros((n, 3), np.float64)
+    have_f = f is not None
+    f = np.zeros((n, 3), np.float64) if f is None else np.ascontiguousarray(f, dtype=np.float64).copy()
     e = np.zeros((nsteps + 1, 3), np.float64)
-    r = lib.orc_verlet(n, _d(xyz), _d(v), _d(f), 0, _d(_box(L)), float(rc), float(dt),
+    r = lib.orc_verlet(n, _d(xyz), _d(v), _d(f), int(have_f), _d(_box(L)), float(rc), float(dt),
                        int(nsteps), _d(e))
     if r:
         raise RuntimeError(f"orc_verlet failed ({r})")

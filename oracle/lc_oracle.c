@@ -396,19 +396,22 @@ int orc_forces_sample(int64_t n, const double *x, const double *y, const double 
  * v += dt/2 F.  x, v: [3n] interleaved by ID, updated in place; f holds the
  * forces of the current x on entry (computed here if *have_f == 0) and on
  * exit.  e_out[3*(s)] = (U, K, W) after step s for s = 0..nsteps (s = 0 is
- * the initial state).  Forces by orc_lc_forces. */
+ * the initial state; its U and W are NaN when have_f != 0).  Forces by
+ * orc_lc_forces. */
 int orc_verlet(int64_t n, double *xyz, double *v, double *f, int have_f,
                const double L[3], double rc, double dt, int nsteps, double *e_out)
 {
     double *px = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double *py = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double *pz = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-    double U = 0.0, W = 0.0;
+    double U = NAN, W = NAN;
     int64_t np;
+    int rc_ = 0;
     for (int64_t i = 0; i < n; ++i) { px[i] = xyz[3 * i]; py[i] = xyz[3 * i + 1]; pz[i] = xyz[3 * i + 2]; }
-    int rc_ = orc_lc_forces(n, px, py, pz, L, rc, f, &U, &W, &np);
-    if (rc_) return rc_;
-    (void)have_f;
+    if (!have_f) {  /* else f already holds F(x); U, W of step 0 stay NaN */
+        rc_ = orc_lc_forces(n, px, py, pz, L, rc, f, &U, &W, &np);
+        if (rc_) return rc_;
+    }
     double half = 0.5 * dt;
     for (int s = 0; s <= nsteps; ++s) {
         if (s > 0) {

@@ -1,0 +1,430 @@
+// Host side of the C ABI declared in include/lc.h: context set-up, buffer
+// ownership, call-order checks, CUDA-graph capture of the Verlet step.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "lc_internal.cuh"
+
+namespace lc {
+
+void make_stencil(Stencil *s) {
+    int k = 0;
+    for (int oz = -1; oz <= 1; ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+            for (int ox = -1; ox <= 1; ++ox) {
+                bool fwd = oz > 0 || (oz == 0 && oy > 0) || (oz == 0 && oy == 0 && ox > 0);
+                if (!fwd) continue;
+                s->hs[k][0] = ox; s->hs[k][1] = oy; s->hs[k][2] = oz;
+                ++k;
+            }
+    // Offsets with pairwise different parity patterns (|ox|,|oy|,|oz|) may
+    // share a colour phase: two same-colour cells differ by an even number of
+    // cells per dimension, so A + o == A' + o' forces o == o' (mod 2).
+    // Each offset goes to the first group that lacks its pattern.
+    bool used[4][8] = {};
+    int cnt[4] = {0, 0, 0, 0};
+    int members[4][13];
+    for (int i = 0; i < 13; ++i) {
+        int pat = (s->hs[i][0] != 0) + 2 * (s->hs[i][1] != 0) + 4 * (s->hs[i][2] != 0);
+        int g = 0;
+        while (used[g][pat]) ++g;
+        used[g][pat] = true;
+        s->group_of[i] = g;
+        members[g][cnt[g]++] = i;
+    }
+    int pos = 0;
+    for (int g = 0; g < 4; ++g) {
+        s->group_first[g] = pos;
+        for (int i = 0; i < cnt[g]; ++i) s->group_list[pos++] = members[g][i];
+    }
+    s->group_first[4] = pos;
+    // full shell: centre first, then the other 26 in (z, y, x) order
+    s->full[0][0] = s->full[0][1] = s->full[0][2] = 0;
+    int f = 1;
+    for (int oz = -1; oz <= 1; ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+            for (int ox = -1; ox <= 1; ++ox) {
+                if (!ox && !oy && !oz) continue;
+                s->full[f][0] = ox; s->full[f][1] = oy; s->full[f][2] = oz;
+                ++f;
+            }
+}
+
+void make_grid(Grid *g, const double box[3], double rc) {
+    memset(g, 0, sizeof(*g));
+    g->rc = rc;
+    g->rc2 = rc * rc;
+    g->ncell = 1;
+    for (int d = 0; d < 3; ++d) {
+        g->L[d] = box[d];
+        g->nc[d] = (int)floor(box[d] / rc);
+        g->h[d] = box[d] / (double)g->nc[d];
+        g->inv[d] = (double)g->nc[d] / box[d];
+        g->hf[d] = (float)g->h[d];
+        g->ncell *= g->nc[d];
+    }
+    float rc2f = (float)g->rc2;
+    g->rc2f_lo = rc2f * (1.0f - kCutBand);
+    g->rc2f_hi = rc2f * (1.0f + kCutBand);
+    for (int d = 0; d < 3; ++d) {
+        for (int a = 0; a < 3; ++a) g->class_count[d][a] = 0;
+        for (int c = 0; c < g->nc[d]; ++c) g->class_count[d][colour_class(c, g->nc[d])]++;
+    }
+    int r = 0;
+    for (int raw = 0; raw < 27; ++raw) {
+        int a[3] = {raw % 3, (raw / 3) % 3, raw / 9};
+        bool present = g->class_count[0][a[0]] && g->class_count[1][a[1]] && g->class_count[2][a[2]];
+        g->colour_of_raw[raw] = present ? r : -1;
+        g->raw_of_colour[raw] = -1;
+        if (present) { g->raw_of_colour[r] = raw; ++r; }
+    }
+    g->ncolours = r;
+}
+
+}  // namespace lc
+
+using namespace lc;
+
+struct lc_ctx : public Ctx {};
+
+static lc_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return LC_OK;
+    if (e == cudaErrorMemoryAllocation) return LC_ERR_OOM;
+    return LC_ERR_CUDA;
+}
+
+#define LC_TRY(expr)                              \
+    do {                                          \
+        cudaError_t _e = (expr);                  \
+        if (_e != cudaSuccess) {                  \
+            cudaGetLastError();                   \
+            return from_cuda(_e);                 \
+        }                                         \
+    } while (0)
+
+template <typename T>
+static cudaError_t dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, sizeof(T) * count);
+}
+
+static void free_ctx(Ctx *c) {
+    if (!c) return;
+    void *ptrs[] = {c->cur.x, c->cur.vx, c->cur.id, c->nxt.x, c->nxt.vx, c->nxt.id, c->d_cell, c->d_rank,
+                    c->d_count, c->d_start, c->d_src, c->d_blocksums, c->d_colour, c->d_p4, c->fx, c->kx,
+                    c->d_warp_acc, c->d_warp_pairs, c->d_kin_part, c->d_result, c->d_npairs, c->d_err,
+                    c->d_stamp, c->d_visit, c->d_counters};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (int k = 0; k < 6; ++k)
+        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+    delete static_cast<lc_ctx *>(c);
+}
+
+static cudaError_t alloc_state(State *st, int64_t n) {
+    cudaError_t e;
+    double *xs, *vs;
+    if ((e = dalloc(&xs, 3 * (size_t)n))) return e;
+    st->x = xs; st->y = xs + n; st->z = xs + 2 * n;
+    if ((e = dalloc(&vs, 3 * (size_t)n))) return e;
+    st->vx = vs; st->vy = vs + n; st->vz = vs + 2 * n;
+    return dalloc(&st->id, (size_t)n);
+}
+
+extern "C" {
+
+const char *lc_status_str(lc_status s) {
+    switch (s) {
+        case LC_OK: return "ok";
+        case LC_ERR_INVALID_ARG: return "invalid argument";
+        case LC_ERR_BOX_TOO_SMALL: return "box too small: fewer than 3 cells of side >= rc in some dimension";
+        case LC_ERR_CUDA: return "CUDA runtime error";
+        case LC_ERR_OOM: return "device out of memory";
+        case LC_ERR_NONFINITE: return "non-finite position or velocity";
+        case LC_ERR_TIMEOUT: return "bounded device wait expired";
+        case LC_ERR_STATE: return "call order violated";
+        case LC_ERR_RACE: return "colour phase wrote a cell twice";
+        case LC_ERR_TOO_LARGE: return "size beyond the supported maximum";
+    }
+    return "unknown status";
+}
+
+lc_status lc_create(const double box[3], double rc, int64_t n, lc_precision prec, lc_ctx **out) {
+    if (!out) return LC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!box || !(rc > 0.0) || n < 0 || (prec != LC_PREC_FP64 && prec != LC_PREC_MIXED)) return LC_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (!(box[d] > 0.0) || !isfinite(box[d])) return LC_ERR_INVALID_ARG;
+    if (n >= kMaxParticles) return LC_ERR_TOO_LARGE;
+    for (int d = 0; d < 3; ++d)
+        if (floor(box[d] / rc) < 3.0) return LC_ERR_BOX_TOO_SMALL;
+    if (floor(box[0] / rc) * floor(box[1] / rc) * floor(box[2] / rc) > 1.0e9) return LC_ERR_TOO_LARGE;
+
+    lc_ctx *c = new lc_ctx();
+    memset(static_cast<Ctx *>(c), 0, sizeof(Ctx));
+    make_grid(&c->g, box, rc);
+    c->n = n;
+    c->prec = prec;
+    c->ni = 16;
+    c->warps = 8;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e) { cudaGetLastError(); free_ctx(c); return from_cuda(e); }
+    Stencil st;
+    make_stencil(&st);
+    const size_t N = (size_t)n, NC = (size_t)c->g.ncell;
+    const int ntiles = (c->g.ncell + 4095) / 4096;
+    c->nwarp_max = c->num_sms * 64;
+    if ((e = upload_stencil(st)) || (e = alloc_state(&c->cur, n)) || (e = alloc_state(&c->nxt, n)) ||
+        (e = dalloc(&c->d_cell, N)) || (e = dalloc(&c->d_rank, N)) || (e = dalloc(&c->d_count, NC)) ||
+        (e = dalloc(&c->d_start, NC + 1)) || (e = dalloc(&c->d_src, N)) ||
+        (e = dalloc(&c->d_blocksums, (size_t)ntiles + 1)) || (e = dalloc(&c->d_colour, NC)) ||
+        (e = dalloc(&c->d_p4, N)) || (e = dalloc(&c->fx, 3 * N)) || (e = dalloc(&c->kx, 3 * N)) ||
+        (e = dalloc(&c->d_warp_acc, 4 * (size_t)c->nwarp_max)) || (e = dalloc(&c->d_warp_pairs, (size_t)c->nwarp_max)) ||
+        (e = dalloc(&c->d_kin_part, (size_t)c->num_sms * 2)) || (e = dalloc(&c->d_result, 4)) ||
+        (e = dalloc(&c->d_npairs, 1)) || (e = dalloc(&c->d_err, 1)) || (e = dalloc(&c->d_stamp, NC)) ||
+        (e = dalloc(&c->d_visit, 27 * NC)) || (e = dalloc(&c->d_counters, 4))) {
+        cudaGetLastError();
+        free_ctx(c);
+        return from_cuda(e);
+    }
+    c->state_a = c->cur.x;
+    if ((e = init_force_kernels())) { cudaGetLastError(); free_ctx(c); return from_cuda(e); }
+    c->fy = c->fx + N; c->fz = c->fx + 2 * N;
+    c->ky = c->kx + N; c->kz = c->kx + 2 * N;
+    cudaStream_t s = 0;
+    if ((e = cudaMemsetAsync(c->d_err, 0, sizeof(int), s)) || (e = cudaMemsetAsync(c->d_result, 0, 4 * sizeof(double), s)) ||
+        (e = cudaMemsetAsync(c->fx, 0, 3 * N * sizeof(double), s)) || (e = launch_colour(c, s)) ||
+        (e = cudaStreamSynchronize(s))) {
+        cudaGetLastError();
+        free_ctx(c);
+        return from_cuda(e);
+    }
+    *out = c;
+    return LC_OK;
+}
+
+void lc_destroy(lc_ctx *ctx) {
+    if (!ctx) return;
+    cudaDeviceSynchronize();
+    free_ctx(ctx);
+}
+
+lc_status lc_set_state(lc_ctx *c, const double *pos, const double *vel, const int32_t *id, int on_device,
+                       void *stream) {
+    if (!c || (!pos && c->n > 0) || id) return LC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * 3 * (size_t)c->n;
+    const double *dpos = pos, *dvel = vel;
+    if (c->n > 0 && !on_device) {
+        // stage through the force buffer (3n doubles) and the Kahan buffer
+        LC_TRY(cudaMemcpyAsync(c->fx, pos, bytes, cudaMemcpyHostToDevice, s));
+        dpos = c->fx;
+        if (vel) {
+            LC_TRY(cudaMemcpyAsync(c->nxt.x, vel, bytes, cudaMemcpyHostToDevice, s));
+            dvel = c->nxt.x;
+        }
+    }
+    LC_TRY(launch_set_state(c, dpos, dvel, s));
+    LC_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
+    if (!on_device) LC_TRY(cudaStreamSynchronize(s));  // host buffers are the caller's again on return
+    c->have_state = true;
+    c->binned = false;
+    c->forces_valid = false;
+    return LC_OK;
+}
+
+lc_status lc_bin(lc_ctx *c, void *stream) {
+    if (!c) return LC_ERR_INVALID_ARG;
+    if (!c->have_state) return LC_ERR_STATE;
+    int launches = 0;
+    LC_TRY(launch_bin(c, (cudaStream_t)stream, &launches));
+    c->binned = true;
+    return LC_OK;
+}
+
+static lc_status do_forces(lc_ctx *c, lc_schedule sched, cudaStream_t s, int *launches) {
+    if (!c->binned) {
+        LC_TRY(launch_bin(c, s, launches));
+        c->binned = true;
+    }
+    LC_TRY(launch_forces(c, sched, s, launches));
+    c->forces_valid = true;
+    return LC_OK;
+}
+
+lc_status lc_forces(lc_ctx *c, lc_schedule sched, void *stream) {
+    if (!c || sched < LC_SCHED_COLOUR || sched > LC_SCHED_FULLSHELL) return LC_ERR_INVALID_ARG;
+    if (!c->have_state) return LC_ERR_STATE;
+    int launches = 0;
+    lc_status st = do_forces(c, sched, (cudaStream_t)stream, &launches);
+    c->launches_force = launches;
+    return st;
+}
+
+// One Verlet step as a sequence of stream-ordered launches.
+static cudaError_t step_launches(lc_ctx *c, double dt, lc_schedule sched, cudaStream_t s, int *launches) {
+    cudaError_t e;
+    if ((e = launch_kick_drift(c, dt, s))) return e;
+    ++*launches;
+    if ((e = launch_bin(c, s, launches))) return e;
+    if ((e = launch_forces(c, sched, s, launches))) return e;
+    if ((e = launch_kick(c, dt, s))) return e;
+    ++*launches;
+    return cudaSuccess;
+}
+
+lc_status lc_verlet_step(lc_ctx *c, double dt, int nsteps, lc_schedule sched, void *stream) {
+    if (!c || nsteps < 0 || !isfinite(dt) || sched < LC_SCHED_COLOUR || sched > LC_SCHED_FULLSHELL)
+        return LC_ERR_INVALID_ARG;
+    if (!c->have_state) return LC_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    int launches = 0;
+    if (!c->forces_valid) {
+        lc_status st = do_forces(c, sched, s, &launches);
+        if (st) return st;
+    }
+    if (nsteps == 0) return LC_OK;
+    // The step swaps the two state buffers once (in the binning), so one
+    // graph holds two steps and returns the buffers to where they were; a
+    // separate graph serves each buffer parity.
+    const int k = 2 * (int)sched + (c->cur.x == c->state_a ? 0 : 1);
+    if (!c->graph[k] || c->graph_dt[k] != dt) {
+        if (c->graph[k]) { cudaGraphExecDestroy(c->graph[k]); c->graph[k] = nullptr; }
+        cudaStream_t cap;
+        LC_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        State saved_cur = c->cur, saved_nxt = c->nxt;
+        cudaGraph_t graph;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        int per2 = 0;
+        if (!e) e = step_launches(c, dt, sched, cap, &per2);
+        if (!e) e = step_launches(c, dt, sched, cap, &per2);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        c->cur = saved_cur; c->nxt = saved_nxt;   // two swaps: same as before
+        if (!e) e = e2;
+        if (!e) e = cudaGraphInstantiate(&c->graph[k], graph, 0);
+        if (graph && !e2) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cap);
+        if (e) { cudaGetLastError(); c->graph[k] = nullptr; return from_cuda(e); }
+        c->graph_dt[k] = dt;
+        c->launches_step = per2 / 2;
+    }
+    int done = 0;
+    while (done + 2 <= nsteps) {
+        LC_TRY(cudaGraphLaunch(c->graph[k], s));
+        done += 2;
+    }
+    if (done < nsteps) {
+        int l = 0;
+        LC_TRY(step_launches(c, dt, sched, s, &l));
+        ++done;
+    }
+    c->binned = true;
+    c->forces_valid = true;
+    return LC_OK;
+}
+
+static lc_status read_err(lc_ctx *c, cudaStream_t s) {
+    int err = 0;
+    LC_TRY(cudaMemcpyAsync(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LC_TRY(cudaStreamSynchronize(s));
+    if (err & kErrNonfinite) return LC_ERR_NONFINITE;
+    if (err & kErrTimeout) return LC_ERR_TIMEOUT;
+    return LC_OK;
+}
+
+lc_status lc_energy_virial(lc_ctx *c, double *u_pot, double *k_kin, double *virial, int64_t *npairs, void *stream) {
+    if (!c) return LC_ERR_INVALID_ARG;
+    if (!c->have_state) return LC_ERR_STATE;
+    if ((u_pot || virial || npairs) && !c->forces_valid) return LC_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    LC_TRY(launch_kinetic(c, s));
+    double r[4];
+    long long np = 0;
+    LC_TRY(cudaMemcpyAsync(r, c->d_result, sizeof(r), cudaMemcpyDeviceToHost, s));
+    LC_TRY(cudaMemcpyAsync(&np, c->d_npairs, sizeof(np), cudaMemcpyDeviceToHost, s));
+    lc_status st = read_err(c, s);
+    if (st) return st;
+    if (u_pot) *u_pot = r[0];
+    if (virial) *virial = r[1];
+    if (npairs) *npairs = (int64_t)np;
+    if (k_kin) *k_kin = r[3];
+    return LC_OK;
+}
+
+lc_status lc_get(lc_ctx *c, lc_get_what what, void *dst, int on_device, void *stream) {
+    if (!c || !dst) return LC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = (size_t)c->n, NC = (size_t)c->g.ncell;
+    const void *src = nullptr;
+    size_t bytes = 0;
+    switch (what) {
+        case LC_GET_CELL_COUNT: if (!c->binned) return LC_ERR_STATE; src = c->d_count; bytes = 4 * NC; break;
+        case LC_GET_CELL_START: if (!c->binned) return LC_ERR_STATE; src = c->d_start; bytes = 4 * NC; break;
+        case LC_GET_PERM: if (!c->binned) return LC_ERR_STATE; src = c->cur.id; bytes = 4 * N; break;
+        case LC_GET_COLOUR: src = c->d_colour; bytes = NC; break;
+        case LC_GET_FORCES:
+        case LC_GET_POS:
+        case LC_GET_VEL: {
+            if (!c->have_state) return LC_ERR_STATE;
+            if (what == LC_GET_FORCES && !c->forces_valid) return LC_ERR_STATE;
+            double *tmp = c->nxt.x;   // 3n doubles of scratch between binnings
+            if (what == LC_GET_FORCES) LC_TRY(launch_unsort_vec(c, c->fx, c->fy, c->fz, tmp, s, 0));
+            else if (what == LC_GET_POS) LC_TRY(launch_unsort_vec(c, c->cur.x, c->cur.y, c->cur.z, tmp, s, 1));
+            else LC_TRY(launch_unsort_vec(c, c->cur.vx, c->cur.vy, c->cur.vz, tmp, s, 0));
+            src = tmp;
+            bytes = 3 * N * sizeof(double);
+            break;
+        }
+        default: return LC_ERR_INVALID_ARG;
+    }
+    if (bytes == 0) return LC_OK;
+    LC_TRY(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (!on_device) return read_err(c, s);
+    return LC_OK;
+}
+
+lc_status lc_grid(const lc_ctx *c, int32_t nc[3], int32_t *ncolours, int32_t *nphases) {
+    if (!c) return LC_ERR_INVALID_ARG;
+    if (nc) for (int d = 0; d < 3; ++d) nc[d] = c->g.nc[d];
+    if (ncolours) *ncolours = c->g.ncolours;
+    if (nphases) *nphases = 4 * c->g.ncolours;
+    return LC_OK;
+}
+
+lc_status lc_schedule_check(lc_ctx *c, lc_schedule sched, int64_t *conflicts, int64_t *coverage_errors, void *stream) {
+    if (!c || sched < LC_SCHED_COLOUR || sched > LC_SCHED_FULLSHELL) return LC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    LC_TRY(launch_schedule_check(c, sched, s));
+    unsigned long long cnt[4];
+    LC_TRY(cudaMemcpyAsync(cnt, c->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    LC_TRY(cudaStreamSynchronize(s));
+    if (conflicts) *conflicts = cnt[0];
+    if (coverage_errors) *coverage_errors = cnt[1];
+    return cnt[0] ? LC_ERR_RACE : LC_OK;
+}
+
+lc_status lc_set_tile(lc_ctx *c, int ni, int warps) {
+    if (!c) return LC_ERR_INVALID_ARG;
+    if (ni && ni != 8 && ni != 16 && ni != 32) return LC_ERR_INVALID_ARG;
+    if (warps < 0 || warps > 16) return LC_ERR_INVALID_ARG;
+    if (ni) c->ni = ni;
+    if (warps) c->warps = warps;
+    for (int k = 0; k < 6; ++k)
+        if (c->graph[k]) { cudaGraphExecDestroy(c->graph[k]); c->graph[k] = nullptr; }
+    return LC_OK;
+}
+
+lc_status lc_launch_counts(const lc_ctx *c, int32_t *per_force, int32_t *per_step) {
+    if (!c) return LC_ERR_INVALID_ARG;
+    if (per_force) *per_force = c->launches_force;
+    if (per_step) *per_step = c->launches_step;
+    return LC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,286 @@
+// Counting-sort binning of the link-cell method (paper Sec. IV: cells of
+// side >= r_c, partners only in the 27 surrounding cells).
+//
+//   k_cellid    wrap (FP64, each op rounded once), cell index, atomic count
+//               per cell; the atomic's return value is a provisional rank
+//   k_scan_*    exclusive prefix sum of the counts -> cell start
+//   k_scatter   provisional slot start[cell] + rank
+//   k_cellsort  one warp per cell: rank the cell's particles by ID (counting
+//               comparison, so the result does not depend on the order in
+//               which the atomics were served), then gather the FP64 state
+//               into the new slot and write the FP32 cell-centre-local
+//               coordinates used by the mixed-precision force sweep.
+// The final permutation is stable by particle ID inside each cell, so the
+// whole binning is bit-exact and reproducible.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lc_internal.cuh"
+
+namespace lc {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__global__ void k_cellid(Grid g, int n, const double *__restrict__ x, const double *__restrict__ y,
+                         const double *__restrict__ z, int *__restrict__ cell, int *__restrict__ rank,
+                         int *__restrict__ count, int *__restrict__ err) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        double X = x[s], Y = y[s], Z = z[s];
+        int c = 0;
+        if (isfinite(X) && isfinite(Y) && isfinite(Z)) {
+            int cx = cell_coord(wrap_coord(X, g.L[0]), g.inv[0], g.nc[0]);
+            int cy = cell_coord(wrap_coord(Y, g.L[1]), g.inv[1], g.nc[1]);
+            int cz = cell_coord(wrap_coord(Z, g.L[2]), g.inv[2], g.nc[2]);
+            c = cx + g.nc[0] * (cy + g.nc[1] * cz);
+        } else {
+            atomicOr(err, kErrNonfinite);
+        }
+        cell[s] = c;
+        rank[s] = atomicAdd(count + c, 1);
+    }
+}
+
+// Block-level exclusive scan of kScanTile counts; block totals to partial[].
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(int ncell, const int *__restrict__ count,
+                                                            int *__restrict__ start, int *__restrict__ partial) {
+    __shared__ int warp_tot[kScanThreads / 32];
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (base + k < ncell) ? count[base + k] : 0;
+        sum += v[k];
+    }
+    // warp inclusive scan of the thread sums
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int inc = sum;
+#pragma unroll
+    for (int m = 1; m < 32; m <<= 1) {
+        int t = __shfl_up_sync(kFull, inc, m);
+        if (lane >= m) inc += t;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int t = warp_tot[lane];
+        int ti = t;
+#pragma unroll
+        for (int m = 1; m < 32; m <<= 1) {
+            int u = __shfl_up_sync(kFull, ti, m);
+            if (lane >= m) ti += u;
+        }
+        warp_tot[lane] = ti - t;   // exclusive
+        if (lane == 31) partial[blockIdx.x] = ti;
+    }
+    __syncthreads();
+    int run = warp_tot[wid] + inc - sum;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < ncell) start[base + k] = run;
+        run += v[k];
+    }
+}
+
+// Exclusive scan of the tile totals (one block; loops if there are more
+// tiles than threads).
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials(int ntiles, int *__restrict__ partial) {
+    __shared__ int warp_tot[kScanThreads / 32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int b0 = 0; b0 < ntiles; b0 += kScanThreads) {
+        int i = b0 + threadIdx.x;
+        int v = i < ntiles ? partial[i] : 0;
+        int inc = v;
+#pragma unroll
+        for (int m = 1; m < 32; m <<= 1) {
+            int t = __shfl_up_sync(kFull, inc, m);
+            if (lane >= m) inc += t;
+        }
+        if (lane == 31) warp_tot[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            int t = warp_tot[lane];
+            int ti = t;
+#pragma unroll
+            for (int m = 1; m < 32; m <<= 1) {
+                int u = __shfl_up_sync(kFull, ti, m);
+                if (lane >= m) ti += u;
+            }
+            warp_tot[lane] = ti - t;
+        }
+        __syncthreads();
+        int c0 = carry;
+        if (i < ntiles) partial[i] = c0 + warp_tot[wid] + inc - v;
+        __syncthreads();
+        if (threadIdx.x == kScanThreads - 1) carry = c0 + warp_tot[wid] + inc;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_add(int ncell, int n, int *__restrict__ start, const int *__restrict__ partial) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x)
+        start[c] += partial[c / kScanTile];
+    if (blockIdx.x == 0 && threadIdx.x == 0) start[ncell] = n;
+}
+
+__global__ void k_scatter(int n, const int *__restrict__ cell, const int *__restrict__ rank,
+                          const int *__restrict__ start, int *__restrict__ src) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        src[start[cell[s]] + rank[s]] = s;
+}
+
+// One warp per cell.  Rank of an entry = number of entries of the cell with
+// a smaller ID (IDs are unique), so slot = start + rank is stable by ID.
+__global__ void k_cellsort(Grid g, int write_p4, const int *__restrict__ start, const int *__restrict__ count,
+                           const int *__restrict__ src, State in, State out, float4 *__restrict__ p4) {
+    const int lane = threadIdx.x & 31;
+    const int W = gridDim.x * (blockDim.x >> 5);
+    for (int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < g.ncell; c += W) {
+        const int base = start[c], cnt = count[c];
+        int cc[3];
+        cc[0] = c % g.nc[0];
+        cc[1] = (c / g.nc[0]) % g.nc[1];
+        cc[2] = c / (g.nc[0] * g.nc[1]);
+        double org[3];
+        for (int d = 0; d < 3; ++d) org[d] = __dmul_rn((double)cc[d] + 0.5, g.h[d]);
+        for (int e0 = 0; e0 < cnt; e0 += 32) {
+            const int e = e0 + lane;
+            int my_src = 0, my_id = 0;
+            if (e < cnt) {
+                my_src = src[base + e];
+                my_id = in.id[my_src];
+            }
+            int r = 0;
+            if (cnt <= 32) {
+                for (int k = 0; k < cnt; ++k) {
+                    int other = __shfl_sync(kFull, my_id, k);
+                    r += (other < my_id) ? 1 : 0;
+                }
+            } else if (e < cnt) {
+                for (int k = 0; k < cnt; ++k) r += (in.id[src[base + k]] < my_id) ? 1 : 0;
+            }
+            if (e < cnt) {
+                const int dst = base + r;
+                double X = wrap_coord(in.x[my_src], g.L[0]);
+                double Y = wrap_coord(in.y[my_src], g.L[1]);
+                double Z = wrap_coord(in.z[my_src], g.L[2]);
+                out.x[dst] = X; out.y[dst] = Y; out.z[dst] = Z;
+                out.vx[dst] = in.vx[my_src]; out.vy[dst] = in.vy[my_src]; out.vz[dst] = in.vz[my_src];
+                out.id[dst] = my_id;
+                if (write_p4) {
+                    // FP32 offsets from the cell centre; the rounding residual of
+                    // each (|r| <= 2^-23 for |offset| < 4) is kept as a 10-bit
+                    // signed fraction of 2^-23 in the spare fourth word.
+                    double l[3] = {__dsub_rn(X, org[0]), __dsub_rn(Y, org[1]), __dsub_rn(Z, org[2])};
+                    float hi[3];
+                    unsigned w = 0;
+                    for (int d = 0; d < 3; ++d) {
+                        hi[d] = (float)l[d];
+                        double r = __dsub_rn(l[d], (double)hi[d]);
+                        int q = (int)rint(r * kLoScale);
+                        q = q > 511 ? 511 : (q < -511 ? -511 : q);
+                        w |= (unsigned)(q + 512) << (10 * d);
+                    }
+                    p4[dst] = make_float4(hi[0], hi[1], hi[2], __uint_as_float(w));
+                }
+            }
+        }
+    }
+}
+
+__global__ void k_colour(Grid g, int8_t *colour) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncell; c += gridDim.x * blockDim.x) {
+        int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
+        int raw = colour_class(cx, g.nc[0]) + 3 * colour_class(cy, g.nc[1]) + 9 * colour_class(cz, g.nc[2]);
+        colour[c] = (int8_t)g.colour_of_raw[raw];
+    }
+}
+
+cudaError_t launch_colour(Ctx *c, cudaStream_t s) {
+    k_colour<<<c->num_sms * 4, 256, 0, s>>>(c->g, c->d_colour);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches) {
+    const int n = (int)c->n;
+    const int ncell = c->g.ncell;
+    const int ntiles = (ncell + kScanTile - 1) / kScanTile;
+    const int grid_n = c->num_sms * 8;
+    cudaError_t e = cudaMemsetAsync(c->d_count, 0, sizeof(int) * (size_t)ncell, s);
+    if (e) return e;
+    if (n > 0) {
+        k_cellid<<<grid_n, 256, 0, s>>>(c->g, n, c->cur.x, c->cur.y, c->cur.z, c->d_cell, c->d_rank,
+                                        c->d_count, c->d_err);
+        ++*launches;
+    }
+    k_scan_tiles<<<ntiles, kScanThreads, 0, s>>>(ncell, c->d_count, c->d_start, c->d_blocksums);
+    k_scan_partials<<<1, kScanThreads, 0, s>>>(ntiles, c->d_blocksums);
+    k_scan_add<<<c->num_sms * 4, 256, 0, s>>>(ncell, n, c->d_start, c->d_blocksums);
+    *launches += 3;
+    if (n > 0) {
+        k_scatter<<<grid_n, 256, 0, s>>>(n, c->d_cell, c->d_rank, c->d_start, c->d_src);
+        k_cellsort<<<c->num_sms * 8, 256, 0, s>>>(c->g, c->prec == LC_PREC_MIXED, c->d_start, c->d_count,
+                                                  c->d_src, c->cur, c->nxt, c->d_p4);
+        *launches += 2;
+    }
+    e = cudaGetLastError();
+    if (e) return e;
+    State t = c->cur; c->cur = c->nxt; c->nxt = t;
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------- state I/O ---
+__global__ void k_deinterleave(int n, const double *__restrict__ in, double *__restrict__ a,
+                               double *__restrict__ b, double *__restrict__ cc) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        a[s] = in[3 * s + 0]; b[s] = in[3 * s + 1]; cc[s] = in[3 * s + 2];
+    }
+}
+
+__global__ void k_iota(int n, int *id) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) id[s] = s;
+}
+
+// dst[id[s]] = (a[s], b[s], c[s]); wrap != 0 wraps positions into [0, L).
+__global__ void k_unsort_vec(int n, Grid g, int wrap, const int *__restrict__ id, const double *__restrict__ a,
+                             const double *__restrict__ b, const double *__restrict__ cc, double *__restrict__ dst) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        double va = a[s], vb = b[s], vc = cc[s];
+        if (wrap) {
+            va = wrap_coord(va, g.L[0]); vb = wrap_coord(vb, g.L[1]); vc = wrap_coord(vc, g.L[2]);
+        }
+        int i = id[s];
+        dst[3 * i + 0] = va; dst[3 * i + 1] = vb; dst[3 * i + 2] = vc;
+    }
+}
+
+cudaError_t launch_set_state(Ctx *c, const double *pos, const double *vel, cudaStream_t s) {
+    const int n = (int)c->n;
+    if (n == 0) return cudaSuccess;
+    const int grid_n = c->num_sms * 8;
+    k_deinterleave<<<grid_n, 256, 0, s>>>(n, pos, c->cur.x, c->cur.y, c->cur.z);
+    if (vel) {
+        k_deinterleave<<<grid_n, 256, 0, s>>>(n, vel, c->cur.vx, c->cur.vy, c->cur.vz);
+    } else {
+        cudaMemsetAsync(c->cur.vx, 0, sizeof(double) * (size_t)n, s);
+        cudaMemsetAsync(c->cur.vy, 0, sizeof(double) * (size_t)n, s);
+        cudaMemsetAsync(c->cur.vz, 0, sizeof(double) * (size_t)n, s);
+    }
+    k_iota<<<grid_n, 256, 0, s>>>(n, c->cur.id);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unsort_vec(Ctx *c, const double *a, const double *b, const double *cc, double *dst,
+                              cudaStream_t s, int wrap) {
+    const int n = (int)c->n;
+    if (n == 0) return cudaSuccess;
+    k_unsort_vec<<<c->num_sms * 8, 256, 0, s>>>(n, c->g, wrap, c->cur.id, a, b, cc, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace lc

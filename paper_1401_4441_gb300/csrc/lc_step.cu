@@ -1,0 +1,131 @@
+// Velocity-Verlet integration (m = 1) and the FP64 reductions of energy,
+// virial and kinetic energy.  All state lives in cell-sorted order, so the
+// integrator streams contiguous FP64 arrays; every product and sum is
+// rounded once (__dmul_rn / __dadd_rn), as in the definition
+//   v <- v + (dt/2) F,  x <- x + dt v   (wrap happens in the next binning).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lc_internal.cuh"
+
+namespace lc {
+
+constexpr int kRedThreads = 1024;
+
+__global__ void k_kick_drift(int n, double half, double dt, State st, const double *__restrict__ fx,
+                             const double *__restrict__ fy, const double *__restrict__ fz) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        double vx = __dadd_rn(st.vx[s], __dmul_rn(half, fx[s]));
+        double vy = __dadd_rn(st.vy[s], __dmul_rn(half, fy[s]));
+        double vz = __dadd_rn(st.vz[s], __dmul_rn(half, fz[s]));
+        st.vx[s] = vx; st.vy[s] = vy; st.vz[s] = vz;
+        st.x[s] = __dadd_rn(st.x[s], __dmul_rn(dt, vx));
+        st.y[s] = __dadd_rn(st.y[s], __dmul_rn(dt, vy));
+        st.z[s] = __dadd_rn(st.z[s], __dmul_rn(dt, vz));
+    }
+}
+
+__global__ void k_kick(int n, double half, State st, const double *__restrict__ fx,
+                       const double *__restrict__ fy, const double *__restrict__ fz) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        st.vx[s] = __dadd_rn(st.vx[s], __dmul_rn(half, fx[s]));
+        st.vy[s] = __dadd_rn(st.vy[s], __dmul_rn(half, fy[s]));
+        st.vz[s] = __dadd_rn(st.vz[s], __dmul_rn(half, fz[s]));
+    }
+}
+
+// Block partial sums of v^2 (grid-stride, fixed assignment: deterministic).
+__global__ void __launch_bounds__(256) k_kinetic(int n, State st, double *__restrict__ part) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        double vx = st.vx[s], vy = st.vy[s], vz = st.vz[s];
+        acc += vx * vx + vy * vy + vz * vz;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int m = 128; m > 0; m >>= 1) {
+        if (threadIdx.x < m) red[threadIdx.x] += red[threadIdx.x + m];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// Sum of the per-warp partials in a fixed tree order.
+// out[0] = U, out[1] = W, out[2] = pairs, out[3] = K (kinetic pass only).
+__global__ void __launch_bounds__(kRedThreads) k_final_pot(int nw, const double *__restrict__ warp_acc,
+                                                           const long long *__restrict__ warp_pairs, int full,
+                                                           double *__restrict__ out, long long *__restrict__ npairs) {
+    __shared__ double r6[kRedThreads], r12[kRedThreads];
+    __shared__ long long rp[kRedThreads];
+    double a6 = 0.0, a12 = 0.0;
+    long long ap = 0;
+    for (int w = threadIdx.x; w < nw; w += kRedThreads) {
+        a6 += warp_acc[4 * w + 0];
+        a12 += warp_acc[4 * w + 1];
+        ap += warp_pairs[w];
+    }
+    r6[threadIdx.x] = a6; r12[threadIdx.x] = a12; rp[threadIdx.x] = ap;
+    __syncthreads();
+    for (int m = kRedThreads / 2; m > 0; m >>= 1) {
+        if (threadIdx.x < m) {
+            r6[threadIdx.x] += r6[threadIdx.x + m];
+            r12[threadIdx.x] += r12[threadIdx.x + m];
+            rp[threadIdx.x] += rp[threadIdx.x + m];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double s6 = r6[0], s12 = r12[0];
+        double scale = full ? 0.5 : 1.0;       // the full shell sees each pair twice
+        out[0] = scale * 4.0 * (s12 - s6);      // U = 4 sum (r^-12 - r^-6)
+        out[1] = scale * 24.0 * (2.0 * s12 - s6);  // W = sum r.F = 24 sum (2 r^-12 - r^-6)
+        long long p = full ? rp[0] / 2 : rp[0];
+        out[2] = (double)p;
+        *npairs = p;
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_final_kin(int nb, const double *__restrict__ part,
+                                                           double *__restrict__ out) {
+    __shared__ double r[kRedThreads];
+    double a = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kRedThreads) a += part[b];
+    r[threadIdx.x] = a;
+    __syncthreads();
+    for (int m = kRedThreads / 2; m > 0; m >>= 1) {
+        if (threadIdx.x < m) r[threadIdx.x] += r[threadIdx.x + m];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[3] = 0.5 * r[0];
+}
+
+cudaError_t launch_kick_drift(Ctx *c, double dt, cudaStream_t s) {
+    if (c->n == 0) return cudaSuccess;
+    k_kick_drift<<<c->num_sms * 8, 256, 0, s>>>((int)c->n, 0.5 * dt, dt, c->cur, c->fx, c->fy, c->fz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kick(Ctx *c, double dt, cudaStream_t s) {
+    if (c->n == 0) return cudaSuccess;
+    k_kick<<<c->num_sms * 8, 256, 0, s>>>((int)c->n, 0.5 * dt, c->cur, c->fx, c->fy, c->fz);
+    return cudaGetLastError();
+}
+
+int kinetic_blocks(const Ctx *c) { return c->num_sms * 2; }
+
+cudaError_t launch_kinetic(Ctx *c, cudaStream_t s) {
+    const int nb = kinetic_blocks(c);
+    double *part = c->d_kin_part;
+    k_kinetic<<<nb, 256, 0, s>>>((int)c->n, c->cur, part);
+    k_final_kin<<<1, kRedThreads, 0, s>>>(nb, part, c->d_result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_reduce(Ctx *c, cudaStream_t s, int full) {
+    k_final_pot<<<1, kRedThreads, 0, s>>>(force_grid_warps(c), c->d_warp_acc, c->d_warp_pairs, full,
+                                          c->d_result, c->d_npairs);
+    return cudaGetLastError();
+}
+
+}  // namespace lc

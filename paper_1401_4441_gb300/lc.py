@@ -1,0 +1,194 @@
+"""Thin ctypes binding of liblc.so (include/lc.h).
+
+Argument marshalling only: every step of the force sweep, binning and
+integration runs in the library's CUDA kernels.  There is no CPU fallback:
+if the compiled library is missing, loading raises.  PyTorch is used for
+device buffers and streams only (``torch.cuda.current_stream()``).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "liblc.so")
+
+SCHED = {"colour": 0, "atomic": 1, "fullshell": 2}
+PREC = {"fp64": 0, "mixed": 1}
+GET = {"cell_count": 0, "cell_start": 1, "perm": 2, "colour": 3, "forces": 4, "pos": 5, "vel": 6}
+STATUS = {0: "LC_OK", 1: "LC_ERR_INVALID_ARG", 2: "LC_ERR_BOX_TOO_SMALL", 3: "LC_ERR_CUDA",
+          4: "LC_ERR_OOM", 5: "LC_ERR_NONFINITE", 6: "LC_ERR_TIMEOUT", 7: "LC_ERR_STATE",
+          8: "LC_ERR_RACE", 9: "LC_ERR_TOO_LARGE"}
+
+_lib = None
+
+
+class LCError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        name = STATUS.get(code, str(code))
+        msg = _load().lc_status_str(code).decode() if _lib is not None else name
+        super().__init__(f"{where}: {name} ({msg})")
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"liblc.so not built ({LIB_PATH}); run paper_1401_4441_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, dp, ip, lp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), \
+        ctypes.POINTER(ctypes.c_int64)
+    ctx_pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "lc_create": ([dp, ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctx_pp], ctypes.c_int),
+        "lc_set_state": ([vp, vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
+        "lc_bin": ([vp, vp], ctypes.c_int),
+        "lc_forces": ([vp, ctypes.c_int, vp], ctypes.c_int),
+        "lc_verlet_step": ([vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, vp], ctypes.c_int),
+        "lc_energy_virial": ([vp, dp, dp, dp, lp, vp], ctypes.c_int),
+        "lc_get": ([vp, ctypes.c_int, vp, ctypes.c_int, vp], ctypes.c_int),
+        "lc_grid": ([vp, ip, ip, ip], ctypes.c_int),
+        "lc_schedule_check": ([vp, ctypes.c_int, lp, lp, vp], ctypes.c_int),
+        "lc_set_tile": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "lc_launch_counts": ([vp, ip, ip], ctypes.c_int),
+        "lc_destroy": ([vp], None),
+        "lc_status_str": ([ctypes.c_int], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def lib():
+    return _load()
+
+
+def _check(code, where):
+    if code != 0:
+        raise LCError(code, where)
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(0)
+
+
+def _ptr(a):
+    """(pointer, on_device) of a host numpy array or a CUDA torch tensor."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        return ctypes.c_void_p(a.ctypes.data), 0
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+class Box:
+    """One periodic box on the GPU (an lc_ctx)."""
+
+    def __init__(self, box, rc, n, precision="mixed"):
+        self._lib = _load()
+        self.n = int(n)
+        self.box = np.ascontiguousarray(np.broadcast_to(np.asarray(box, np.float64), (3,)))
+        self.rc = float(rc)
+        self.precision = precision
+        h = ctypes.c_void_p()
+        _check(self._lib.lc_create(self.box.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.rc,
+                                   self.n, PREC[precision], ctypes.byref(h)), "lc_create")
+        self._h = h
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.lc_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls -------------------------------------------------------------
+    def set_state(self, pos, vel=None, stream=None):
+        if isinstance(pos, np.ndarray):
+            pos = np.ascontiguousarray(pos, dtype=np.float64)
+            vel = None if vel is None else np.ascontiguousarray(vel, dtype=np.float64)
+        p, dev = _ptr(pos)
+        v, _ = _ptr(vel)
+        _check(self._lib.lc_set_state(self._h, p, v, None, dev, _stream(stream)), "lc_set_state")
+
+    def bin(self, stream=None):
+        _check(self._lib.lc_bin(self._h, _stream(stream)), "lc_bin")
+
+    def forces(self, schedule="colour", stream=None):
+        _check(self._lib.lc_forces(self._h, SCHED[schedule], _stream(stream)), "lc_forces")
+
+    def verlet(self, dt, nsteps, schedule="colour", stream=None):
+        _check(self._lib.lc_verlet_step(self._h, float(dt), int(nsteps), SCHED[schedule], _stream(stream)),
+               "lc_verlet_step")
+
+    def energy(self, stream=None):
+        """(U, K, W, npairs) of the current state."""
+        u, k, w = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        npairs = ctypes.c_int64()
+        _check(self._lib.lc_energy_virial(self._h, ctypes.byref(u), ctypes.byref(k), ctypes.byref(w),
+                                          ctypes.byref(npairs), _stream(stream)), "lc_energy_virial")
+        return u.value, k.value, w.value, npairs.value
+
+    def grid(self):
+        nc = (ctypes.c_int32 * 3)()
+        ncol, nph = ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.lc_grid(self._h, nc, ctypes.byref(ncol), ctypes.byref(nph)), "lc_grid")
+        return np.array(list(nc), np.int32), ncol.value, nph.value
+
+    def get(self, what, out=None, stream=None):
+        """Copy an array out; returns a numpy array unless `out` (host
+        numpy array or CUDA torch tensor of the right size) is given."""
+        nc, _, _ = self.grid()
+        ncell = int(nc.prod())
+        shapes = {"cell_count": ((ncell,), np.int32), "cell_start": ((ncell,), np.int32),
+                  "perm": ((self.n,), np.int32), "colour": ((ncell,), np.int8),
+                  "forces": ((self.n, 3), np.float64), "pos": ((self.n, 3), np.float64),
+                  "vel": ((self.n, 3), np.float64)}
+        shape, dtype = shapes[what]
+        if out is None:
+            out = np.empty(shape, dtype)
+        p, dev = _ptr(out)
+        _check(self._lib.lc_get(self._h, GET[what], p, dev, _stream(stream)), f"lc_get({what})")
+        return out
+
+    def schedule_check(self, schedule, stream=None):
+        conflicts, cover = ctypes.c_int64(), ctypes.c_int64()
+        code = self._lib.lc_schedule_check(self._h, SCHED[schedule], ctypes.byref(conflicts), ctypes.byref(cover),
+                                           _stream(stream))
+        if code not in (0, 8):
+            _check(code, "lc_schedule_check")
+        return conflicts.value, cover.value
+
+    def set_tile(self, ni=0, warps=0):
+        _check(self._lib.lc_set_tile(self._h, int(ni), int(warps)), "lc_set_tile")
+
+    def launch_counts(self):
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.lc_launch_counts(self._h, ctypes.byref(a), ctypes.byref(b)), "lc_launch_counts")
+        return a.value, b.value

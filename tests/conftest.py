@@ -17,3 +17,16 @@ def oracle_lib():
     import oracle
     oracle._load()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def lc():
+    """The CUDA library (built in-tree on first use) and its binding."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1401_4441_gb300 import build
+    build.build()
+    from paper_1401_4441_gb300 import lc as lcmod
+    lcmod.lib()
+    return lcmod

@@ -1,0 +1,51 @@
+"""The C-ABI library loads and exports every function include/*.h declares
+(no CUDA work: only host-side argument checks are called)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ ]*[\s\*]+(lc_[a-z0-9_]+)\s*\(", text, re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def so():
+    from paper_1401_4441_gb300 import build
+    return ctypes.CDLL(build.build())
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lc_create", "lc_bin", "lc_forces", "lc_verlet_step", "lc_energy_virial",
+                     "lc_set_state", "lc_get", "lc_destroy", "lc_status_str"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(so):
+    missing = [n for n in declared_functions() if not hasattr(so, n)]
+    assert not missing
+
+
+def test_host_side_argument_checks(so):
+    so.lc_status_str.restype = ctypes.c_char_p
+    assert so.lc_status_str(0) == b"ok"
+    assert b"3 cells" in so.lc_status_str(2)
+    box = (ctypes.c_double * 3)(10.0, 10.0, 7.4)
+    h = ctypes.c_void_p()
+    so.lc_create.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+    assert so.lc_create(box, 2.5, 10, 1, ctypes.byref(h)) == 2     # box too small, before any CUDA call
+    assert so.lc_create(box, -1.0, 10, 1, ctypes.byref(h)) == 1
+    assert so.lc_create(box, 2.5, -1, 1, ctypes.byref(h)) == 1
+    assert h.value is None

@@ -1,0 +1,262 @@
+"""GPU path (C ABI via the ctypes binding) against the FP64 oracle.
+
+Bit-exact: cell counts, cell starts, the slot -> ID permutation, colours and
+the number of pairs inside r_c.  Floating point: FP64 path within 1e-10 of
+the RMS force; mixed path within 1e-5 (max over particles of |dF| / RMS |F|),
+energy and virial within 1e-5 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_4441_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+RC = 2.5
+SCHEDS = ["colour", "atomic", "fullshell"]
+TOL = {"fp64": 1e-10, "mixed": 1e-5}
+
+
+def rel_force_err(f, fref):
+    rms = math.sqrt(float((fref ** 2).sum(1).mean()))
+    return float(np.sqrt(((f - fref) ** 2).sum(1)).max()) / rms, rms
+
+
+def make(lc, pos, box, prec, vel=None):
+    b = lc.Box(box, RC, pos.shape[0], prec)
+    b.set_state(pos, vel)
+    return b
+
+
+def check_bin(lc, pos, box):
+    ref = oracle.bin(pos[:, 0], pos[:, 1], pos[:, 2], box, RC)
+    with make(lc, pos, box, "mixed") as b:
+        b.bin()
+        assert np.array_equal(b.get("cell_count"), ref["count"])
+        assert np.array_equal(b.get("cell_start"), ref["start"])
+        assert np.array_equal(b.get("perm"), ref["perm"])
+        assert np.array_equal(b.get("colour"), ref["colour"])
+        nc, ncol, nph = b.grid()
+        assert np.array_equal(nc, ref["nc"]) and ncol == ref["ncolours"] and nph == 4 * ncol
+        p = b.get("pos")
+        for i in range(0, pos.shape[0], max(1, pos.shape[0] // 50)):
+            for d in range(3):
+                assert p[i, d] == oracle.wrap(pos[i, d], box[d])
+
+
+def test_binning_bit_exact_small(lc):
+    b = inputs.fcc_box(4000, 0.8442, 0.72, jitter=0.05)
+    check_bin(lc, b["pos"], b["box"])
+    b = inputs.fcc_box(4000, 0.8442, 0.72, jitter=0.0)
+    check_bin(lc, b["pos"], b["box"])
+
+
+def test_binning_bit_exact_uneven_and_outside(lc):
+    n = 3000
+    box = np.array([9.1, 7.6, 12.7])        # 3 x 3 x 5 cells: 27 colours... odd dims
+    pos = inputs.uniform(5, 0, 3 * n).reshape(n, 3) * box * 3.0 - box   # spans [-L, 2L)
+    check_bin(lc, pos, box)
+
+
+def test_binning_dense_cells(lc):
+    """Cells holding far more than a warp of particles (ragged, > 32 and > 512)."""
+    n = 2500
+    box = np.array([10.0, 10.0, 10.0])
+    u = inputs.uniform(6, 0, 3 * n).reshape(n, 3)
+    pos = np.where(np.arange(n)[:, None] < 1800, u * 2.4 + 0.05, u * box)
+    check_bin(lc, pos, box)
+
+
+def test_binning_bit_exact_1m(lc):
+    b = inputs.workload("liquid1m")
+    check_bin(lc, b["pos"], b["box"])
+
+
+def forces_case(lc, pos, box, prec, sched):
+    fref, U, W, npairs = oracle.lc_forces(pos[:, 0], pos[:, 1], pos[:, 2], box, RC)
+    with make(lc, pos, box, prec) as b:
+        b.forces(sched)
+        f = b.get("forces")
+        u, k, w, np_ = b.energy()
+    err, rms = rel_force_err(f, fref)
+    assert np_ == npairs
+    assert err <= TOL[prec], (prec, sched, err)
+    assert u == pytest.approx(U, rel=TOL[prec], abs=1e-12)
+    assert w == pytest.approx(W, rel=TOL[prec], abs=1e-12)
+    return err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_forces_4k_jittered(lc, prec, sched):
+    b = inputs.fcc_box(4000, 0.8442, 0.72, jitter=0.05)
+    forces_case(lc, b["pos"], b["box"], prec, sched)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_forces_liquid_like(lc, prec, sched):
+    """Strong jitter (RMS force 86, harsher than an equilibrium liquid at
+    T = 0.72): close pairs, uneven occupancy, many pairs near r_c."""
+    b = inputs.fcc_box(20000, 0.8442, 1.0, seed=3, jitter=0.12)
+    forces_case(lc, b["pos"], b["box"], prec, sched)
+
+
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_forces_overlap_stress(lc, sched):
+    """Overlapping particles (min distance 0.46 sigma, forces up to 1e6,
+    heavy-tailed): FP32 pair math keeps about 1e-6 of each particle's own
+    force, which is up to 5e-5 of the RMS force here.  The FP64 path still
+    meets 1e-10; the mixed path is held to 1e-4 of the RMS and the exact pair
+    set."""
+    b = inputs.fcc_box(20000, 0.8442, 1.0, seed=3, jitter=0.25)
+    pos, box = b["pos"], b["box"]
+    fref, U, W, npairs = oracle.lc_forces(pos[:, 0], pos[:, 1], pos[:, 2], box, RC)
+    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-4)):
+        with make(lc, pos, box, prec) as g:
+            g.forces(sched)
+            f = g.get("forces")
+            u, k, w, np_ = g.energy()
+        err, rms = rel_force_err(f, fref)
+        assert np_ == npairs
+        assert err <= tol, (prec, err)
+        assert u == pytest.approx(U, rel=tol)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_forces_odd_and_minimal_grids(lc, prec, sched):
+    for box in (np.array([7.6, 7.6, 7.6]), np.array([9.1, 7.6, 12.7]), np.array([10.2, 15.3, 7.9])):
+        n = int(0.7 * box.prod())
+        pos = inputs.uniform(9, 0, 3 * n).reshape(n, 3) * box
+        # keep the uniform random positions but drop near-overlaps
+        keep = np.ones(n, bool)
+        from scipy.spatial import cKDTree
+        pairs = cKDTree(np.mod(pos, box), boxsize=box).query_pairs(0.8, output_type="ndarray")
+        keep[np.unique(pairs[:, 1])] = False
+        forces_case(lc, pos[keep], box, prec, sched)
+
+
+def test_forces_dense_cells(lc):
+    """Particles crowded into few cells (> 32 and > NI per cell, j lists over
+    512 entries), all schedules agree with the oracle."""
+    n = 1500
+    box = np.array([10.0, 10.0, 10.0])
+    u = inputs.uniform(8, 0, 3 * n).reshape(n, 3)
+    pos = np.where(np.arange(n)[:, None] < 900, u * 4.9 + 0.05, u * box)
+    from scipy.spatial import cKDTree
+    pairs = cKDTree(np.mod(pos, box), boxsize=box).query_pairs(0.35, output_type="ndarray")
+    keep = np.ones(n, bool)
+    keep[np.unique(pairs[:, 1])] = False
+    pos = pos[keep]
+    for prec in ("fp64", "mixed"):
+        for sched in SCHEDS:
+            forces_case(lc, pos, box, prec, sched)
+
+
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_forces_1m_mixed(lc, sched):
+    b = inputs.workload("liquid1m")
+    err = forces_case(lc, b["pos"], b["box"], "mixed", sched)
+    print(f"1M {sched}: max |dF|/rms = {err:.3e}")
+
+
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_schedule_check(lc, sched):
+    for box in (np.array([16.8, 16.8, 16.8]), np.array([7.6, 7.6, 7.6]), np.array([12.7, 10.2, 17.6])):
+        with lc.Box(box, RC, 10, "mixed") as b:
+            conflicts, cover = b.schedule_check(sched)
+            assert conflicts == 0 and cover == 0
+
+
+def test_empty_and_single(lc):
+    box = np.array([8.0, 8.0, 8.0])
+    for n in (0, 1):
+        pos = np.full((n, 3), 1.0)
+        with make(lc, pos, box, "mixed") as b:
+            for s in SCHEDS:
+                b.forces(s)
+                u, k, w, np_ = b.energy()
+                assert (u, w, np_) == (0.0, 0.0, 0)
+                if n:
+                    assert np.all(b.get("forces") == 0.0)
+
+
+def test_errors(lc):
+    with pytest.raises(lc.LCError) as e:
+        lc.Box([7.4, 8.0, 8.0], RC, 10)
+    assert e.value.code == 2
+    box = np.array([8.0, 8.0, 8.0])
+    pos = np.full((5, 3), 1.0)
+    pos[3, 1] = np.nan
+    with make(lc, pos, box, "mixed") as b:
+        b.forces("atomic")
+        with pytest.raises(lc.LCError) as e:
+            b.energy()
+        assert e.value.code == 5
+    with lc.Box(box, RC, 5) as b:
+        with pytest.raises(lc.LCError) as e:
+            b.forces("colour")
+        assert e.value.code == 7
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_verlet_4k(lc, prec):
+    b = inputs.workload("fcc4k")
+    x, v, f, e = oracle.verlet(b["pos"], b["vel"], b["box"], RC, 0.005, 10)
+    with make(lc, b["pos"], b["box"], prec, b["vel"]) as g:
+        g.forces("colour")
+        u0, k0, w0, _ = g.energy()
+        assert u0 == pytest.approx(e[0, 0], rel=TOL[prec])
+        assert k0 == pytest.approx(e[0, 1], rel=1e-12)
+        g.verlet(0.005, 10, "colour")
+        u, k, w, np_ = g.energy()
+        p = g.get("pos")
+        vel = g.get("vel")
+    dx = p - x
+    dx -= b["box"] * np.rint(dx / b["box"])
+    tol = 1e-9 if prec == "fp64" else 1e-6
+    assert np.abs(dx).max() < tol
+    assert np.abs(vel - v).max() < tol * 10
+    assert u == pytest.approx(e[-1, 0], rel=tol)
+    assert k == pytest.approx(e[-1, 1], rel=tol)
+
+
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_verlet_schedules_agree(lc, sched):
+    """Odd step counts (graph of two steps + one direct step) and repeated
+    calls give the oracle's trajectory."""
+    b = inputs.fcc_box(4000, 0.8442, 0.72, jitter=0.05)
+    x, v, f, e = oracle.verlet(b["pos"], b["vel"], b["box"], RC, 0.005, 7)
+    with make(lc, b["pos"], b["box"], "fp64", b["vel"]) as g:
+        g.verlet(0.005, 3, sched)
+        g.verlet(0.005, 1, sched)
+        g.verlet(0.005, 3, sched)
+        p = g.get("pos")
+        u, k, w, _ = g.energy()
+    dx = p - x
+    dx -= b["box"] * np.rint(dx / b["box"])
+    assert np.abs(dx).max() < 1e-9
+    assert u == pytest.approx(e[-1, 0], rel=1e-9)
+
+
+def test_16m_sampled(lc):
+    """Full 16.7M-particle box, mixed colour schedule, against per-particle
+    oracle sums on a sample of particles, plus pair-count and Newton-3 checks."""
+    b = inputs.workload("fcc16m")
+    pos, box = b["pos"], b["box"]
+    with make(lc, pos, box, "mixed") as g:
+        g.forces("colour")
+        f = g.get("forces")
+        u, k, w, np_ = g.energy()
+    ids = np.linspace(0, pos.shape[0] - 1, 3000).astype(np.int64)
+    fref, nn = oracle.forces_sample(pos[:, 0], pos[:, 1], pos[:, 2], box, RC, ids)
+    scale = max(1e-3, math.sqrt(float((fref ** 2).sum(1).mean())))
+    assert np.abs(f[ids] - fref).max() <= 1e-5 * scale + 1e-9
+    assert np_ > 0
+    # Newton's third law: the net force per particle vanishes (lattice
+    # rounding is coherent across cells, so bound the mean, not sqrt(N))
+    assert np.abs(f.sum(0)).max() < 1e-6 * pos.shape[0]
