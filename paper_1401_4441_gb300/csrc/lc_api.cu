@@ -64,6 +64,10 @@ void make_grid(Grid *g, const double box[3], double rc) {
         g->h[d] = box[d] / (double)g->nc[d];
         g->inv[d] = (double)g->nc[d] / box[d];
         g->hf[d] = (float)g->h[d];
+        g->hl[d] = (float)(g->h[d] - (double)g->hf[d]);
+        g->invf[d] = (float)g->inv[d];
+        g->Lf_lo[d] = (float)(box[d] * (1.0 - 1.0e-6));
+        g->cmargin[d] = (float)(2.0e-6 * g->nc[d] + 1.0e-6);
         g->ncell *= g->nc[d];
     }
     float rc2f = (float)g->rc2;

@@ -27,13 +27,21 @@ __global__ void k_cellid(Grid g, int n, const double *__restrict__ x, const doub
                          const double *__restrict__ z, int *__restrict__ cell, int *__restrict__ rank,
                          int *__restrict__ count, int *__restrict__ err) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        double X = x[s], Y = y[s], Z = z[s];
+        const double X[3] = {x[s], y[s], z[s]};
+        int cc[3];
+        bool fast = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            Split sp;
+            fast = fast && split_f64(X[d], sp) && cell_coord_fast(sp, g.Lf_lo[d], g.invf[d], g.nc[d], g.cmargin[d], cc[d]);
+        }
         int c = 0;
-        if (isfinite(X) && isfinite(Y) && isfinite(Z)) {
-            int cx = cell_coord(wrap_coord(X, g.L[0]), g.inv[0], g.nc[0]);
-            int cy = cell_coord(wrap_coord(Y, g.L[1]), g.inv[1], g.nc[1]);
-            int cz = cell_coord(wrap_coord(Z, g.L[2]), g.inv[2], g.nc[2]);
-            c = cx + g.nc[0] * (cy + g.nc[1] * cz);
+        if (fast) {
+            c = cc[0] + g.nc[0] * (cc[1] + g.nc[1] * cc[2]);
+        } else if (isfinite(X[0]) && isfinite(X[1]) && isfinite(X[2])) {
+            // exact FP64 path: outside (0, L) or within the margin of a cell face
+            for (int d = 0; d < 3; ++d) cc[d] = cell_coord(wrap_coord(X[d], g.L[d]), g.inv[d], g.nc[d]);
+            c = cc[0] + g.nc[0] * (cc[1] + g.nc[1] * cc[2]);
         } else {
             atomicOr(err, kErrNonfinite);
         }
@@ -146,8 +154,6 @@ __global__ void k_cellsort(Grid g, int write_p4, const int *__restrict__ start, 
         cc[0] = c % g.nc[0];
         cc[1] = (c / g.nc[0]) % g.nc[1];
         cc[2] = c / (g.nc[0] * g.nc[1]);
-        double org[3];
-        for (int d = 0; d < 3; ++d) org[d] = __dmul_rn((double)cc[d] + 0.5, g.h[d]);
         for (int e0 = 0; e0 < cnt; e0 += 32) {
             const int e = e0 + lane;
             int my_src = 0, my_id = 0;
@@ -166,23 +172,43 @@ __global__ void k_cellsort(Grid g, int write_p4, const int *__restrict__ start, 
             }
             if (e < cnt) {
                 const int dst = base + r;
-                double X = wrap_coord(in.x[my_src], g.L[0]);
-                double Y = wrap_coord(in.y[my_src], g.L[1]);
-                double Z = wrap_coord(in.z[my_src], g.L[2]);
-                out.x[dst] = X; out.y[dst] = Y; out.z[dst] = Z;
+                double X[3] = {in.x[my_src], in.y[my_src], in.z[my_src]};
+                Split sp[3];
+                bool fast = true;
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    fast = fast && split_f64(X[d], sp[d]) && sp[d].hi > 0.0f && sp[d].hi < g.Lf_lo[d];
+                if (!fast) {
+                    // exact wrap (rare: the particle left the box or sits at 0)
+                    for (int d = 0; d < 3; ++d) {
+                        X[d] = wrap_coord(X[d], g.L[d]);
+                        if (!split_f64(X[d], sp[d])) sp[d].hi = sp[d].lo = 0.0f;
+                    }
+                }
+                out.x[dst] = X[0]; out.y[dst] = X[1]; out.z[dst] = X[2];
                 out.vx[dst] = in.vx[my_src]; out.vy[dst] = in.vy[my_src]; out.vz[dst] = in.vz[my_src];
                 out.id[dst] = my_id;
                 if (write_p4) {
-                    // FP32 offsets from the cell centre; the rounding residual of
-                    // each (|r| <= 2^-23 for |offset| < 4) is kept as a 10-bit
+                    // FP32 offset from the cell centre (c + 1/2) h, formed in
+                    // double-float arithmetic (TwoProduct / TwoSum) from the
+                    // hi + lo split of x; the rounding residual of each offset
+                    // (|r| <= 2^-23 for |offset| < 4) is kept as a 10-bit
                     // signed fraction of 2^-23 in the spare fourth word.
-                    double l[3] = {__dsub_rn(X, org[0]), __dsub_rn(Y, org[1]), __dsub_rn(Z, org[2])};
                     float hi[3];
                     unsigned w = 0;
+#pragma unroll
                     for (int d = 0; d < 3; ++d) {
-                        hi[d] = (float)l[d];
-                        double r = __dsub_rn(l[d], (double)hi[d]);
-                        int q = (int)rint(r * kLoScale);
+                        const float cf = (float)cc[d] + 0.5f;
+                        const float ph = cf * g.hf[d];
+                        const float pl = fmaf(cf, g.hf[d], -ph) + cf * g.hl[d];
+                        const float s = sp[d].hi - ph;                  // TwoSum(hi, -ph)
+                        const float bb = s - sp[d].hi;
+                        const float e2 = (sp[d].hi - (s - bb)) + (-ph - bb);
+                        const float rest = (sp[d].lo - pl) + e2;
+                        const float t = s + rest;
+                        const float res = rest - (t - s);
+                        hi[d] = t;
+                        int q = __float2int_rn(res * (float)kLoScale);
                         q = q > 511 ? 511 : (q < -511 ? -511 : q);
                         w |= (unsigned)(q + 512) << (10 * d);
                     }

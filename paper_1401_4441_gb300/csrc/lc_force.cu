@@ -56,6 +56,8 @@ struct ForceArgs {
     long long *warp_pairs;      // [W]
     int group, colour;          // colour phase
     int ntasks;
+    float sh[27][3];            // o * h rounded to FP32, offset index (ox+1) + 3 (oy+1) + 9 (oz+1)
+    float sl[27][3];            // o * h - sh, rounded to FP32
 };
 
 // ---------------------------------------------------------------- tasks ----
@@ -125,14 +127,32 @@ __device__ __forceinline__ TaskCells make_task(const Grid &g, int group, int col
 // ----------------------------------------------------- per-warp scratch ----
 template <typename T>
 struct alignas(16) WarpSmem {
-    T ix[32], iy[32], iz[32];   // centre-cell particles of the current i chunk
+    float4 i4[32];              // mixed: centre-cell particle (x, y, z, slot bits)
+    float corr[32][3];          // mixed: i-side forces of near-r_c pairs
+    T ix[32], iy[32], iz[32];   // FP64: centre-cell particles
     int islot[32];
     int jl[kJCap];              // slot | (neighbour index << 26)
-    int nb_start[kMaxNb], nb_count[kMaxNb], nb_cell[kMaxNb];
+    int nb_start[kMaxNb], nb_count[kMaxNb];
+    int nb_img[kMaxNb];         // periodic image s_d in {-1,0,1} as (s+1) in 2-bit fields
     float nb_sh[kMaxNb][3];     // o * h rounded to FP32 (mixed)
     float nb_sl[kMaxNb][3];     // o * h - nb_sh, rounded to FP32
-    double nb_sL[kMaxNb][3];    // periodic image s * L in FP64
 };
+
+__device__ __forceinline__ double image_shift(const Grid &g, int img, int d) {
+    const int s = ((img >> (2 * d)) & 3) - 1;
+    return s == 0 ? 0.0 : (s > 0 ? g.L[d] : -g.L[d]);
+}
+
+// Shared-memory vector load kept inside the loop (volatile): the centre-cell
+// particles are re-read per candidate instead of being pinned in registers,
+// which keeps the kernel at two resident blocks per SM.
+__device__ __forceinline__ float4 lds4(const float4 *p) {
+    float4 v;
+    const unsigned addr = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+    return v;
+}
 
 // Reciprocal: hardware approximation refined by one Newton-Raphson step
 // y <- y (2 - r y), written as two FMAs.
@@ -144,7 +164,9 @@ __device__ __forceinline__ float rcp_nr(float r) {
 }
 
 // Butterfly reduce-scatter of v[NI] over the 32 lanes of a warp.  On return
-// lane l holds in v[0] the warp-wide sum of element (l / (32 / NI)) % NI.
+// lane l holds in v[0] the warp-wide sum of element e(l), where fold k (lane
+// bit 4 - k) picks bit log2(NI) - 1 - k of e; lanes that differ only in the
+// low log2(32 / NI) bits hold the same element.
 template <typename T, int NI>
 __device__ __forceinline__ void reduce_scatter(T (&v)[NI], int lane) {
 #pragma unroll
@@ -157,9 +179,17 @@ __device__ __forceinline__ void reduce_scatter(T (&v)[NI], int lane) {
             v[k] = keep + __shfl_xor_sync(kFull, send, m);
         }
     }
-    // remaining lanes above the NI split hold partial sums of the same element
 #pragma unroll
     for (int m = 16 / NI; m >= 1; m >>= 1) v[0] += __shfl_xor_sync(kFull, v[0], m);
+}
+
+template <int NI>
+__device__ __forceinline__ int scattered_element(int lane) {
+    int bits = 0;
+    for (int n = NI; n > 1; n >>= 1) ++bits;
+    int e = 0;
+    for (int k = 0; k < bits; ++k) e |= ((lane >> (4 - k)) & 1) << (bits - 1 - k);
+    return e;
 }
 
 // Kahan-compensated accumulation of v into (s, c): true sum ~ s - c.
@@ -170,15 +200,22 @@ __device__ __forceinline__ void kahan_add(float2 &acc, float v) {
     acc.x = t;
 }
 
-template <int MODE, bool MIXED>
-__device__ __forceinline__ void write_force(const ForceArgs &a, int slot, double vx, double vy, double vz) {
-    if (MODE == kAtomic) {
-        atomicAdd(a.fx + slot, vx);
-        atomicAdd(a.fy + slot, vy);
-        atomicAdd(a.fz + slot, vz);
-    } else if (MODE == kFullShell) {
-        a.fx[slot] = vx; a.fy[slot] = vy; a.fz[slot] = vz;
-    } else if (MIXED) {
+template <typename T>
+__device__ __forceinline__ double to_f64(T v) {
+    if constexpr (std::is_same<T, float>::value) return f32_to_f64_bits(v);
+    else return v;
+}
+
+// One task's partial force on one particle enters its accumulator.
+template <int MODE, bool MIXED, typename T>
+__device__ __forceinline__ void write_force(const ForceArgs &a, int slot, T vx, T vy, T vz) {
+    if constexpr (MODE == kAtomic) {
+        atomicAdd(a.fx + slot, to_f64(vx));
+        atomicAdd(a.fy + slot, to_f64(vy));
+        atomicAdd(a.fz + slot, to_f64(vz));
+    } else if constexpr (MODE == kFullShell) {
+        a.fx[slot] = to_f64(vx); a.fy[slot] = to_f64(vy); a.fz[slot] = to_f64(vz);
+    } else if constexpr (MIXED) {
         float2 kx = a.kx[slot], ky = a.ky[slot], kz = a.kz[slot];
         kahan_add(kx, (float)vx); kahan_add(ky, (float)vy); kahan_add(kz, (float)vz);
         a.kx[slot] = kx; a.ky[slot] = ky; a.kz[slot] = kz;
@@ -204,216 +241,324 @@ struct LaneEnergy {
     long long pairs;
 };
 
-template <bool MIXED, int NI, int MODE>
-__device__ void run_task(const ForceArgs &a, WarpSmem<typename std::conditional<MIXED, float, double>::type> &sm,
-                         const TaskCells &tc, int lane, LaneEnergy &le) {
-    using T = typename std::conditional<MIXED, float, double>::type;
-    constexpr bool N3 = (MODE != kFullShell);
-    const Grid &g = a.g;
+// A neighbour slot as loaded for one lane (prefetched one chunk ahead).
+struct JLoad {
+    int w;            // slot | neighbour index << 26, or -1 past the list
+    float4 p;         // mixed: packed FP32 offsets + residuals
+    double x, y, z;   // FP64 path
+};
 
-    // neighbour table: lane k fills entry k
+template <bool MIXED>
+__device__ __forceinline__ JLoad load_j(const ForceArgs &a, const int *jl, int e, int nj) {
+    JLoad r;
+    r.w = -1;
+    if (e < nj) {
+        r.w = jl[e];
+        const int sj = r.w & ((1 << 26) - 1);
+        if constexpr (MIXED) {
+            r.p = a.p4[sj];
+        } else {
+            r.x = a.x[sj]; r.y = a.y[sj]; r.z = a.z[sj];
+        }
+    }
+    return r;
+}
+
+// Neighbour cells of a task: start, count, FP32 shift and periodic image per
+// entry, filled by lanes 0 .. nnb-1.
+template <bool MIXED, int MODE>
+__device__ __forceinline__ void setup_neighbours(const ForceArgs &a, WarpSmem<typename std::conditional<MIXED, float, double>::type> &sm,
+                                                 const TaskCells &tc, int lane) {
+    const Grid &g = a.g;
+    // neighbour table: lane k fills entry k (no FP64: shifts come from the
+    // per-offset tables, the periodic image is kept as a code)
     if (lane < tc.nnb) {
         int o[3];
         task_offset<MODE>(a.group, lane, tc.self, o);
         int c[3];
-        double sL[3];
+        int img = 0;
         for (int d = 0; d < 3; ++d) {
             c[d] = tc.cA[d] + o[d];
-            sL[d] = 0.0;
-            if (c[d] >= g.nc[d]) { c[d] -= g.nc[d]; sL[d] = g.L[d]; }
-            else if (c[d] < 0) { c[d] += g.nc[d]; sL[d] = -g.L[d]; }
-            const double S = (double)o[d] * g.h[d];
-            const float Sh = (float)S;
-            sm.nb_sh[lane][d] = Sh;
-            sm.nb_sl[lane][d] = (float)(S - (double)Sh);
-            sm.nb_sL[lane][d] = sL[d];
+            int sgn = 0;
+            if (c[d] >= g.nc[d]) { c[d] -= g.nc[d]; sgn = 1; }
+            else if (c[d] < 0) { c[d] += g.nc[d]; sgn = -1; }
+            img |= (sgn + 1) << (2 * d);
         }
-        int B = c[0] + g.nc[0] * (c[1] + g.nc[1] * c[2]);
-        sm.nb_cell[lane] = B;
+        const int oi = (o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1);
+        for (int d = 0; d < 3; ++d) {
+            sm.nb_sh[lane][d] = a.sh[oi][d];
+            sm.nb_sl[lane][d] = a.sl[oi][d];
+        }
+        sm.nb_img[lane] = img;
+        const int B = c[0] + g.nc[0] * (c[1] + g.nc[1] * c[2]);
         sm.nb_start[lane] = a.start[B];
         sm.nb_count[lane] = a.count[B];
     }
     __syncwarp();
+}
+
+// Next batch of neighbour slots (slot | entry << 26) into sm.jl; returns
+// how many were listed.  (b, kin) is the walk position over the entries.
+template <typename S>
+__device__ __forceinline__ int fill_batch(S &sm, int nnb, int &b, int &kin, int lane) {
+    int nj = 0;
+    while (b < nnb && nj < kJCap) {
+        const int cnt = sm.nb_count[b] - kin;
+        const int take = min(cnt, kJCap - nj);
+        const int st = sm.nb_start[b] + kin;
+        for (int k = lane; k < take; k += kWarp) sm.jl[nj + k] = (st + k) | (b << 26);
+        nj += take;
+        kin += take;
+        if (kin >= sm.nb_count[b]) { ++b; kin = 0; }
+    }
+    __syncwarp();
+    return nj;
+}
+
+// Reduce-scatter the i chunk's per-lane partials and let the owner lanes
+// write them (plus the near-r_c corrections of the mixed path).
+template <bool MIXED, int NI, int MODE, typename T, typename S>
+__device__ __forceinline__ void write_i_chunk(const ForceArgs &a, S &sm, T (&ax)[NI], T (&ay)[NI], T (&az)[NI],
+                                              int a0, int i0, int na, int lane) {
+    reduce_scatter<T, NI>(ax, lane);
+    reduce_scatter<T, NI>(ay, lane);
+    reduce_scatter<T, NI>(az, lane);
+    __syncwarp();   // order the j-side writes to A before the i-side ones
+    const int elem = scattered_element<NI>(lane);
+    if ((lane & ((32 / NI) - 1)) == 0) {
+        const int ii = i0 + elem;
+        if (ii < na) {
+            if constexpr (MIXED) {
+                ax[0] += sm.corr[elem][0]; ay[0] += sm.corr[elem][1]; az[0] += sm.corr[elem][2];
+            }
+            write_force<MODE, MIXED, T>(a, a0 + ii, ax[0], ay[0], az[0]);
+        }
+    }
+    __syncwarp();
+}
+
+// Mixed precision: FP32 pair arithmetic, two centre-cell particles per
+// packed f32x2 operation (the lane's j is the same for both).
+template <int NI, int MODE>
+__device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const TaskCells &tc, int lane, LaneEnergy &le) {
+    constexpr bool N3 = (MODE != kFullShell);
+    const Grid &g = a.g;
+    setup_neighbours<true, MODE>(a, sm, tc, lane);
     const int a0 = a.start[tc.A];
     const int na = a.count[tc.A];
-    const T far_i = (T)1.0e15, far_j = (T)-1.0e15;
     const float rc2lo = g.rc2f_lo, rc2hi = g.rc2f_hi;
-    const float rc2mid = 0.5f * (rc2lo + rc2hi), band = 0.5f * (rc2hi - rc2lo);
-    const T rc2 = MIXED ? (T)0 : (T)g.rc2;
+    const float2 one2 = make_float2(1.0f, 1.0f);
+    const float2 c48 = make_float2(48.0f, 48.0f), cm24 = make_float2(-24.0f, -24.0f);
 
     for (int i0 = 0; i0 < na; i0 += NI) {
-        // stage the i chunk
-        if (lane < NI) {
-            int ii = i0 + lane;
-            if (ii < na) {
-                int s = a0 + ii;
-                if (MIXED) {
-                    float4 p = a.p4[s];
-                    sm.ix[lane] = (T)p.x; sm.iy[lane] = (T)p.y; sm.iz[lane] = (T)p.z;
-                } else {
-                    sm.ix[lane] = (T)a.x[s]; sm.iy[lane] = (T)a.y[s]; sm.iz[lane] = (T)a.z[s];
-                }
-                sm.islot[lane] = s;
-            } else {
-                sm.ix[lane] = far_i; sm.iy[lane] = far_i; sm.iz[lane] = far_i;
-                sm.islot[lane] = 0x7fffffff;
-            }
+        if (lane < NI) {   // stage the i chunk (far-away sentinels past the end)
+            const int ii = i0 + lane;
+            float4 p = make_float4(1.0e15f, 1.0e15f, 1.0e15f, 0.f);
+            if (ii < na) p = a.p4[a0 + ii];
+            p.w = __int_as_float(ii < na ? a0 + ii : 0x7fffffff);
+            sm.i4[lane] = p;
+            sm.corr[lane][0] = sm.corr[lane][1] = sm.corr[lane][2] = 0.f;
         }
-        T ax[NI], ay[NI], az[NI];
+        float2 ax2[NI / 2], ay2[NI / 2], az2[NI / 2];
 #pragma unroll
-        for (int k = 0; k < NI; ++k) { ax[k] = ay[k] = az[k] = (T)0; }
-        T e6 = 0, e12 = 0;
+        for (int k = 0; k < NI / 2; ++k) ax2[k] = ay2[k] = az2[k] = make_float2(0.f, 0.f);
+        float2 e6 = make_float2(0.f, 0.f), e12 = make_float2(0.f, 0.f);
         int npair = 0;
         __syncwarp();
 
-        // walk the neighbour cells in batches of at most kJCap slots
         int b = 0, kin = 0;
         while (b < tc.nnb) {
-            int nj = 0;
-            while (b < tc.nnb && nj < kJCap) {
-                int cnt = sm.nb_count[b] - kin;
-                int take = min(cnt, kJCap - nj);
-                int st = sm.nb_start[b] + kin;
-                for (int k = lane; k < take; k += kWarp) sm.jl[nj + k] = (st + k) | (b << 26);
-                nj += take;
-                kin += take;
-                if (kin >= sm.nb_count[b]) { ++b; kin = 0; }
-            }
-            __syncwarp();
+            const int nj = fill_batch(sm, tc.nnb, b, kin, lane);
+            JLoad nxt = load_j<true>(a, sm.jl, lane, nj);
             for (int jc = 0; jc < nj; jc += kWarp) {
-                const int e = jc + lane;
-                const bool valid = e < nj;
-                int sj = 0x7fffffff, nb = 0;
-                T pjx = far_j, pjy = far_j, pjz = far_j;
-                // mixed: the j position in the centre cell's frame as an
-                // unevaluated sum hi + lo (the shift o*h added by Fast2Sum,
-                // |o*h| >= |x_j| whenever o != 0, plus the stored residual)
-                float ljx = 0.f, ljy = 0.f, ljz = 0.f;
+                const JLoad cur = nxt;
+                nxt = load_j<true>(a, sm.jl, jc + kWarp + lane, nj);   // prefetch
+                const bool valid = cur.w >= 0;
+                const int sj = valid ? (cur.w & ((1 << 26) - 1)) : 0x7fffffff;
+                const int nb = valid ? (cur.w >> 26) : 0;
+                const bool is_self = valid && tc.self && nb == 0;
+                const int jlim = (N3 && is_self) ? sj : 0x7fffffff;   // Newton-3 intra: slot_i < slot_j
+                const int jexcl = (!N3 && is_self) ? sj : -1;         // full shell: skip i == j
+                // the j position in the centre cell's frame as hi + lo: the
+                // shift o*h added by Fast2Sum (|o*h| >= |x_j| when o != 0)
+                // plus the stored rounding residual
+                float pj[3] = {-1.0e15f, -1.0e15f, -1.0e15f}, lj[3] = {0.f, 0.f, 0.f};
                 if (valid) {
-                    int w = sm.jl[e];
-                    sj = w & ((1 << 26) - 1);
-                    nb = w >> 26;
-                    if (MIXED) {
-                        const float4 p = a.p4[sj];
-                        const unsigned q = __float_as_uint(p.w);
-                        const float pin[3] = {p.x, p.y, p.z};
-                        float hi[3], lo[3];
+                    const unsigned q = __float_as_uint(cur.p.w);
+                    const float pin[3] = {cur.p.x, cur.p.y, cur.p.z};
 #pragma unroll
-                        for (int d = 0; d < 3; ++d) {
-                            const float Sh = sm.nb_sh[nb][d];
-                            const float s = Sh + pin[d];
-                            const float err = pin[d] - (s - Sh);
-                            const float res = (float)((int)((q >> (10 * d)) & 1023u) - 512) * kLoUnit;
-                            hi[d] = s;
-                            lo[d] = (err + res) + sm.nb_sl[nb][d];
-                        }
-                        pjx = hi[0]; pjy = hi[1]; pjz = hi[2];
-                        ljx = lo[0]; ljy = lo[1]; ljz = lo[2];
-                    } else {
-                        pjx = (T)a.x[sj]; pjy = (T)a.y[sj]; pjz = (T)a.z[sj];
+                    for (int d = 0; d < 3; ++d) {
+                        const float Sh = sm.nb_sh[nb][d];
+                        const float sum = Sh + pin[d];
+                        const float err = pin[d] - (sum - Sh);
+                        const float res = (float)((int)((q >> (10 * d)) & 1023u) - 512) * kLoUnit;
+                        pj[d] = sum;
+                        lj[d] = (err + res) + sm.nb_sl[nb][d];
                     }
                 }
+                const float2 npx = make_float2(-pj[0], -pj[0]), npy = make_float2(-pj[1], -pj[1]),
+                             npz = make_float2(-pj[2], -pj[2]);
+                const float2 nlx = make_float2(-lj[0], -lj[0]), nly = make_float2(-lj[1], -lj[1]),
+                             nlz = make_float2(-lj[2], -lj[2]);
+                float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;   // sum of f d over the i's (j gets -g)
+                bool amb = false;
+#pragma unroll
+                for (int k = 0; k < NI; k += 2) {
+                    const float4 pa = lds4(&sm.i4[k]);
+                    const float4 pb = lds4(&sm.i4[k + 1]);
+                    const int sa = __float_as_int(pa.w), sb = __float_as_int(pb.w);
+                    const bool oka = N3 ? (sa < jlim) : (sa != jexcl);
+                    const bool okb = N3 ? (sb < jlim) : (sb != jexcl);
+                    const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(pa.x, pb.x), npx), nlx);
+                    const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(pa.y, pb.y), npy), nly);
+                    const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(pa.z, pb.z), npz), nlz);
+                    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                    const bool neara = oka && (r2.x < rc2hi), nearb = okb && (r2.y < rc2hi);
+                    const bool hita = neara && (r2.x < rc2lo), hitb = nearb && (r2.y < rc2lo);
+                    amb |= (neara && !hita) || (nearb && !hitb);
+                    float2 y;
+                    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y.x) : "f"(r2.x));
+                    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y.y) : "f"(r2.y));
+                    const float2 e = __ffma2_rn(make_float2(-r2.x, -r2.y), y, one2);   // Newton step
+                    y = __ffma2_rn(y, e, y);
+                    y.x = hita ? y.x : 0.0f;   // masks misses and r2 = 0 (i == j)
+                    y.y = hitb ? y.y : 0.0f;
+                    const float2 s6 = __fmul2_rn(__fmul2_rn(y, y), y);
+                    const float2 f = __fmul2_rn(__fmul2_rn(s6, y), __ffma2_rn(s6, c48, cm24));
+                    ax2[k / 2] = __ffma2_rn(f, dx, ax2[k / 2]);
+                    ay2[k / 2] = __ffma2_rn(f, dy, ay2[k / 2]);
+                    az2[k / 2] = __ffma2_rn(f, dz, az2[k / 2]);
+                    if (N3) {
+                        gx = __ffma2_rn(f, dx, gx);
+                        gy = __ffma2_rn(f, dy, gy);
+                        gz = __ffma2_rn(f, dz, gz);
+                    }
+                    e6 = __fadd2_rn(e6, s6);
+                    e12 = __ffma2_rn(s6, s6, e12);
+                    npair += (hita ? 1 : 0) + (hitb ? 1 : 0);
+                }
+                float fjx = -(gx.x + gx.y), fjy = -(gy.x + gy.y), fjz = -(gz.x + gz.y);
+                if (__any_sync(kFull, amb)) {
+                    // rare: candidates within the band around r_c^2 are decided
+                    // with the FP64 definition; the ones inside are added here
+                    // (i side through the warp's shared correction slots)
+                    double sL[3];
+                    for (int d = 0; d < 3; ++d) sL[d] = image_shift(g, sm.nb_img[nb], d);
+#pragma unroll 1
+                    for (int k = 0; k < NI; ++k) {
+                        const float4 pi = lds4(&sm.i4[k]);
+                        const int si = __float_as_int(pi.w);
+                        const bool ok = N3 ? (si < jlim) : (si != jexcl);
+                        const float dx = (pi.x + npx.x) + nlx.x;
+                        const float dy = (pi.y + npy.x) + nly.x;
+                        const float dz = (pi.z + npz.x) + nlz.x;
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        if (valid && ok && r2 < rc2hi && !(r2 < rc2lo) && exact_inside(a, si, sj, sL)) {
+                            const float inv = rcp_nr(r2);
+                            const float s6 = inv * inv * inv;
+                            const float f = (s6 * inv) * fmaf(48.0f, s6, -24.0f);
+                            atomicAdd(&sm.corr[k][0], f * dx);
+                            atomicAdd(&sm.corr[k][1], f * dy);
+                            atomicAdd(&sm.corr[k][2], f * dz);
+                            fjx = fmaf(-f, dx, fjx); fjy = fmaf(-f, dy, fjy); fjz = fmaf(-f, dz, fjz);
+                            e6.x += s6;
+                            e12.x = fmaf(s6, s6, e12.x);
+                            npair += 1;
+                        }
+                    }
+                }
+                if (N3 && valid) write_force<MODE, true, float>(a, sj, fjx, fjy, fjz);
+            }
+            __syncwarp();
+        }
+        float ax[NI], ay[NI], az[NI];
+#pragma unroll
+        for (int k = 0; k < NI / 2; ++k) {
+            ax[2 * k] = ax2[k].x; ax[2 * k + 1] = ax2[k].y;
+            ay[2 * k] = ay2[k].x; ay[2 * k + 1] = ay2[k].y;
+            az[2 * k] = az2[k].x; az[2 * k + 1] = az2[k].y;
+        }
+        write_i_chunk<true, NI, MODE>(a, sm, ax, ay, az, a0, i0, na, lane);
+        kahan_add(le.s6, e6.x + e6.y);
+        kahan_add(le.s12, e12.x + e12.y);
+        le.pairs += npair;
+    }
+}
+
+// FP64: the definition's arithmetic in double precision throughout.
+template <int NI, int MODE>
+__device__ void run_task_fp64(const ForceArgs &a, WarpSmem<double> &sm, const TaskCells &tc, int lane, LaneEnergy &le) {
+    constexpr bool N3 = (MODE != kFullShell);
+    const Grid &g = a.g;
+    setup_neighbours<false, MODE>(a, sm, tc, lane);
+    const int a0 = a.start[tc.A];
+    const int na = a.count[tc.A];
+    const double rc2 = g.rc2;
+    for (int i0 = 0; i0 < na; i0 += NI) {
+        if (lane < NI) {
+            const int ii = i0 + lane;
+            const bool in = ii < na;
+            const int s = in ? a0 + ii : 0x7fffffff;
+            sm.ix[lane] = in ? a.x[s] : 1.0e15;
+            sm.iy[lane] = in ? a.y[s] : 1.0e15;
+            sm.iz[lane] = in ? a.z[s] : 1.0e15;
+            sm.islot[lane] = s;
+        }
+        double ax[NI], ay[NI], az[NI];
+#pragma unroll
+        for (int k = 0; k < NI; ++k) ax[k] = ay[k] = az[k] = 0.0;
+        double e6 = 0.0, e12 = 0.0;
+        int npair = 0;
+        __syncwarp();
+        int b = 0, kin = 0;
+        while (b < tc.nnb) {
+            const int nj = fill_batch(sm, tc.nnb, b, kin, lane);
+            JLoad nxt = load_j<false>(a, sm.jl, lane, nj);
+            for (int jc = 0; jc < nj; jc += kWarp) {
+                const JLoad cur = nxt;
+                nxt = load_j<false>(a, sm.jl, jc + kWarp + lane, nj);
+                const bool valid = cur.w >= 0;
+                const int sj = valid ? (cur.w & ((1 << 26) - 1)) : 0x7fffffff;
+                const int nb = valid ? (cur.w >> 26) : 0;
                 const bool is_self = valid && tc.self && nb == 0;
-                // Newton-3 intra pairs need slot_i < slot_j; full shell skips i == j
                 const int jlim = (N3 && is_self) ? sj : 0x7fffffff;
                 const int jexcl = (!N3 && is_self) ? sj : -1;
-                T sLx = 0, sLy = 0, sLz = 0;
-                if (!MIXED) { sLx = (T)sm.nb_sL[nb][0]; sLy = (T)sm.nb_sL[nb][1]; sLz = (T)sm.nb_sL[nb][2]; }
-                T fjx = 0, fjy = 0, fjz = 0;
-                bool amb = false;
+                const double pjx = valid ? cur.x : -1.0e15, pjy = valid ? cur.y : -1.0e15,
+                             pjz = valid ? cur.z : -1.0e15;
+                const int img = sm.nb_img[nb];
+                const double sLx = image_shift(g, img, 0), sLy = image_shift(g, img, 1), sLz = image_shift(g, img, 2);
+                double fjx = 0.0, fjy = 0.0, fjz = 0.0;
 #pragma unroll
                 for (int k = 0; k < NI; ++k) {
                     const int si = sm.islot[k];
                     const bool ok = N3 ? (si < jlim) : (si != jexcl);
-                    T dx, dy, dz, r2;
-                    if (MIXED) {
-                        dx = (sm.ix[k] - pjx) - (T)ljx;
-                        dy = (sm.iy[k] - pjy) - (T)ljy;
-                        dz = (sm.iz[k] - pjz) - (T)ljz;
-                        r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    } else {
-                        dx = __dsub_rn(__dsub_rn(sm.ix[k], pjx), sLx);
-                        dy = __dsub_rn(__dsub_rn(sm.iy[k], pjy), sLy);
-                        dz = __dsub_rn(__dsub_rn(sm.iz[k], pjz), sLz);
-                        r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-                    }
-                    bool hit;
-                    T inv;
-                    if (MIXED) {
-                        hit = ok && ((float)r2 < rc2lo);
-                        amb |= ok && (fabsf((float)r2 - rc2mid) < band);
-                        inv = (T)rcp_nr((float)r2);
-                        inv = hit ? inv : (T)0;   // masks r2 = 0 (i == j) as well
-                    } else {
-                        hit = ok && (r2 < rc2);
-                        inv = hit ? (T)1.0 / r2 : (T)0;
-                    }
-                    const T s6 = inv * inv * inv;
-                    const T f = (s6 * inv) * ((T)48 * s6 - (T)24);
+                    const double dx = __dsub_rn(__dsub_rn(sm.ix[k], pjx), sLx);
+                    const double dy = __dsub_rn(__dsub_rn(sm.iy[k], pjy), sLy);
+                    const double dz = __dsub_rn(__dsub_rn(sm.iz[k], pjz), sLz);
+                    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+                    const bool hit = ok && (r2 < rc2);
+                    const double inv = hit ? 1.0 / r2 : 0.0;
+                    const double s6 = inv * inv * inv;
+                    const double f = (s6 * inv) * (48.0 * s6 - 24.0);
                     ax[k] += f * dx; ay[k] += f * dy; az[k] += f * dz;
                     if (N3) { fjx -= f * dx; fjy -= f * dy; fjz -= f * dz; }
                     e6 += s6;
                     e12 += s6 * s6;
                     npair += hit ? 1 : 0;
                 }
-                if (MIXED && __any_sync(kFull, amb)) {
-                    // candidates near r_c: decide with the FP64 definition
-                    double sL[3] = {sm.nb_sL[nb][0], sm.nb_sL[nb][1], sm.nb_sL[nb][2]};
-#pragma unroll
-                    for (int k = 0; k < NI; ++k) {
-                        const int si = sm.islot[k];
-                        const bool ok = N3 ? (si < jlim) : (si != jexcl);
-                        float dx = ((float)sm.ix[k] - (float)pjx) - ljx;
-                        float dy = ((float)sm.iy[k] - (float)pjy) - ljy;
-                        float dz = ((float)sm.iz[k] - (float)pjz) - ljz;
-                        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        if (valid && ok && fabsf(r2 - rc2mid) < band && exact_inside(a, si, sj, sL)) {
-                            float inv = rcp_nr(r2);
-                            float s6 = inv * inv * inv;
-                            float f = (s6 * inv) * (48.0f * s6 - 24.0f);
-                            ax[k] += (T)(f * dx); ay[k] += (T)(f * dy); az[k] += (T)(f * dz);
-                            if (N3) { fjx -= (T)(f * dx); fjy -= (T)(f * dy); fjz -= (T)(f * dz); }
-                            e6 += (T)s6;
-                            e12 += (T)(s6 * s6);
-                            npair += 1;
-                        }
-                    }
-                }
-                if (N3 && valid) write_force<MODE, MIXED>(a, sj, (double)fjx, (double)fjy, (double)fjz);
+                if (N3 && valid) write_force<MODE, false, double>(a, sj, fjx, fjy, fjz);
             }
             __syncwarp();
         }
-        // the i chunk's forces: reduce-scatter over lanes, owners write
-        reduce_scatter<T, NI>(ax, lane);
-        reduce_scatter<T, NI>(ay, lane);
-        reduce_scatter<T, NI>(az, lane);
-        __syncwarp();   // order the j-side writes to A before the i-side ones
-        // element held by this lane after the butterfly: bit (4 - k) of the
-        // lane selects bit (log2 NI - 1 - k) of the element index
-        int bits = 0;
-        for (int n = NI; n > 1; n >>= 1) ++bits;
-        int elem = 0;
-        for (int k = 0; k < bits; ++k) elem |= ((lane >> (4 - k)) & 1) << (bits - 1 - k);
-        const int lowmask = (32 / NI) - 1;
-        if ((lane & lowmask) == 0) {
-            const int ii = i0 + elem;
-            if (ii < na) write_force<MODE, MIXED>(a, a0 + ii, (double)ax[0], (double)ay[0], (double)az[0]);
-        }
-        // energies of this chunk
-        if (MIXED) {
-            kahan_add(le.s6, (float)e6);
-            kahan_add(le.s12, (float)e12);
-        } else {
-            le.d6 += (double)e6;
-            le.d12 += (double)e12;
-        }
+        write_i_chunk<false, NI, MODE>(a, sm, ax, ay, az, a0, i0, na, lane);
+        le.d6 += e6;
+        le.d12 += e12;
         le.pairs += npair;
-        __syncwarp();
     }
 }
 
 template <bool MIXED, int NI, int MODE>
-__global__ void __launch_bounds__(256) k_force(ForceArgs a) {
+__global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
     using T = typename std::conditional<MIXED, float, double>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -428,11 +573,12 @@ __global__ void __launch_bounds__(256) k_force(ForceArgs a) {
     le.pairs = 0;
     for (int t = w; t < a.ntasks; t += W) {
         TaskCells tc = make_task<MODE>(a.g, a.group, a.colour, t);
-        run_task<MIXED, NI, MODE>(a, sm, tc, lane, le);
+        if constexpr (MIXED) run_task_mixed<NI, MODE>(a, sm, tc, lane, le);
+        else run_task_fp64<NI, MODE>(a, sm, tc, lane, le);
     }
     // warp reduction of the energy partials in FP64, fixed order
-    double s6 = MIXED ? ((double)le.s6.x - (double)le.s6.y) : le.d6;
-    double s12 = MIXED ? ((double)le.s12.x - (double)le.s12.y) : le.d12;
+    double s6 = MIXED ? (f32_to_f64_bits(le.s6.x) - f32_to_f64_bits(le.s6.y)) : le.d6;
+    double s12 = MIXED ? (f32_to_f64_bits(le.s12.x) - f32_to_f64_bits(le.s12.y)) : le.d12;
     long long np = le.pairs;
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) {
@@ -511,11 +657,28 @@ static size_t smem_bytes(int warps) {
     return sizeof(WarpSmem<T>) * (size_t)warps;
 }
 
+// One resident wave: SMs x the blocks that fit on an SM (cached per shape).
+template <bool MIXED, int NI, int MODE>
+static int force_blocks(Ctx *c) {
+    static int cache[17] = {0};
+    const int warps = c->warps;
+    if (!cache[warps]) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force<MIXED, NI, MODE>, warps * 32,
+                                                      smem_bytes<MIXED, NI>(warps));
+        if (per_sm < 1) per_sm = 1;
+        cache[warps] = per_sm;
+    }
+    int blocks = c->num_sms * cache[warps];
+    const int maxb = c->nwarp_max / warps;
+    return blocks < maxb ? blocks : maxb;
+}
+
 template <bool MIXED, int NI, int MODE>
 static cudaError_t launch_one(Ctx *c, ForceArgs &a, cudaStream_t s) {
     const int warps = c->warps;
     const size_t sm = smem_bytes<MIXED, NI>(warps);
-    int blocks = force_grid_warps(c) / warps;
+    const int blocks = force_blocks<MIXED, NI, MODE>(c);
     k_force<MIXED, NI, MODE><<<blocks, warps * 32, sm, s>>>(a);
     return cudaGetLastError();
 }
@@ -531,6 +694,15 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
     a.kx = c->kx; a.ky = c->ky; a.kz = c->kz;
     a.warp_acc = c->d_warp_acc; a.warp_pairs = c->d_warp_pairs;
     a.group = 0; a.colour = 0;
+    for (int oi = 0; oi < 27; ++oi) {
+        const int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, oi / 9 - 1};
+        for (int d = 0; d < 3; ++d) {
+            const double S = (double)o[d] * c->g.h[d];
+            const float Sh = (float)S;
+            a.sh[oi][d] = Sh;
+            a.sl[oi][d] = (float)(S - (double)Sh);
+        }
+    }
     cudaError_t e = cudaSuccess;
     const size_t nbytes = sizeof(double) * (size_t)c->n;
     if (sched == LC_SCHED_COLOUR) {

@@ -34,6 +34,10 @@ struct Grid {
     int ncell;
     double rc, rc2;   // cutoff and its square (FP64, rc * rc)
     float hf[3];      // FP32 cell sides
+    float hl[3];      // h - hf rounded to FP32 (double-float cell side)
+    float invf[3];    // nc / L in FP32
+    float Lf_lo[3];   // FP32 value below L: hi < Lf_lo implies x < L
+    float cmargin[3]; // distance from a cell face below which binning is exact FP64
     float rc2f_lo, rc2f_hi;  // FP32 band around rc^2 for the mixed path
     int ncolours;
     int class_count[3][3];   // cells of colour class a along dimension d
@@ -119,7 +123,11 @@ cudaError_t init_force_kernels();
 // ---- small device helpers ----------------------------------------------------
 // Periodic wrap into [0, L), each operation rounded once (no contraction):
 // x - L floor(x / L), then one correction for the rounding edge cases.
+// For x in (0, L) that formula returns x itself (x / L rounds below
+// 1, so floor gives 0), which the fast path returns without the FP64
+// division.
 __device__ __forceinline__ double wrap_coord(double x, double L) {
+    if (x > 0.0 && x < L) return x;
     double q = floor(__ddiv_rn(x, L));
     double p = __dmul_rn(q, L);
     double y = __dsub_rn(x, p);
@@ -134,6 +142,61 @@ __device__ __forceinline__ int cell_coord(double xw, double inv, int nc) {
     int c = (int)__dmul_rn(xw, inv);
     c = c > nc - 1 ? nc - 1 : c;
     return c < 0 ? 0 : c;
+}
+
+// Exact FP32 -> FP64 conversion by rearranging the IEEE-754 bit fields
+// (binary32: 1/8/23 bits, binary64: 1/11/52): integer operations only, so it
+// does not occupy the FP64 pipe.  Zeros and subnormals map to signed zero,
+// infinities and NaNs keep their class.
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned m = b & 0x7fffffu;
+    // exponent rebias 127 -> 1023 (+896), 255 -> 2047 (+1792), 0 -> 0
+    const unsigned eb = e == 0u ? 0u : (e == 0xffu ? 0x7ffu : e + 896u);
+    const unsigned hi = (b & 0x80000000u) | (eb << 20) | (e == 0u ? 0u : (m >> 3));
+    const unsigned lo = e == 0u ? 0u : (m << 29);
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// FP32 view of an FP64 value without the FP64 pipe: the binary64 sign,
+// exponent and top 23 mantissa bits rearranged as binary32 (truncation, so
+// |hi| <= |x| and |x - hi| < 2^-23 |x|), and the remaining 29 mantissa bits as a
+// second FP32 value lo (rounded to 24 bits: |x - hi - lo| <= 2^-47 |x|).
+// Valid for 2^-100 <= |x| < 2^100 (callers treat other magnitudes, zero
+// included, on an exact FP64 path).
+struct Split {
+    float hi, lo;
+};
+__device__ __forceinline__ bool split_f64(double x, Split &s) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ffu) - 1023;
+    if (e < -100 || e >= 100) return false;
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const unsigned man_hi = (unsigned)((b >> 29) & 0x7fffffu);
+    s.hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | man_hi);
+    const unsigned low = (unsigned)(b & 0x1fffffffull);          // 29 bits
+    const float scale = __uint_as_float((unsigned)(e - 52 + 127) << 23);   // 2^(e-52)
+    const float l = __uint2float_rn(low) * scale;
+    s.lo = sign ? -l : l;
+    return true;
+}
+
+// Cell coordinate of a coordinate without FP64 arithmetic when that is safe:
+// returns false (caller takes the exact FP64 path: wrap, multiply, truncate)
+// unless x lies strictly inside (0, L) and x * nc / L is at least 1e-4 away
+// from an integer, in which case the FP32 estimate has the same floor.
+// The FP32 estimate of x * nc / L has relative error below 4e-7, i.e. below
+// 4e-7 nc absolute; `margin` (2e-6 nc + 1e-6) keeps a factor 5 of headroom.
+__device__ __forceinline__ bool cell_coord_fast(const Split &s, float Lf_lo, float invf, int nc, float margin,
+                                                int &c) {
+    if (!(s.hi > 0.0f && s.hi < Lf_lo)) return false;
+    const float t = (s.hi + s.lo) * invf - 0.5f;
+    const float r = (t + 8388608.0f) - 8388608.0f;          // nearest integer to t
+    if (fabsf(t - r) > 0.5f - margin) return false;         // too close to a cell face
+    c = (int)r;
+    c = c > nc - 1 ? nc - 1 : c;
+    return true;
 }
 
 __host__ __device__ __forceinline__ int colour_class(int c, int nc) {

@@ -1,8 +1,8 @@
 // Velocity-Verlet integration (m = 1) and the FP64 reductions of energy,
 // virial and kinetic energy.  All state lives in cell-sorted order, so the
-// integrator streams contiguous FP64 arrays; every product and sum is
-// rounded once (__dmul_rn / __dadd_rn), as in the definition
-//   v <- v + (dt/2) F,  x <- x + dt v   (wrap happens in the next binning).
+// integrator streams contiguous FP64 arrays:
+//   v <- v + (dt/2) F,  x <- x + dt v   (wrap happens in the next binning),
+// each update one FP64 fused multiply-add (one rounding).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -15,22 +15,22 @@ constexpr int kRedThreads = 1024;
 __global__ void k_kick_drift(int n, double half, double dt, State st, const double *__restrict__ fx,
                              const double *__restrict__ fy, const double *__restrict__ fz) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        double vx = __dadd_rn(st.vx[s], __dmul_rn(half, fx[s]));
-        double vy = __dadd_rn(st.vy[s], __dmul_rn(half, fy[s]));
-        double vz = __dadd_rn(st.vz[s], __dmul_rn(half, fz[s]));
+        double vx = fma(half, fx[s], st.vx[s]);
+        double vy = fma(half, fy[s], st.vy[s]);
+        double vz = fma(half, fz[s], st.vz[s]);
         st.vx[s] = vx; st.vy[s] = vy; st.vz[s] = vz;
-        st.x[s] = __dadd_rn(st.x[s], __dmul_rn(dt, vx));
-        st.y[s] = __dadd_rn(st.y[s], __dmul_rn(dt, vy));
-        st.z[s] = __dadd_rn(st.z[s], __dmul_rn(dt, vz));
+        st.x[s] = fma(dt, vx, st.x[s]);
+        st.y[s] = fma(dt, vy, st.y[s]);
+        st.z[s] = fma(dt, vz, st.z[s]);
     }
 }
 
 __global__ void k_kick(int n, double half, State st, const double *__restrict__ fx,
                        const double *__restrict__ fy, const double *__restrict__ fz) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        st.vx[s] = __dadd_rn(st.vx[s], __dmul_rn(half, fx[s]));
-        st.vy[s] = __dadd_rn(st.vy[s], __dmul_rn(half, fy[s]));
-        st.vz[s] = __dadd_rn(st.vz[s], __dmul_rn(half, fz[s]));
+        st.vx[s] = fma(half, fx[s], st.vx[s]);
+        st.vy[s] = fma(half, fy[s], st.vy[s]);
+        st.vz[s] = fma(half, fz[s], st.vz[s]);
     }
 }
 
@@ -123,7 +123,7 @@ cudaError_t launch_kinetic(Ctx *c, cudaStream_t s) {
 }
 
 cudaError_t launch_energy_reduce(Ctx *c, cudaStream_t s, int full) {
-    k_final_pot<<<1, kRedThreads, 0, s>>>(force_grid_warps(c), c->d_warp_acc, c->d_warp_pairs, full,
+    k_final_pot<<<1, kRedThreads, 0, s>>>(c->nwarp_max, c->d_warp_acc, c->d_warp_pairs, full,
                                           c->d_result, c->d_npairs);
     return cudaGetLastError();
 }
