@@ -118,7 +118,9 @@ lc_status lc_forces(lc_ctx *ctx, lc_schedule sched, void *stream);
 /* nsteps velocity-Verlet steps of size dt (m = 1): v += dt/2 F; x += dt v;
  * bin; F = F(x); v += dt/2 F.  Computes the forces first if they are stale.
  * The step's kernels are captured once into a CUDA graph per (schedule, dt)
- * and replayed. */
+ * and replayed.  Potential energy, virial and pair count are accumulated in
+ * the last step of the call (lc_energy_virial reports them); the other
+ * steps skip that accumulation. */
 lc_status lc_verlet_step(lc_ctx *ctx, double dt, int nsteps, lc_schedule sched, void *stream);
 
 /* Energies of the current state, FP64: potential U and virial W of the last
@@ -149,7 +151,7 @@ lc_status lc_schedule_check(lc_ctx *ctx, lc_schedule sched, int64_t *conflicts,
                             int64_t *coverage_errors, void *stream);
 
 /* Tile shape of the force kernels: ni = particles of the centre cell held
- * per warp (8, 16 or 32), warps = warps per thread block (1 .. 16).  0 keeps
+ * per warp (8 or 16), warps = warps per thread block (1 .. 16).  0 keeps
  * the current value.  Used by the autotuner. */
 lc_status lc_set_tile(lc_ctx *ctx, int ni, int warps);
 

@@ -119,7 +119,7 @@ static cudaError_t dalloc(T **p, size_t count) {
 static void free_ctx(Ctx *c) {
     if (!c) return;
     void *ptrs[] = {c->cur.x, c->cur.vx, c->cur.id, c->nxt.x, c->nxt.vx, c->nxt.id, c->d_cell, c->d_rank,
-                    c->d_count, c->d_start, c->d_src, c->d_blocksums, c->d_colour, c->d_p4, c->fx, c->kx,
+                    c->d_count, c->d_start, c->d_src, c->d_key, c->d_blocksums, c->d_colour, c->d_p4, c->fx, c->kx,
                     c->d_warp_acc, c->d_warp_pairs, c->d_kin_part, c->d_result, c->d_npairs, c->d_err,
                     c->d_stamp, c->d_visit, c->d_counters};
     for (void *p : ptrs)
@@ -186,7 +186,7 @@ lc_status lc_create(const double box[3], double rc, int64_t n, lc_precision prec
     c->nwarp_max = c->num_sms * 64;
     if ((e = upload_stencil(st)) || (e = alloc_state(&c->cur, n)) || (e = alloc_state(&c->nxt, n)) ||
         (e = dalloc(&c->d_cell, N)) || (e = dalloc(&c->d_rank, N)) || (e = dalloc(&c->d_count, NC)) ||
-        (e = dalloc(&c->d_start, NC + 1)) || (e = dalloc(&c->d_src, N)) ||
+        (e = dalloc(&c->d_start, NC + 1)) || (e = dalloc(&c->d_src, N)) || (e = dalloc(&c->d_key, N)) ||
         (e = dalloc(&c->d_blocksums, (size_t)ntiles + 1)) || (e = dalloc(&c->d_colour, NC)) ||
         (e = dalloc(&c->d_p4, N)) || (e = dalloc(&c->fx, 3 * N)) || (e = dalloc(&c->kx, 3 * N)) ||
         (e = dalloc(&c->d_warp_acc, 4 * (size_t)c->nwarp_max)) || (e = dalloc(&c->d_warp_pairs, (size_t)c->nwarp_max)) ||
@@ -271,13 +271,16 @@ lc_status lc_forces(lc_ctx *c, lc_schedule sched, void *stream) {
     return st;
 }
 
-// One Verlet step as a sequence of stream-ordered launches.
-static cudaError_t step_launches(lc_ctx *c, double dt, lc_schedule sched, cudaStream_t s, int *launches) {
+// One Verlet step as a sequence of stream-ordered launches.  stats: the
+// force evaluation also produces energy, virial and pair count (the last
+// step of every lc_verlet_step call does, so lc_energy_virial stays valid).
+static cudaError_t step_launches(lc_ctx *c, double dt, lc_schedule sched, cudaStream_t s, int *launches,
+                                 bool stats) {
     cudaError_t e;
     if ((e = launch_kick_drift(c, dt, s))) return e;
     ++*launches;
     if ((e = launch_bin(c, s, launches))) return e;
-    if ((e = launch_forces(c, sched, s, launches))) return e;
+    if ((e = launch_forces(c, sched, s, launches, stats))) return e;
     if ((e = launch_kick(c, dt, s))) return e;
     ++*launches;
     return cudaSuccess;
@@ -306,8 +309,8 @@ lc_status lc_verlet_step(lc_ctx *c, double dt, int nsteps, lc_schedule sched, vo
         cudaGraph_t graph;
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         int per2 = 0;
-        if (!e) e = step_launches(c, dt, sched, cap, &per2);
-        if (!e) e = step_launches(c, dt, sched, cap, &per2);
+        if (!e) e = step_launches(c, dt, sched, cap, &per2, false);
+        if (!e) e = step_launches(c, dt, sched, cap, &per2, true);
         cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
         c->cur = saved_cur; c->nxt = saved_nxt;   // two swaps: same as before
         if (!e) e = e2;
@@ -325,7 +328,7 @@ lc_status lc_verlet_step(lc_ctx *c, double dt, int nsteps, lc_schedule sched, vo
     }
     if (done < nsteps) {
         int l = 0;
-        LC_TRY(step_launches(c, dt, sched, s, &l));
+        LC_TRY(step_launches(c, dt, sched, s, &l, true));
         ++done;
     }
     c->binned = true;
@@ -415,7 +418,7 @@ lc_status lc_schedule_check(lc_ctx *c, lc_schedule sched, int64_t *conflicts, in
 
 lc_status lc_set_tile(lc_ctx *c, int ni, int warps) {
     if (!c) return LC_ERR_INVALID_ARG;
-    if (ni && ni != 8 && ni != 16 && ni != 32) return LC_ERR_INVALID_ARG;
+    if (ni && ni != 8 && ni != 16) return LC_ERR_INVALID_ARG;
     if (warps < 0 || warps > 16) return LC_ERR_INVALID_ARG;
     if (ni) c->ni = ni;
     if (warps) c->warps = warps;

@@ -1,15 +1,17 @@
 // Counting-sort binning of the link-cell method (paper Sec. IV: cells of
 // side >= r_c, partners only in the 27 surrounding cells).
 //
-//   k_cellid    wrap (FP64, each op rounded once), cell index, atomic count
-//               per cell; the atomic's return value is a provisional rank
-//   k_scan_*    exclusive prefix sum of the counts -> cell start
-//   k_scatter   provisional slot start[cell] + rank
-//   k_cellsort  one warp per cell: rank the cell's particles by ID (counting
-//               comparison, so the result does not depend on the order in
-//               which the atomics were served), then gather the FP64 state
-//               into the new slot and write the FP32 cell-centre-local
-//               coordinates used by the mixed-precision force sweep.
+//   k_cellid      wrap, cell index, count per cell (warp-aggregated atomics;
+//                 the atomic's return value gives a provisional rank)
+//   k_scan_*      exclusive prefix sum of the counts -> cell start
+//   k_scatter     provisional slot start[cell] + rank: source index and ID
+//   k_rank_gather one thread per slot: final rank = number of the cell's
+//                 particles with a smaller ID (so the result does not depend
+//                 on the order in which the atomics were served); gather the
+//                 FP64 state into that slot and write the FP32
+//                 cell-centre-local coordinates of the mixed-precision sweep.
+// Cell indices and wraps avoid the FP64 pipe except near a cell face or for
+// a coordinate outside (0, L), where the exact FP64 formula decides.
 // The final permutation is stable by particle ID inside each cell, so the
 // whole binning is bit-exact and reproducible.
 #include <cuda_runtime.h>
@@ -26,27 +28,43 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 __global__ void k_cellid(Grid g, int n, const double *__restrict__ x, const double *__restrict__ y,
                          const double *__restrict__ z, int *__restrict__ cell, int *__restrict__ rank,
                          int *__restrict__ count, int *__restrict__ err) {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        const double X[3] = {x[s], y[s], z[s]};
-        int cc[3];
-        bool fast = true;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            Split sp;
-            fast = fast && split_f64(X[d], sp) && cell_coord_fast(sp, g.Lf_lo[d], g.invf[d], g.nc[d], g.cmargin[d], cc[d]);
-        }
+    const int lane = threadIdx.x & 31;
+    for (int s0 = blockIdx.x * blockDim.x; s0 < n; s0 += gridDim.x * blockDim.x) {
+        const int s = s0 + threadIdx.x;
+        const bool act = s < n;
         int c = 0;
-        if (fast) {
-            c = cc[0] + g.nc[0] * (cc[1] + g.nc[1] * cc[2]);
-        } else if (isfinite(X[0]) && isfinite(X[1]) && isfinite(X[2])) {
-            // exact FP64 path: outside (0, L) or within the margin of a cell face
-            for (int d = 0; d < 3; ++d) cc[d] = cell_coord(wrap_coord(X[d], g.L[d]), g.inv[d], g.nc[d]);
-            c = cc[0] + g.nc[0] * (cc[1] + g.nc[1] * cc[2]);
-        } else {
-            atomicOr(err, kErrNonfinite);
+        if (act) {
+            const double X[3] = {x[s], y[s], z[s]};
+            int cc[3];
+            bool fast = true;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                Split sp;
+                fast = fast && split_f64(X[d], sp) &&
+                       cell_coord_fast(sp, g.Lf_lo[d], g.invf[d], g.nc[d], g.cmargin[d], cc[d]);
+            }
+            if (fast) {
+                c = cc[0] + g.nc[0] * (cc[1] + g.nc[1] * cc[2]);
+            } else if (isfinite(X[0]) && isfinite(X[1]) && isfinite(X[2])) {
+                // exact FP64 path: outside (0, L) or within the margin of a cell face
+                for (int d = 0; d < 3; ++d) cc[d] = cell_coord(wrap_coord(X[d], g.L[d]), g.inv[d], g.nc[d]);
+                c = cc[0] + g.nc[0] * (cc[1] + g.nc[1] * cc[2]);
+            } else {
+                atomicOr(err, kErrNonfinite);
+            }
         }
-        cell[s] = c;
-        rank[s] = atomicAdd(count + c, 1);
+        // lanes of a warp mostly share cells (the previous order is cell
+        // sorted): one atomic per distinct cell, ranks by lane order
+        const unsigned mask = __ballot_sync(kFull, act);
+        if (act) {
+            const unsigned peers = __match_any_sync(mask, c);
+            const int leader = __ffs(peers) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(count + c, __popc(peers));
+            base = __shfl_sync(peers, base, leader);
+            cell[s] = c;
+            rank[s] = base + __popc(peers & ((1u << lane) - 1u));
+        }
     }
 }
 
@@ -137,84 +155,74 @@ __global__ void k_scan_add(int ncell, int n, int *__restrict__ start, const int 
 }
 
 __global__ void k_scatter(int n, const int *__restrict__ cell, const int *__restrict__ rank,
-                          const int *__restrict__ start, int *__restrict__ src) {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
-        src[start[cell[s]] + rank[s]] = s;
+                          const int *__restrict__ start, const int *__restrict__ id, int *__restrict__ src,
+                          int *__restrict__ key) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const int t = start[cell[s]] + rank[s];
+        src[t] = s;
+        key[t] = id[s];
+    }
 }
 
-// One warp per cell.  Rank of an entry = number of entries of the cell with
-// a smaller ID (IDs are unique), so slot = start + rank is stable by ID.
-__global__ void k_cellsort(Grid g, int write_p4, const int *__restrict__ start, const int *__restrict__ count,
-                           const int *__restrict__ src, State in, State out, float4 *__restrict__ p4) {
-    const int lane = threadIdx.x & 31;
-    const int W = gridDim.x * (blockDim.x >> 5);
-    for (int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < g.ncell; c += W) {
+// One thread per slot t of the new order.  Rank = number of the cell's
+// particles with a smaller ID (IDs are unique), so slot = start + rank is
+// stable by ID whatever order the atomics were served in.
+__global__ void k_rank_gather(Grid g, int n, int write_p4, const int *__restrict__ start,
+                              const int *__restrict__ count, const int *__restrict__ cell,
+                              const int *__restrict__ src, const int *__restrict__ key, State in, State out,
+                              float4 *__restrict__ p4) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int s = src[t];
+        const int my_id = key[t];
+        const int c = cell[s];
         const int base = start[c], cnt = count[c];
+        int r = 0;
+        for (int k = 0; k < cnt; ++k) r += (key[base + k] < my_id) ? 1 : 0;
+        const int dst = base + r;
         int cc[3];
         cc[0] = c % g.nc[0];
         cc[1] = (c / g.nc[0]) % g.nc[1];
         cc[2] = c / (g.nc[0] * g.nc[1]);
-        for (int e0 = 0; e0 < cnt; e0 += 32) {
-            const int e = e0 + lane;
-            int my_src = 0, my_id = 0;
-            if (e < cnt) {
-                my_src = src[base + e];
-                my_id = in.id[my_src];
-            }
-            int r = 0;
-            if (cnt <= 32) {
-                for (int k = 0; k < cnt; ++k) {
-                    int other = __shfl_sync(kFull, my_id, k);
-                    r += (other < my_id) ? 1 : 0;
-                }
-            } else if (e < cnt) {
-                for (int k = 0; k < cnt; ++k) r += (in.id[src[base + k]] < my_id) ? 1 : 0;
-            }
-            if (e < cnt) {
-                const int dst = base + r;
-                double X[3] = {in.x[my_src], in.y[my_src], in.z[my_src]};
-                Split sp[3];
-                bool fast = true;
+        double X[3] = {in.x[s], in.y[s], in.z[s]};
+        Split sp[3];
+        bool fast = true;
 #pragma unroll
-                for (int d = 0; d < 3; ++d)
-                    fast = fast && split_f64(X[d], sp[d]) && sp[d].hi > 0.0f && sp[d].hi < g.Lf_lo[d];
-                if (!fast) {
-                    // exact wrap (rare: the particle left the box or sits at 0)
-                    for (int d = 0; d < 3; ++d) {
-                        X[d] = wrap_coord(X[d], g.L[d]);
-                        if (!split_f64(X[d], sp[d])) sp[d].hi = sp[d].lo = 0.0f;
-                    }
-                }
-                out.x[dst] = X[0]; out.y[dst] = X[1]; out.z[dst] = X[2];
-                out.vx[dst] = in.vx[my_src]; out.vy[dst] = in.vy[my_src]; out.vz[dst] = in.vz[my_src];
-                out.id[dst] = my_id;
-                if (write_p4) {
-                    // FP32 offset from the cell centre (c + 1/2) h, formed in
-                    // double-float arithmetic (TwoProduct / TwoSum) from the
-                    // hi + lo split of x; the rounding residual of each offset
-                    // (|r| <= 2^-23 for |offset| < 4) is kept as a 10-bit
-                    // signed fraction of 2^-23 in the spare fourth word.
-                    float hi[3];
-                    unsigned w = 0;
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        const float cf = (float)cc[d] + 0.5f;
-                        const float ph = cf * g.hf[d];
-                        const float pl = fmaf(cf, g.hf[d], -ph) + cf * g.hl[d];
-                        const float s = sp[d].hi - ph;                  // TwoSum(hi, -ph)
-                        const float bb = s - sp[d].hi;
-                        const float e2 = (sp[d].hi - (s - bb)) + (-ph - bb);
-                        const float rest = (sp[d].lo - pl) + e2;
-                        const float t = s + rest;
-                        const float res = rest - (t - s);
-                        hi[d] = t;
-                        int q = __float2int_rn(res * (float)kLoScale);
-                        q = q > 511 ? 511 : (q < -511 ? -511 : q);
-                        w |= (unsigned)(q + 512) << (10 * d);
-                    }
-                    p4[dst] = make_float4(hi[0], hi[1], hi[2], __uint_as_float(w));
-                }
+        for (int d = 0; d < 3; ++d) fast = fast && split_f64(X[d], sp[d]) && sp[d].hi > 0.0f && sp[d].hi < g.Lf_lo[d];
+        if (!fast) {
+            // exact wrap (rare: the particle left the box or sits at 0)
+            for (int d = 0; d < 3; ++d) {
+                X[d] = wrap_coord(X[d], g.L[d]);
+                if (!split_f64(X[d], sp[d])) sp[d].hi = sp[d].lo = 0.0f;
             }
+        }
+        out.x[dst] = X[0]; out.y[dst] = X[1]; out.z[dst] = X[2];
+        out.vx[dst] = in.vx[s]; out.vy[dst] = in.vy[s]; out.vz[dst] = in.vz[s];
+        out.id[dst] = my_id;
+        if (write_p4) {
+            // FP32 offset from the cell centre (c + 1/2) h, formed in
+            // double-float arithmetic (TwoProduct / TwoSum) from the hi + lo
+            // split of x; the rounding residual of each offset (|r| <= 2^-23
+            // for |offset| < 4) is kept as a 10-bit signed fraction of 2^-23
+            // in the spare fourth word.
+            float hi[3];
+            unsigned w = 0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float cf = (float)cc[d] + 0.5f;
+                const float ph = cf * g.hf[d];
+                const float pl = fmaf(cf, g.hf[d], -ph) + cf * g.hl[d];
+                const float sum = sp[d].hi - ph;                 // TwoSum(hi, -ph)
+                const float bb = sum - sp[d].hi;
+                const float e2 = (sp[d].hi - (sum - bb)) + (-ph - bb);
+                const float rest = (sp[d].lo - pl) + e2;
+                const float tt = sum + rest;
+                const float res = rest - (tt - sum);
+                hi[d] = tt;
+                int q = __float2int_rn(res * (float)kLoScale);
+                q = q > 511 ? 511 : (q < -511 ? -511 : q);
+                w |= (unsigned)(q + 512) << (10 * d);
+            }
+            p4[dst] = make_float4(hi[0], hi[1], hi[2], __uint_as_float(w));
         }
     }
 }
@@ -249,9 +257,9 @@ cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches) {
     k_scan_add<<<c->num_sms * 4, 256, 0, s>>>(ncell, n, c->d_start, c->d_blocksums);
     *launches += 3;
     if (n > 0) {
-        k_scatter<<<grid_n, 256, 0, s>>>(n, c->d_cell, c->d_rank, c->d_start, c->d_src);
-        k_cellsort<<<c->num_sms * 8, 256, 0, s>>>(c->g, c->prec == LC_PREC_MIXED, c->d_start, c->d_count,
-                                                  c->d_src, c->cur, c->nxt, c->d_p4);
+        k_scatter<<<grid_n, 256, 0, s>>>(n, c->d_cell, c->d_rank, c->d_start, c->cur.id, c->d_src, c->d_key);
+        k_rank_gather<<<grid_n, 256, 0, s>>>(c->g, n, c->prec == LC_PREC_MIXED, c->d_start, c->d_count, c->d_cell,
+                                             c->d_src, c->d_key, c->cur, c->nxt, c->d_p4);
         *launches += 2;
     }
     e = cudaGetLastError();

@@ -56,6 +56,7 @@ struct ForceArgs {
     long long *warp_pairs;      // [W]
     int group, colour;          // colour phase
     int ntasks;
+    int stats;                  // accumulate energy, virial and pair count
     float sh[27][3];            // o * h rounded to FP32, offset index (ox+1) + 3 (oy+1) + 9 (oz+1)
     float sl[27][3];            // o * h - sh, rounded to FP32
 };
@@ -127,7 +128,8 @@ __device__ __forceinline__ TaskCells make_task(const Grid &g, int group, int col
 // ----------------------------------------------------- per-warp scratch ----
 template <typename T>
 struct alignas(16) WarpSmem {
-    float4 i4[32];              // mixed: centre-cell particle (x, y, z, slot bits)
+    float4 ipa[16];             // mixed: particles 2m, 2m+1 as (x, x', y, y')
+    float4 ipb[16];             // mixed: (z, z', slot bits, slot' bits)
     float corr[32][3];          // mixed: i-side forces of near-r_c pairs
     T ix[32], iy[32], iz[32];   // FP64: centre-cell particles
     int islot[32];
@@ -337,9 +339,71 @@ __device__ __forceinline__ void write_i_chunk(const ForceArgs &a, S &sm, T (&ax)
     __syncwarp();
 }
 
+// Mixed-precision candidate loop of one 32-slot neighbour chunk against the
+// NI staged centre-cell particles, two of them per packed f32x2 operation.
+// SELF: the chunk holds intra-cell entries (slot order decides the pair);
+// STATS: accumulate energy partials and the pair count.
+template <int NI, bool N3, bool SELF, bool STATS>
+__device__ __forceinline__ void pair_loop(const WarpSmem<float> &sm, const float (&pj)[3], const float (&lj)[3],
+                                          int jlim, int jexcl, float rc2lo, float rc2hi,
+                                          float2 (&ax2)[NI / 2], float2 (&ay2)[NI / 2], float2 (&az2)[NI / 2],
+                                          float2 &gx, float2 &gy, float2 &gz, float2 &e6, float2 &e12,
+                                          int &npair, bool &amb) {
+    const float2 one2 = make_float2(1.0f, 1.0f);
+    const float2 c48 = make_float2(48.0f, 48.0f), cm24 = make_float2(-24.0f, -24.0f);
+    const float2 npx = make_float2(-pj[0], -pj[0]), npy = make_float2(-pj[1], -pj[1]), npz = make_float2(-pj[2], -pj[2]);
+    const float2 nlx = make_float2(-lj[0], -lj[0]), nly = make_float2(-lj[1], -lj[1]), nlz = make_float2(-lj[2], -lj[2]);
+#pragma unroll
+    for (int m = 0; m < NI / 2; ++m) {
+        const float4 A = lds4(&sm.ipa[m]);
+        const float4 B = lds4(&sm.ipb[m]);
+        bool oka = true, okb = true;
+        if (SELF) {
+            const int sa = __float_as_int(B.z), sb = __float_as_int(B.w);
+            oka = N3 ? (sa < jlim) : (sa != jexcl);
+            okb = N3 ? (sb < jlim) : (sb != jexcl);
+        }
+        const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), npx), nlx);
+        const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), npy), nly);
+        const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), npz), nlz);
+        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+        const bool neara = oka && (r2.x < rc2hi), nearb = okb && (r2.y < rc2hi);
+        const bool hita = neara && (r2.x < rc2lo), hitb = nearb && (r2.y < rc2lo);
+        amb |= (neara && !hita) || (nearb && !hitb);
+        float2 y;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y.x) : "f"(r2.x));
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y.y) : "f"(r2.y));
+        const float2 e = __ffma2_rn(make_float2(-r2.x, -r2.y), y, one2);   // Newton step
+        y = __ffma2_rn(y, e, y);
+        y.x = hita ? y.x : 0.0f;   // masks misses and r2 = 0 (i == j)
+        y.y = hitb ? y.y : 0.0f;
+        const float2 s6 = __fmul2_rn(__fmul2_rn(y, y), y);
+        const float2 f = __fmul2_rn(__fmul2_rn(s6, y), __ffma2_rn(s6, c48, cm24));
+        ax2[m] = __ffma2_rn(f, dx, ax2[m]);
+        ay2[m] = __ffma2_rn(f, dy, ay2[m]);
+        az2[m] = __ffma2_rn(f, dz, az2[m]);
+        if (N3) {
+            gx = __ffma2_rn(f, dx, gx);
+            gy = __ffma2_rn(f, dy, gy);
+            gz = __ffma2_rn(f, dz, gz);
+        }
+        if (STATS) {
+            e6 = __fadd2_rn(e6, s6);
+            e12 = __ffma2_rn(s6, s6, e12);
+            npair += (hita ? 1 : 0) + (hitb ? 1 : 0);
+        }
+    }
+}
+
+__device__ __forceinline__ float staged(const float4 *arr, int k, int comp) {
+    // component comp (0: x or z, 1: y or slot) of staged particle k
+    const float *f = reinterpret_cast<const float *>(arr);
+    return f[4 * (k >> 1) + 2 * comp + (k & 1)];
+}
+
 // Mixed precision: FP32 pair arithmetic, two centre-cell particles per
 // packed f32x2 operation (the lane's j is the same for both).
-template <int NI, int MODE>
+template <int NI, int MODE, bool STATS>
 __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const TaskCells &tc, int lane, LaneEnergy &le) {
     constexpr bool N3 = (MODE != kFullShell);
     const Grid &g = a.g;
@@ -347,16 +411,19 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
     const int a0 = a.start[tc.A];
     const int na = a.count[tc.A];
     const float rc2lo = g.rc2f_lo, rc2hi = g.rc2f_hi;
-    const float2 one2 = make_float2(1.0f, 1.0f);
-    const float2 c48 = make_float2(48.0f, 48.0f), cm24 = make_float2(-24.0f, -24.0f);
 
     for (int i0 = 0; i0 < na; i0 += NI) {
         if (lane < NI) {   // stage the i chunk (far-away sentinels past the end)
             const int ii = i0 + lane;
             float4 p = make_float4(1.0e15f, 1.0e15f, 1.0e15f, 0.f);
             if (ii < na) p = a.p4[a0 + ii];
-            p.w = __int_as_float(ii < na ? a0 + ii : 0x7fffffff);
-            sm.i4[lane] = p;
+            float *A = reinterpret_cast<float *>(sm.ipa);
+            float *B = reinterpret_cast<float *>(sm.ipb);
+            const int m = lane >> 1, h = lane & 1;
+            A[4 * m + h] = p.x;
+            A[4 * m + 2 + h] = p.y;
+            B[4 * m + h] = p.z;
+            B[4 * m + 2 + h] = __int_as_float(ii < na ? a0 + ii : 0x7fffffff);
             sm.corr[lane][0] = sm.corr[lane][1] = sm.corr[lane][2] = 0.f;
         }
         float2 ax2[NI / 2], ay2[NI / 2], az2[NI / 2];
@@ -396,47 +463,14 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
                         lj[d] = (err + res) + sm.nb_sl[nb][d];
                     }
                 }
-                const float2 npx = make_float2(-pj[0], -pj[0]), npy = make_float2(-pj[1], -pj[1]),
-                             npz = make_float2(-pj[2], -pj[2]);
-                const float2 nlx = make_float2(-lj[0], -lj[0]), nly = make_float2(-lj[1], -lj[1]),
-                             nlz = make_float2(-lj[2], -lj[2]);
                 float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;   // sum of f d over the i's (j gets -g)
                 bool amb = false;
-#pragma unroll
-                for (int k = 0; k < NI; k += 2) {
-                    const float4 pa = lds4(&sm.i4[k]);
-                    const float4 pb = lds4(&sm.i4[k + 1]);
-                    const int sa = __float_as_int(pa.w), sb = __float_as_int(pb.w);
-                    const bool oka = N3 ? (sa < jlim) : (sa != jexcl);
-                    const bool okb = N3 ? (sb < jlim) : (sb != jexcl);
-                    const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(pa.x, pb.x), npx), nlx);
-                    const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(pa.y, pb.y), npy), nly);
-                    const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(pa.z, pb.z), npz), nlz);
-                    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-                    const bool neara = oka && (r2.x < rc2hi), nearb = okb && (r2.y < rc2hi);
-                    const bool hita = neara && (r2.x < rc2lo), hitb = nearb && (r2.y < rc2lo);
-                    amb |= (neara && !hita) || (nearb && !hitb);
-                    float2 y;
-                    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y.x) : "f"(r2.x));
-                    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y.y) : "f"(r2.y));
-                    const float2 e = __ffma2_rn(make_float2(-r2.x, -r2.y), y, one2);   // Newton step
-                    y = __ffma2_rn(y, e, y);
-                    y.x = hita ? y.x : 0.0f;   // masks misses and r2 = 0 (i == j)
-                    y.y = hitb ? y.y : 0.0f;
-                    const float2 s6 = __fmul2_rn(__fmul2_rn(y, y), y);
-                    const float2 f = __fmul2_rn(__fmul2_rn(s6, y), __ffma2_rn(s6, c48, cm24));
-                    ax2[k / 2] = __ffma2_rn(f, dx, ax2[k / 2]);
-                    ay2[k / 2] = __ffma2_rn(f, dy, ay2[k / 2]);
-                    az2[k / 2] = __ffma2_rn(f, dz, az2[k / 2]);
-                    if (N3) {
-                        gx = __ffma2_rn(f, dx, gx);
-                        gy = __ffma2_rn(f, dy, gy);
-                        gz = __ffma2_rn(f, dz, gz);
-                    }
-                    e6 = __fadd2_rn(e6, s6);
-                    e12 = __ffma2_rn(s6, s6, e12);
-                    npair += (hita ? 1 : 0) + (hitb ? 1 : 0);
-                }
+                if (__any_sync(kFull, is_self))
+                    pair_loop<NI, N3, true, STATS>(sm, pj, lj, jlim, jexcl, rc2lo, rc2hi, ax2, ay2, az2, gx, gy, gz,
+                                                   e6, e12, npair, amb);
+                else
+                    pair_loop<NI, N3, false, STATS>(sm, pj, lj, jlim, jexcl, rc2lo, rc2hi, ax2, ay2, az2, gx, gy, gz,
+                                                    e6, e12, npair, amb);
                 float fjx = -(gx.x + gx.y), fjy = -(gy.x + gy.y), fjz = -(gz.x + gz.y);
                 if (__any_sync(kFull, amb)) {
                     // rare: candidates within the band around r_c^2 are decided
@@ -446,12 +480,11 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
                     for (int d = 0; d < 3; ++d) sL[d] = image_shift(g, sm.nb_img[nb], d);
 #pragma unroll 1
                     for (int k = 0; k < NI; ++k) {
-                        const float4 pi = lds4(&sm.i4[k]);
-                        const int si = __float_as_int(pi.w);
+                        const int si = __float_as_int(staged(sm.ipb, k, 1));
                         const bool ok = N3 ? (si < jlim) : (si != jexcl);
-                        const float dx = (pi.x + npx.x) + nlx.x;
-                        const float dy = (pi.y + npy.x) + nly.x;
-                        const float dz = (pi.z + npz.x) + nlz.x;
+                        const float dx = (staged(sm.ipa, k, 0) - pj[0]) - lj[0];
+                        const float dy = (staged(sm.ipa, k, 1) - pj[1]) - lj[1];
+                        const float dz = (staged(sm.ipb, k, 0) - pj[2]) - lj[2];
                         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                         if (valid && ok && r2 < rc2hi && !(r2 < rc2lo) && exact_inside(a, si, sj, sL)) {
                             const float inv = rcp_nr(r2);
@@ -479,9 +512,11 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
             az[2 * k] = az2[k].x; az[2 * k + 1] = az2[k].y;
         }
         write_i_chunk<true, NI, MODE>(a, sm, ax, ay, az, a0, i0, na, lane);
-        kahan_add(le.s6, e6.x + e6.y);
-        kahan_add(le.s12, e12.x + e12.y);
-        le.pairs += npair;
+        if (STATS) {
+            kahan_add(le.s6, e6.x + e6.y);
+            kahan_add(le.s12, e12.x + e12.y);
+            le.pairs += npair;
+        }
     }
 }
 
@@ -557,7 +592,7 @@ __device__ void run_task_fp64(const ForceArgs &a, WarpSmem<double> &sm, const Ta
     }
 }
 
-template <bool MIXED, int NI, int MODE>
+template <bool MIXED, int NI, int MODE, bool STATS>
 __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
     using T = typename std::conditional<MIXED, float, double>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -573,7 +608,7 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
     le.pairs = 0;
     for (int t = w; t < a.ntasks; t += W) {
         TaskCells tc = make_task<MODE>(a.g, a.group, a.colour, t);
-        if constexpr (MIXED) run_task_mixed<NI, MODE>(a, sm, tc, lane, le);
+        if constexpr (MIXED) run_task_mixed<NI, MODE, STATS>(a, sm, tc, lane, le);
         else run_task_fp64<NI, MODE>(a, sm, tc, lane, le);
     }
     // warp reduction of the energy partials in FP64, fixed order
@@ -586,7 +621,7 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
         s12 += __shfl_xor_sync(kFull, s12, m);
         np += __shfl_xor_sync(kFull, np, m);
     }
-    if (lane == 0) {
+    if (STATS && lane == 0) {
         a.warp_acc[4 * w + 0] += s6;
         a.warp_acc[4 * w + 1] += s12;
         a.warp_pairs[w] += np;
@@ -658,13 +693,13 @@ static size_t smem_bytes(int warps) {
 }
 
 // One resident wave: SMs x the blocks that fit on an SM (cached per shape).
-template <bool MIXED, int NI, int MODE>
+template <bool MIXED, int NI, int MODE, bool STATS>
 static int force_blocks(Ctx *c) {
     static int cache[17] = {0};
     const int warps = c->warps;
     if (!cache[warps]) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force<MIXED, NI, MODE>, warps * 32,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force<MIXED, NI, MODE, STATS>, warps * 32,
                                                       smem_bytes<MIXED, NI>(warps));
         if (per_sm < 1) per_sm = 1;
         cache[warps] = per_sm;
@@ -674,17 +709,24 @@ static int force_blocks(Ctx *c) {
     return blocks < maxb ? blocks : maxb;
 }
 
-template <bool MIXED, int NI, int MODE>
+template <bool MIXED, int NI, int MODE, bool STATS>
 static cudaError_t launch_one(Ctx *c, ForceArgs &a, cudaStream_t s) {
     const int warps = c->warps;
     const size_t sm = smem_bytes<MIXED, NI>(warps);
-    const int blocks = force_blocks<MIXED, NI, MODE>(c);
-    k_force<MIXED, NI, MODE><<<blocks, warps * 32, sm, s>>>(a);
+    const int blocks = force_blocks<MIXED, NI, MODE, STATS>(c);
+    k_force<MIXED, NI, MODE, STATS><<<blocks, warps * 32, sm, s>>>(a);
     return cudaGetLastError();
 }
 
+template <bool MIXED, int NI, int MODE>
+static cudaError_t launch_mode(Ctx *c, ForceArgs &a, cudaStream_t s, bool stats) {
+    // the FP64 comparator always accumulates its statistics
+    if (!MIXED || stats) return launch_one<MIXED, NI, MODE, true>(c, a, s);
+    return launch_one<MIXED, NI, MODE, (MIXED ? false : true)>(c, a, s);
+}
+
 template <bool MIXED, int NI>
-static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *launches) {
+static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *launches, bool stats) {
     ForceArgs a;
     a.g = c->g;
     a.p4 = c->d_p4;
@@ -694,6 +736,7 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
     a.kx = c->kx; a.ky = c->ky; a.kz = c->kz;
     a.warp_acc = c->d_warp_acc; a.warp_pairs = c->d_warp_pairs;
     a.group = 0; a.colour = 0;
+    a.stats = stats ? 1 : 0;
     for (int oi = 0; oi < 27; ++oi) {
         const int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, oi / 9 - 1};
         for (int d = 0; d < 3; ++d) {
@@ -718,7 +761,7 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
                 int raw = c->g.raw_of_colour[k];
                 a.ntasks = c->g.class_count[0][raw % 3] * c->g.class_count[1][(raw / 3) % 3] *
                            c->g.class_count[2][raw / 9];
-                e = launch_one<MIXED, NI, kColour>(c, a, s);
+                e = launch_mode<MIXED, NI, kColour>(c, a, s, stats);
                 if (e) return e;
                 ++*launches;
             }
@@ -731,38 +774,33 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
         e = cudaMemsetAsync(c->fx, 0, 3 * nbytes, s);
         if (e) return e;
         a.ntasks = c->g.ncell;
-        e = launch_one<MIXED, NI, kAtomic>(c, a, s);
+        e = launch_mode<MIXED, NI, kAtomic>(c, a, s, stats);
         ++*launches;
     } else {
         a.ntasks = c->g.ncell;
-        e = launch_one<MIXED, NI, kFullShell>(c, a, s);
+        e = launch_mode<MIXED, NI, kFullShell>(c, a, s, stats);
         ++*launches;
     }
     return e;
 }
 
-int force_grid_warps(const Ctx *c) {
-    // persistent-style grid: 16 resident warps per SM
-    int per_sm = 16;
-    int w = c->num_sms * per_sm;
-    w = (w / c->warps) * c->warps;
-    return w > 0 ? w : c->warps;
-}
+int force_grid_warps(const Ctx *c) { return c->nwarp_max; }
 
-cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launches) {
-    cudaError_t e = cudaMemsetAsync(c->d_warp_acc, 0, sizeof(double) * 4 * (size_t)c->nwarp_max, s);
-    if (e) return e;
-    e = cudaMemsetAsync(c->d_warp_pairs, 0, sizeof(long long) * (size_t)c->nwarp_max, s);
-    if (e) return e;
+cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launches, bool stats) {
+    cudaError_t e;
     const bool mixed = (c->prec == LC_PREC_MIXED);
-    switch (c->ni) {
-        case 8: e = mixed ? launch_sched<true, 8>(c, sched, s, launches) : launch_sched<false, 8>(c, sched, s, launches); break;
-        case 32: e = mixed ? launch_sched<true, 32>(c, sched, s, launches) : launch_sched<false, 32>(c, sched, s, launches); break;
-        default: e = mixed ? launch_sched<true, 16>(c, sched, s, launches) : launch_sched<false, 16>(c, sched, s, launches); break;
+    if (!mixed) stats = true;
+    if (stats) {
+        if ((e = cudaMemsetAsync(c->d_warp_acc, 0, sizeof(double) * 4 * (size_t)c->nwarp_max, s))) return e;
+        if ((e = cudaMemsetAsync(c->d_warp_pairs, 0, sizeof(long long) * (size_t)c->nwarp_max, s))) return e;
     }
+    if (c->ni == 8) e = mixed ? launch_sched<true, 8>(c, sched, s, launches, stats) : launch_sched<false, 8>(c, sched, s, launches, stats);
+    else e = mixed ? launch_sched<true, 16>(c, sched, s, launches, stats) : launch_sched<false, 16>(c, sched, s, launches, stats);
     if (e) return e;
-    e = launch_energy_reduce(c, s, sched == LC_SCHED_FULLSHELL);
-    ++*launches;
+    if (stats) {
+        e = launch_energy_reduce(c, s, sched == LC_SCHED_FULLSHELL);
+        ++*launches;
+    }
     return e;
 }
 
@@ -792,21 +830,21 @@ cudaError_t launch_schedule_check(Ctx *c, lc_schedule sched, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <bool MIXED, int NI>
+template <bool MIXED, int NI, bool STATS>
 static cudaError_t attrs_for() {
     cudaError_t e;
     const int bytes = (int)smem_bytes<MIXED, NI>(16);
-    if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kColour>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
-    if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kAtomic>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
-    return cudaFuncSetAttribute(k_force<MIXED, NI, kFullShell>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kColour, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kAtomic, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    return cudaFuncSetAttribute(k_force<MIXED, NI, kFullShell, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 // Opt the force kernels into the shared memory of the largest tile shape
 // (called once per context, before any stream capture).
 cudaError_t init_force_kernels() {
     cudaError_t e;
-    if ((e = attrs_for<true, 8>()) || (e = attrs_for<true, 16>()) || (e = attrs_for<true, 32>()) ||
-        (e = attrs_for<false, 8>()) || (e = attrs_for<false, 16>()) || (e = attrs_for<false, 32>()))
+    if ((e = attrs_for<true, 8, true>()) || (e = attrs_for<true, 16, true>()) || (e = attrs_for<true, 8, false>()) ||
+        (e = attrs_for<true, 16, false>()) || (e = attrs_for<false, 8, true>()) || (e = attrs_for<false, 16, true>()))
         return e;
     return cudaSuccess;
 }

@@ -77,6 +77,7 @@ struct Ctx {
     int *d_count;          // [ncell]
     int *d_start;          // [ncell + 1]
     int *d_src;            // slot -> index in the previous order
+    int *d_key;            // slot -> particle ID (before the final ranking)
     int *d_blocksums;      // scan partials
     int8_t *d_colour;      // [ncell]
     float4 *d_p4;          // FP32 cell-centre-local coordinates, sorted
@@ -105,7 +106,7 @@ struct Ctx {
 
 // ---- kernels / launchers (stream-ordered, return cudaError_t) -------------
 cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches);
-cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launches);
+cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launches, bool stats = true);
 cudaError_t launch_kick_drift(Ctx *c, double dt, cudaStream_t s);
 cudaError_t launch_kick(Ctx *c, double dt, cudaStream_t s);
 cudaError_t launch_kinetic(Ctx *c, cudaStream_t s);
