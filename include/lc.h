@@ -151,7 +151,7 @@ lc_status lc_schedule_check(lc_ctx *ctx, lc_schedule sched, int64_t *conflicts,
                             int64_t *coverage_errors, void *stream);
 
 /* Tile shape of the force kernels: ni = particles of the centre cell held
- * per warp (8 or 16), warps = warps per thread block (1 .. 16).  0 keeps
+ * per warp (8 or 16), warps = warps per thread block (1 .. 8).  0 keeps
  * the current value.  Used by the autotuner. */
 lc_status lc_set_tile(lc_ctx *ctx, int ni, int warps);
 

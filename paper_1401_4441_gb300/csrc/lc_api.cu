@@ -419,7 +419,7 @@ lc_status lc_schedule_check(lc_ctx *c, lc_schedule sched, int64_t *conflicts, in
 lc_status lc_set_tile(lc_ctx *c, int ni, int warps) {
     if (!c) return LC_ERR_INVALID_ARG;
     if (ni && ni != 8 && ni != 16) return LC_ERR_INVALID_ARG;
-    if (warps < 0 || warps > 16) return LC_ERR_INVALID_ARG;
+    if (warps < 0 || warps > 8) return LC_ERR_INVALID_ARG;   // 256-thread launch bound
     if (ni) c->ni = ni;
     if (warps) c->warps = warps;
     for (int k = 0; k < 6; ++k)
