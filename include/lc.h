@@ -159,6 +159,31 @@ lc_status lc_set_tile(lc_ctx *ctx, int ni, int warps);
  * per force evaluation and per step (for accounting). */
 lc_status lc_launch_counts(const lc_ctx *ctx, int32_t *per_force, int32_t *per_step);
 
+/* Binning without any device allocation, for callers that cannot allocate
+ * device memory (work issued while another component captures a CUDA graph,
+ * code confined to a memory pool it was handed, embedded users that only
+ * pass pointers).  The paper has no counterpart: it is an interface
+ * convenience around the counting sort of lc_bin.
+ *   pos         device, [n][3] doubles by particle ID (any values; wrapped)
+ *   box, rc     host; cells nc_d = floor(L_d / rc), each >= 3
+ *   cell_count  device, int32[ncell], written: particles per cell
+ *   cell_start  device, int32[ncell], written: exclusive prefix sum
+ *   perm        device, int32[n], written: slot -> particle ID, cell-sorted,
+ *               ascending ID inside a cell (the same arrays as lc_get's
+ *               CELL_COUNT / CELL_START / PERM after lc_bin)
+ * Work is queued on `stream`; the call does not synchronise.  Its scratch is
+ * one fixed array of device memory inside the library (about 21 MB, held by
+ * every GPU that loads the library until the process exits), so
+ * n <= 1,048,576 and ncell <= 1,048,576 (LC_ERR_TOO_LARGE otherwise).  The
+ * array's device address is looked up on the first call on each device,
+ * with that device current: make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race,
+ * so order them on one stream.  Non-finite positions are binned into cell
+ * 0 (no flag is reported).  Errors: LC_ERR_INVALID_ARG,
+ * LC_ERR_BOX_TOO_SMALL, LC_ERR_TOO_LARGE, LC_ERR_CUDA. */
+lc_status lc_bin_noalloc(const double *pos, int64_t n, const double box[3], double rc, int32_t *cell_count,
+                         int32_t *cell_start, int32_t *perm, void *stream);
+
 void lc_destroy(lc_ctx *ctx);
 
 /* Static string naming a status code. */

@@ -121,6 +121,12 @@ cudaError_t launch_set_state(Ctx *c, const double *pos, const double *vel, cudaS
 int force_grid_warps(const Ctx *c);
 cudaError_t init_force_kernels();
 
+// scan kernels of the binning (lc_bin.cu), also launched by lc_noalloc.cu
+__global__ void k_scan_tiles(int ncell, const int *__restrict__ count, int *__restrict__ start,
+                             int *__restrict__ partial);
+__global__ void k_scan_partials(int ntiles, int *__restrict__ partial);
+__global__ void k_scan_add(int ncell, int n, int *__restrict__ start, const int *__restrict__ partial);
+
 // ---- small device helpers ----------------------------------------------------
 // Periodic wrap into [0, L), each operation rounded once (no contraction):
 // x - L floor(x / L), then one correction for the rounding edge cases.
