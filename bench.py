@@ -205,10 +205,17 @@ def run_reference(args, dist):
 
 
 def workload_config(args, w):
-    nc = [int(math.floor(L / RC)) for L in w["box"]]
-    return {"workload": f"{args.workload}: N={w['pos'].shape[0]} FCC+jitter {inputs.WORKLOADS[args.workload]['jitter']}, "
-                        f"rho={w['rho']}, T={w['T']}, rc={RC}, cubic periodic L={w['box'][0]:.4f}, "
-                        f"cells {nc[0]}^3, dt={DT}",
+    rc = w["rc"]
+    nc = [int(math.floor(L / rc)) for L in w["box"]]
+    if inputs.WORKLOADS[args.workload].get("kind") == "slab":
+        desc = (f"{args.workload}: N={w['pos'].shape[0]} liquid slab 0.80 in x < Lx/3, vapour 0.02 elsewhere, "
+                f"uniform random positions, box {w['box'][0]:.2f} x {w['box'][1]:.2f} x {w['box'][2]:.2f}, "
+                f"rc={rc}, cells {nc[0]}x{nc[1]}x{nc[2]}; step = binning + one force evaluation")
+    else:
+        desc = (f"{args.workload}: N={w['pos'].shape[0]} FCC+jitter {inputs.WORKLOADS[args.workload]['jitter']}, "
+                f"rho={w['rho']}, T={w['T']}, rc={rc}, cubic periodic L={w['box'][0]:.4f}, "
+                f"cells {nc[0]}^3, dt={DT}")
+    return {"workload": desc,
             "particles": int(w["pos"].shape[0]), "cells": nc,
             "precision": args.precision if args.impl == "gb300" else "fp64 (oracle)",
             "schedule": args.schedule, "l2": "flushed (512 MiB memset) between timed iterations",
@@ -223,7 +230,7 @@ def run_profile(args, dist):
     build.build()
     from paper_1401_4441_gb300 import lc
     w = inputs.workload(args.workload)
-    g = lc.Box(w["box"], RC, w["pos"].shape[0], args.precision)
+    g = lc.Box(w["box"], w["rc"], w["pos"].shape[0], args.precision)
     g.set_state(torch.from_numpy(w["pos"]).cuda(), torch.from_numpy(w["vel"]).cuda())
     sched = "atomic" if args.schedule == "auto" else args.schedule
     g.forces(sched)
@@ -239,6 +246,97 @@ def run_profile(args, dist):
     g.close()
 
 
+def run_batch(args, dist):
+    """Batched configuration: 512 independent boxes (N log-uniform in
+    [500, 50000], density U[0.5, 0.9], T U[0.7, 1.2], FCC + jitter 0.05)
+    stepped together (one launch per stage for all boxes, two-step CUDA graph),
+    mixed precision; compared with the plain FP64 path that steps each box
+    alone (its own context, per-box launches)."""
+    import torch
+    from paper_1401_4441_gb300 import build
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    if dist.rank == 0:
+        build.build()
+    dist.barrier()
+    from paper_1401_4441_gb300 import lc
+    boxes = inputs.batch_boxes(seed=inputs.DEFAULT_SEED + 1000 * dist.rank)
+    pos = np.concatenate([b["pos"] for b in boxes])
+    vel = np.concatenate([b["vel"] for b in boxes])
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    g = lc.Batch([b["box"] for b in boxes], RC, [b["pos"].shape[0] for b in boxes], args.precision)
+    dpos, dvel = torch.from_numpy(pos).to(dev), torch.from_numpy(vel).to(dev)
+    sched_ms = {}
+    for sch in ("atomic", "fullshell"):
+        g.set_state(dpos, dvel)
+        g.forces(sch)
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream); g.forces(sch); e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        sched_ms[sch] = min(ts)
+    sched = min(sched_ms, key=sched_ms.get) if args.schedule in ("auto", "colour") else args.schedule
+    g.set_state(dpos, dvel)
+    g.forces(sched)
+    _, _, _, np0 = g.energies()
+    g.verlet(DT, max(2, args.warmup), sched)
+    torch.cuda.synchronize(dev)
+    calls = [2] * (args.steps // 2) + ([1] if args.steps % 2 else [])
+    clocks = ClockSampler(dist.local)
+    dist.barrier()
+    clocks.start()
+    time.sleep(0.3)
+    evs = []
+    for k in calls:
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream); g.verlet(DT, k, sched); e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = dist.max(sum(a.elapsed_time(b) for a, b in evs))
+    _, _, _, np1 = g.energies()
+    pairs = 0.5 * (np0.sum() + np1.sum()) * args.steps
+    value = dist.sum(pairs) / (ms * 1e-3)
+    per_force, per_step = g.launch_counts()
+    g.close()
+
+    # plain FP64 per-box path: every box alone, FP64, its own launches
+    fp64_steps = 2
+    t_fp64 = 0.0
+    pairs_fp64 = 0
+    for b in boxes:
+        gb = lc.Box(b["box"], RC, b["pos"].shape[0], "fp64")
+        gb.set_state(torch.from_numpy(b["pos"]).to(dev), torch.from_numpy(b["vel"]).to(dev))
+        gb.forces("atomic")
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream); gb.verlet(DT, fp64_steps, "atomic"); e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_fp64 += e0.elapsed_time(e1)
+        pairs_fp64 += gb.energy()[3] * fp64_steps
+        gb.close()
+    value_fp64 = pairs_fp64 / (t_fp64 * 1e-3)
+    if dist.rank == 0:
+        ns = [b["pos"].shape[0] for b in boxes]
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
+                "data": "synthetic",
+                "config": {"workload": f"batch512: 512 periodic cubic LJ boxes, N log-uniform in [500, 50000] "
+                                       f"(total {sum(ns)}), density U[0.5, 0.9], T U[0.7, 1.2], rc={RC}, "
+                                       f"FCC + jitter 0.05, dt={DT}", "boxes": len(ns), "particles": int(sum(ns)),
+                           "precision": args.precision, "l2": "flushed between timed iterations"},
+                "schedule": sched, "schedule_force_ms": sched_ms, "clocks": clk,
+                "fp64_per_box": {"value": value_fp64, "unit": UNIT, "ms_per_step": t_fp64 / fp64_steps,
+                                 "how": "each box alone in an FP64 context, atomic schedule, per-box launches"},
+                "vs_fp64_per_box": value / value_fp64, "gpu_launches": per_step * args.steps}
+        print(json.dumps(line), flush=True)
+
+
 def run_gb300(args, dist):
     import torch
     from paper_1401_4441_gb300 import build
@@ -252,37 +350,38 @@ def run_gb300(args, dist):
 
     w = inputs.workload(args.workload, seed=inputs.DEFAULT_SEED + dist.rank)
     pos, vel, box = w["pos"], w["vel"], w["box"]
+    rc = w["rc"]
+    forces_only = inputs.WORKLOADS[args.workload].get("kind") == "slab"
     n = pos.shape[0]
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    g = lc.Box(box, RC, n, args.precision)
+    g = lc.Box(box, rc, n, args.precision)
     dpos = torch.from_numpy(pos).to(dev)
     dvel = torch.from_numpy(vel).to(dev)
     g.set_state(dpos, dvel)
 
-    # schedule: measured, unless fixed on the command line
+    # schedule and tile shape: the autotuner's pick, unless fixed on the command line
+    from paper_1401_4441_gb300 import autotune
+    tuned = autotune.tune(g, use_cache=False)
     sched_ms = {}
-    for s in ("colour", "atomic", "fullshell"):
-        g.set_state(dpos, dvel)
-        g.bin()
-        g.forces(s)
-        ts = []
-        for _ in range(3):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            g.forces(s)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            ts.append(e0.elapsed_time(e1))
-        sched_ms[s] = min(ts)
-    sched = min(sched_ms, key=sched_ms.get) if args.schedule == "auto" else args.schedule
+    for row in tuned["table"]:
+        sched_ms[row["schedule"]] = min(sched_ms.get(row["schedule"], 1e30), row["ms"])
+    if args.schedule == "auto":
+        sched = tuned["schedule"]
+    else:
+        sched = args.schedule
+        best = min((r for r in tuned["table"] if r["schedule"] == sched), key=lambda r: r["ms"])
+        g.set_tile(best["ni"], best["warps"])
+    tile = {"ni": tuned["ni"], "warps": tuned["warps"]} if args.schedule == "auto" else {"ni": best["ni"], "warps": best["warps"]}
 
     g.set_state(dpos, dvel)
     g.forces(sched)
     _, _, _, npairs0 = g.energy()
     for _ in range((args.warmup + 1) // 2):
-        g.verlet(DT, 2, sched)
+        if forces_only:
+            g.forces(sched)
+        else:
+            g.verlet(DT, 2, sched)
     torch.cuda.synchronize(dev)
 
     # timed region: K steps in graph replays of two steps, L2 flushed between
@@ -297,7 +396,14 @@ def run_gb300(args, dist):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        g.verlet(DT, k, sched)
+        if forces_only:
+            # the slab's random start has near-overlaps: a step is binning +
+            # one force evaluation (no dynamics)
+            for _ in range(k):
+                g.set_state(dpos, dvel)
+                g.forces(sched)
+        else:
+            g.verlet(DT, k, sched)
         e1.record(stream)
         evs.append((e0, e1))
     torch.cuda.synchronize(dev)
@@ -312,6 +418,9 @@ def run_gb300(args, dist):
     value = total_pairs / (elapsed_ms * 1e-3)
 
     # dominant kernel: the force sweep of one evaluation (binned state, L2 flushed)
+    if forces_only:
+        g.set_state(dpos, dvel)
+        g.forces(sched)
     counts = g.get("cell_count")
     nc, _, _ = g.grid()
     cand = half_shell_candidates(counts, nc)
@@ -367,7 +476,7 @@ def run_gb300(args, dist):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
                 "data": "synthetic", "config": workload_config(args, w),
                 "steps_per_s": args.steps / (elapsed_ms * 1e-3) * dist.world,
-                "schedule": sched, "schedule_force_ms": sched_ms,
+                "schedule": sched, "schedule_force_ms": sched_ms, "tile": tile,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": per_step * args.steps}
         print(json.dumps(line), flush=True)
@@ -381,7 +490,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--schedule", default="auto", choices=["auto", "colour", "atomic", "fullshell"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="liquid1m", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--workload", default="liquid1m", choices=sorted(inputs.WORKLOADS) + ["batch512"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="only warm-up + timed steps of one schedule (for ncu captures)")
@@ -393,6 +502,8 @@ def main():
             run_reference(args, dist)
         elif args.profile:
             run_profile(args, dist)
+        elif args.workload == "batch512":
+            run_batch(args, dist)
         else:
             run_gb300(args, dist)
     finally:

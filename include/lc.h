@@ -159,6 +159,33 @@ lc_status lc_set_tile(lc_ctx *ctx, int ni, int warps);
  * per force evaluation and per step (for accounting). */
 lc_status lc_launch_counts(const lc_ctx *ctx, int32_t *per_force, int32_t *per_step);
 
+/* ---- batches of independent boxes --------------------------------------
+ * A batch context holds nbox independent periodic boxes (each with its own
+ * edges, cutoff and particle count) and runs every stage over all boxes in
+ * one launch: binning, the force sweep (atomic or full-shell schedule; the
+ * colour schedule is single-box only: LC_ERR_INVALID_ARG), integration.
+ * Particles are numbered box after box: box b owns IDs
+ * [n_0 + ... + n_{b-1}, ... + n_b).  lc_set_state, lc_forces,
+ * lc_verlet_step, lc_get (all but LC_GET_COLOUR) and lc_destroy take a batch
+ * context; lc_energy_virial returns sums over the boxes. */
+
+/* box: [nbox][3] edges, rc: [nbox] cutoffs, n: [nbox] particle counts
+ * (host arrays).  nbox <= 65535, total particles < 2^26.  Errors as
+ * lc_create. */
+lc_status lc_batch_create(int32_t nbox, const double *box, const double *rc, const int64_t *n,
+                          lc_precision prec, lc_ctx **out);
+
+/* Per-box energies of the current state into host arrays of nbox entries
+ * (any may be NULL): potential U and virial W of the last force evaluation,
+ * kinetic K, pairs inside r_c.  Synchronises the stream.  The per-box U and W
+ * are summed with FP64 atomics (order not fixed: the last bits may differ
+ * between runs). */
+lc_status lc_batch_energies(lc_ctx *ctx, double *u_pot, double *k_kin, double *virial, int64_t *npairs,
+                            void *stream);
+
+/* Number of boxes (0 for a single-box context), total particles, total cells. */
+lc_status lc_batch_info(const lc_ctx *ctx, int32_t *nbox, int64_t *total_particles, int64_t *total_cells);
+
 /* Binning without any device allocation, for callers that cannot allocate
  * device memory (work issued while another component captures a CUDA graph,
  * code confined to a memory pool it was handed, embedded users that only

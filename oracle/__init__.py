@@ -12,6 +12,7 @@ Functions (all FP64, positions indexed by particle ID):
   nsq_forces(x, y, z, L, rc)  -> (f[n,3], U, W, npairs)      O(N^2) minimum image
   lc_forces(x, y, z, L, rc)   -> (f[n,3], U, W, npairs)      serial link-cell, literature order
   forces_sample(..., ids)     -> (f[len(ids),3], nneigh)     per-particle sums
+  force_scale(x, y, z, L, rc) -> s[n]                       sum_j |F_ij| per particle
   verlet(xyz, v, L, rc, dt, nsteps) -> (xyz, v, f, energies[nsteps+1, 3])
   half_shell()                -> int[13,3]                   forward half-shell offsets
   offset_groups()             -> int[13]                     parity-pattern groups
@@ -52,6 +53,8 @@ def _load():
         lib.orc_verlet.argtypes = [ctypes.c_int64, dp, dp, dp, ctypes.c_int, dp,
                                    ctypes.c_double, ctypes.c_double, ctypes.c_int, dp]
         lib.orc_verlet.restype = ctypes.c_int
+        lib.orc_force_scale.argtypes = [ctypes.c_int64, dp, dp, dp, dp, ctypes.c_double, dp]
+        lib.orc_force_scale.restype = None
         lib.orc_half_shell.argtypes = [ip]
         lib.orc_half_shell.restype = None
         lib.orc_offset_groups.argtypes = [ip]
@@ -153,6 +156,15 @@ def forces_sample(x, y, z, L, rc, ids):
     if r:
         raise RuntimeError(f"orc_forces_sample failed ({r})")
     return f, nn
+
+
+def force_scale(x, y, z, L, rc):
+    """Per-particle sum of pair-force magnitudes, S_i = sum_j |F_ij|."""
+    lib = _load()
+    x, y, z, L = _f64(x), _f64(y), _f64(z), _box(L)
+    out = np.zeros(x.shape[0])
+    lib.orc_force_scale(x.shape[0], _d(x), _d(y), _d(z), _d(L), float(rc), _d(out))
+    return out
 
 
 def verlet(xyz, v, L, rc, dt, nsteps, f=None):

@@ -340,6 +340,59 @@ int orc_lc_forces(int64_t n, const double *x, const double *y, const double *z,
     return 0;
 }
 
+/* Pair-force scale of every particle: S_i = sum over j within r_c of
+ * |F_ij| (the magnitudes of the pair forces, not of their sum).  Any
+ * arithmetic that rounds each pair force to relative precision eps errs by
+ * at most about eps S_i on F_i, whatever cancellation the sum has; tests
+ * normalise force errors by it where forces cancel strongly.  scale: [n] by
+ * ID.  Same loops and pair test as orc_nsq_forces. */
+void orc_force_scale(int64_t n, const double *x, const double *y, const double *z,
+                     const double L[3], double rc, double *scale)
+{
+    double rc2 = rc * rc;
+    double *xw = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    int32_t nc[3];
+    orc_grid(L, rc, nc);
+    for (int64_t i = 0; i < n; ++i) {
+        xw[3 * i + 0] = orc_wrap(x[i], L[0]);
+        xw[3 * i + 1] = orc_wrap(y[i], L[1]);
+        xw[3 * i + 2] = orc_wrap(z[i], L[2]);
+        scale[i] = 0.0;
+    }
+    /* bucket by cell to keep it O(N) */
+    int64_t ncell = (int64_t)nc[0] * nc[1] * nc[2];
+    int32_t *head = (int32_t *)malloc(sizeof(int32_t) * (size_t)ncell);
+    int32_t *next = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t c = 0; c < ncell; ++c) head[c] = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t c3[3];
+        for (int d = 0; d < 3; ++d) c3[d] = cell_coord(xw[3 * i + d], nc[d], L[d]);
+        int32_t c = c3[0] + nc[0] * (c3[1] + nc[1] * c3[2]);
+        next[i] = head[c];
+        head[c] = (int32_t)i;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t ci[3];
+        for (int d = 0; d < 3; ++d) ci[d] = cell_coord(xw[3 * i + d], nc[d], L[d]);
+        for (int oz = -1; oz <= 1; ++oz)
+            for (int oy = -1; oy <= 1; ++oy)
+                for (int ox = -1; ox <= 1; ++ox) {
+                    int32_t c[3] = {ci[0] + ox, ci[1] + oy, ci[2] + oz};
+                    for (int d = 0; d < 3; ++d) { if (c[d] >= nc[d]) c[d] -= nc[d]; else if (c[d] < 0) c[d] += nc[d]; }
+                    for (int32_t j = head[c[0] + nc[0] * (c[1] + nc[1] * c[2])]; j >= 0; j = next[j]) {
+                        if (j == i) continue;
+                        double dx = min_image(xw[3 * i + 0], xw[3 * j + 0], L[0]);
+                        double dy = min_image(xw[3 * i + 1], xw[3 * j + 1], L[1]);
+                        double dz = min_image(xw[3 * i + 2], xw[3 * j + 2], L[2]);
+                        double fs, u, w;
+                        if (!lj_pair(dx, dy, dz, rc2, &fs, &u, &w)) continue;
+                        scale[i] += fabs(fs) * sqrt(dx * dx + dy * dy + dz * dz);
+                    }
+                }
+    }
+    free(head); free(next); free(xw);
+}
+
 /* Force on selected particles only (sampled checks at sizes where a full
  * sweep is too slow): for each requested ID, the sum over all j != i within
  * r_c, found by scanning the 27 cells around the particle's cell.  Same pair

@@ -88,6 +88,23 @@ void make_grid(Grid *g, const double box[3], double rc) {
     g->ncolours = r;
 }
 
+void make_box(BoxDev *b, const double box[3], double rc, int cell_off, int part_off, int n) {
+    make_grid(&b->g, box, rc);
+    for (int oi = 0; oi < 27; ++oi) {
+        const int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, oi / 9 - 1};
+        for (int d = 0; d < 3; ++d) {
+            const double S = (double)o[d] * b->g.h[d];
+            const float Sh = (float)S;
+            b->sh[oi][d] = Sh;
+            b->sl[oi][d] = (float)(S - (double)Sh);
+        }
+    }
+    b->cell_off = cell_off;
+    b->part_off = part_off;
+    b->n = n;
+    b->pad = 0;
+}
+
 }  // namespace lc
 
 using namespace lc;
@@ -121,11 +138,13 @@ static void free_ctx(Ctx *c) {
     void *ptrs[] = {c->cur.x, c->cur.vx, c->cur.id, c->nxt.x, c->nxt.vx, c->nxt.id, c->d_cell, c->d_rank,
                     c->d_count, c->d_start, c->d_src, c->d_key, c->d_blocksums, c->d_colour, c->d_p4, c->fx, c->kx,
                     c->d_warp_acc, c->d_warp_pairs, c->d_kin_part, c->d_result, c->d_npairs, c->d_err,
-                    c->d_stamp, c->d_visit, c->d_counters};
+                    c->d_stamp, c->d_visit, c->d_counters, c->d_boxes, c->d_cell_box, c->d_slot_box,
+                    c->d_box_acc, c->d_box_pairs, c->d_box_out};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k < 6; ++k)
         if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+    free(c->h_boxes);
     delete static_cast<lc_ctx *>(c);
 }
 
@@ -137,6 +156,46 @@ static cudaError_t alloc_state(State *st, int64_t n) {
     if ((e = dalloc(&vs, 3 * (size_t)n))) return e;
     st->vx = vs; st->vy = vs + n; st->vz = vs + 2 * n;
     return dalloc(&st->id, (size_t)n);
+}
+
+// Device buffers shared by single-box and batch contexts (c->n particles,
+// c->g.ncell cells in total).
+static cudaError_t alloc_common(Ctx *c) {
+    cudaError_t e;
+    Stencil st;
+    make_stencil(&st);
+    const int64_t n = c->n;
+    const size_t N = (size_t)n, NC = (size_t)c->g.ncell;
+    const int ntiles = (c->g.ncell + 4095) / 4096;
+    c->nwarp_max = c->num_sms * 64;
+    if ((e = upload_stencil(st)) || (e = alloc_state(&c->cur, n)) || (e = alloc_state(&c->nxt, n)) ||
+        (e = dalloc(&c->d_cell, N)) || (e = dalloc(&c->d_rank, N)) || (e = dalloc(&c->d_count, NC)) ||
+        (e = dalloc(&c->d_start, NC + 1)) || (e = dalloc(&c->d_src, N)) || (e = dalloc(&c->d_key, N)) ||
+        (e = dalloc(&c->d_blocksums, (size_t)ntiles + 1)) || (e = dalloc(&c->d_colour, NC)) ||
+        (e = dalloc(&c->d_p4, N)) || (e = dalloc(&c->fx, 3 * N)) || (e = dalloc(&c->kx, 3 * N)) ||
+        (e = dalloc(&c->d_warp_acc, 4 * (size_t)c->nwarp_max)) || (e = dalloc(&c->d_warp_pairs, (size_t)c->nwarp_max)) ||
+        (e = dalloc(&c->d_kin_part, (size_t)c->num_sms * 2)) || (e = dalloc(&c->d_result, 4)) ||
+        (e = dalloc(&c->d_npairs, 1)) || (e = dalloc(&c->d_err, 1)) || (e = dalloc(&c->d_stamp, NC)) ||
+        (e = dalloc(&c->d_visit, 27 * NC)) || (e = dalloc(&c->d_counters, 4)))
+        return e;
+    c->state_a = c->cur.x;
+    if ((e = init_force_kernels())) return e;
+    c->fy = c->fx + N; c->fz = c->fx + 2 * N;
+    c->ky = c->kx + N; c->kz = c->kx + 2 * N;
+    cudaStream_t s = 0;
+    if ((e = cudaMemsetAsync(c->d_err, 0, sizeof(int), s)) || (e = cudaMemsetAsync(c->d_result, 0, 4 * sizeof(double), s)) ||
+        (e = cudaMemsetAsync(c->fx, 0, 3 * N * sizeof(double), s)))
+        return e;
+    return cudaSuccess;
+}
+
+static lc_status read_err(lc_ctx *c, cudaStream_t s) {
+    int err = 0;
+    LC_TRY(cudaMemcpyAsync(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LC_TRY(cudaStreamSynchronize(s));
+    if (err & kErrNonfinite) return LC_ERR_NONFINITE;
+    if (err & kErrTimeout) return LC_ERR_TIMEOUT;
+    return LC_OK;
 }
 
 extern "C" {
@@ -179,37 +238,111 @@ lc_status lc_create(const double box[3], double rc, int64_t n, lc_precision prec
     cudaError_t e = cudaGetDevice(&dev);
     if (!e) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e) { cudaGetLastError(); free_ctx(c); return from_cuda(e); }
-    Stencil st;
-    make_stencil(&st);
-    const size_t N = (size_t)n, NC = (size_t)c->g.ncell;
-    const int ntiles = (c->g.ncell + 4095) / 4096;
-    c->nwarp_max = c->num_sms * 64;
-    if ((e = upload_stencil(st)) || (e = alloc_state(&c->cur, n)) || (e = alloc_state(&c->nxt, n)) ||
-        (e = dalloc(&c->d_cell, N)) || (e = dalloc(&c->d_rank, N)) || (e = dalloc(&c->d_count, NC)) ||
-        (e = dalloc(&c->d_start, NC + 1)) || (e = dalloc(&c->d_src, N)) || (e = dalloc(&c->d_key, N)) ||
-        (e = dalloc(&c->d_blocksums, (size_t)ntiles + 1)) || (e = dalloc(&c->d_colour, NC)) ||
-        (e = dalloc(&c->d_p4, N)) || (e = dalloc(&c->fx, 3 * N)) || (e = dalloc(&c->kx, 3 * N)) ||
-        (e = dalloc(&c->d_warp_acc, 4 * (size_t)c->nwarp_max)) || (e = dalloc(&c->d_warp_pairs, (size_t)c->nwarp_max)) ||
-        (e = dalloc(&c->d_kin_part, (size_t)c->num_sms * 2)) || (e = dalloc(&c->d_result, 4)) ||
-        (e = dalloc(&c->d_npairs, 1)) || (e = dalloc(&c->d_err, 1)) || (e = dalloc(&c->d_stamp, NC)) ||
-        (e = dalloc(&c->d_visit, 27 * NC)) || (e = dalloc(&c->d_counters, 4))) {
-        cudaGetLastError();
-        free_ctx(c);
-        return from_cuda(e);
-    }
-    c->state_a = c->cur.x;
-    if ((e = init_force_kernels())) { cudaGetLastError(); free_ctx(c); return from_cuda(e); }
-    c->fy = c->fx + N; c->fz = c->fx + 2 * N;
-    c->ky = c->kx + N; c->kz = c->kx + 2 * N;
-    cudaStream_t s = 0;
-    if ((e = cudaMemsetAsync(c->d_err, 0, sizeof(int), s)) || (e = cudaMemsetAsync(c->d_result, 0, 4 * sizeof(double), s)) ||
-        (e = cudaMemsetAsync(c->fx, 0, 3 * N * sizeof(double), s)) || (e = launch_colour(c, s)) ||
-        (e = cudaStreamSynchronize(s))) {
+    cudaError_t e2 = alloc_common(c);
+    if (e2) { cudaGetLastError(); free_ctx(c); return from_cuda(e2); }
+    if ((e = launch_colour(c, 0)) || (e = cudaStreamSynchronize(0))) {
         cudaGetLastError();
         free_ctx(c);
         return from_cuda(e);
     }
     *out = c;
+    return LC_OK;
+}
+
+lc_status lc_batch_create(int32_t nbox, const double *box, const double *rc, const int64_t *n, lc_precision prec,
+                          lc_ctx **out) {
+    if (!out) return LC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (nbox <= 0 || !box || !rc || !n || (prec != LC_PREC_FP64 && prec != LC_PREC_MIXED)) return LC_ERR_INVALID_ARG;
+    if (nbox > 65535) return LC_ERR_TOO_LARGE;
+    int64_t ntot = 0;
+    double ctot = 0.0;
+    for (int b = 0; b < nbox; ++b) {
+        if (!(rc[b] > 0.0) || n[b] < 0) return LC_ERR_INVALID_ARG;
+        for (int d = 0; d < 3; ++d) {
+            if (!(box[3 * b + d] > 0.0) || !isfinite(box[3 * b + d])) return LC_ERR_INVALID_ARG;
+            if (floor(box[3 * b + d] / rc[b]) < 3.0) return LC_ERR_BOX_TOO_SMALL;
+        }
+        ntot += n[b];
+        ctot += floor(box[3 * b] / rc[b]) * floor(box[3 * b + 1] / rc[b]) * floor(box[3 * b + 2] / rc[b]);
+    }
+    if (ntot >= kMaxParticles || ctot > 1.0e9) return LC_ERR_TOO_LARGE;
+
+    lc_ctx *c = new lc_ctx();
+    memset(static_cast<Ctx *>(c), 0, sizeof(Ctx));
+    c->nbox = nbox;
+    c->h_boxes = (BoxDev *)calloc((size_t)nbox, sizeof(BoxDev));
+    if (!c->h_boxes) { delete c; return LC_ERR_OOM; }
+    int coff = 0, poff = 0;
+    for (int b = 0; b < nbox; ++b) {
+        make_box(&c->h_boxes[b], box + 3 * b, rc[b], coff, poff, (int)n[b]);
+        coff += c->h_boxes[b].g.ncell;
+        poff += (int)n[b];
+    }
+    c->g = c->h_boxes[0].g;   // scalar fields of box 0; totals below
+    c->g.ncell = coff;
+    c->n = ntot;
+    c->prec = prec;
+    c->ni = 16;
+    c->warps = 8;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!e) e = alloc_common(c);
+    if (!e) e = dalloc(&c->d_boxes, (size_t)nbox);
+    if (!e) e = dalloc(&c->d_cell_box, (size_t)coff);
+    if (!e) e = dalloc(&c->d_slot_box, (size_t)(ntot > 0 ? ntot : 1));
+    if (!e) e = dalloc(&c->d_box_acc, 2 * (size_t)nbox);
+    if (!e) e = dalloc(&c->d_box_pairs, (size_t)nbox);
+    if (!e) e = dalloc(&c->d_box_out, 4 * (size_t)nbox);
+    if (e) { cudaGetLastError(); free_ctx(c); return from_cuda(e); }
+    unsigned short *cb = (unsigned short *)malloc(sizeof(unsigned short) * (size_t)(coff > 0 ? coff : 1));
+    unsigned short *sb = (unsigned short *)malloc(sizeof(unsigned short) * (size_t)(ntot > 0 ? ntot : 1));
+    if (!cb || !sb) { free(cb); free(sb); free_ctx(c); return LC_ERR_OOM; }
+    for (int b = 0; b < nbox; ++b) {
+        const BoxDev &bd = c->h_boxes[b];
+        for (int k = 0; k < bd.g.ncell; ++k) cb[bd.cell_off + k] = (unsigned short)b;
+        for (int k = 0; k < bd.n; ++k) sb[bd.part_off + k] = (unsigned short)b;
+    }
+    e = cudaMemcpy(c->d_boxes, c->h_boxes, sizeof(BoxDev) * (size_t)nbox, cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(c->d_cell_box, cb, sizeof(unsigned short) * (size_t)coff, cudaMemcpyHostToDevice);
+    if (!e && ntot > 0) e = cudaMemcpy(c->d_slot_box, sb, sizeof(unsigned short) * (size_t)ntot, cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemset(c->d_box_out, 0, sizeof(double) * 4 * (size_t)nbox);
+    free(cb);
+    free(sb);
+    if (e) { cudaGetLastError(); free_ctx(c); return from_cuda(e); }
+    *out = c;
+    return LC_OK;
+}
+
+lc_status lc_batch_energies(lc_ctx *c, double *u_pot, double *k_kin, double *virial, int64_t *npairs, void *stream) {
+    if (!c || c->nbox <= 0) return LC_ERR_INVALID_ARG;
+    if (!c->have_state) return LC_ERR_STATE;
+    if ((u_pot || virial || npairs) && !c->forces_valid) return LC_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    LC_TRY(launch_box_kinetic(c, s));
+    double *h = (double *)malloc(sizeof(double) * 4 * (size_t)c->nbox);
+    if (!h) return LC_ERR_OOM;
+    cudaError_t e = cudaMemcpyAsync(h, c->d_box_out, sizeof(double) * 4 * (size_t)c->nbox, cudaMemcpyDeviceToHost, s);
+    lc_status st = e ? from_cuda(e) : read_err(c, s);
+    if (st == LC_OK) {
+        for (int b = 0; b < c->nbox; ++b) {
+            if (u_pot) u_pot[b] = h[4 * b + 0];
+            if (virial) virial[b] = h[4 * b + 1];
+            if (npairs) npairs[b] = (int64_t)h[4 * b + 2];
+            if (k_kin) k_kin[b] = h[4 * b + 3];
+        }
+    }
+    free(h);
+    cudaGetLastError();
+    return st;
+}
+
+lc_status lc_batch_info(const lc_ctx *c, int32_t *nbox, int64_t *total_particles, int64_t *total_cells) {
+    if (!c) return LC_ERR_INVALID_ARG;
+    if (nbox) *nbox = c->nbox;
+    if (total_particles) *total_particles = c->n;
+    if (total_cells) *total_cells = c->g.ncell;
     return LC_OK;
 }
 
@@ -264,6 +397,7 @@ static lc_status do_forces(lc_ctx *c, lc_schedule sched, cudaStream_t s, int *la
 
 lc_status lc_forces(lc_ctx *c, lc_schedule sched, void *stream) {
     if (!c || sched < LC_SCHED_COLOUR || sched > LC_SCHED_FULLSHELL) return LC_ERR_INVALID_ARG;
+    if (c->nbox > 0 && sched == LC_SCHED_COLOUR) return LC_ERR_INVALID_ARG;
     if (!c->have_state) return LC_ERR_STATE;
     int launches = 0;
     lc_status st = do_forces(c, sched, (cudaStream_t)stream, &launches);
@@ -289,6 +423,7 @@ static cudaError_t step_launches(lc_ctx *c, double dt, lc_schedule sched, cudaSt
 lc_status lc_verlet_step(lc_ctx *c, double dt, int nsteps, lc_schedule sched, void *stream) {
     if (!c || nsteps < 0 || !isfinite(dt) || sched < LC_SCHED_COLOUR || sched > LC_SCHED_FULLSHELL)
         return LC_ERR_INVALID_ARG;
+    if (c->nbox > 0 && sched == LC_SCHED_COLOUR) return LC_ERR_INVALID_ARG;
     if (!c->have_state) return LC_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     int launches = 0;
@@ -336,20 +471,30 @@ lc_status lc_verlet_step(lc_ctx *c, double dt, int nsteps, lc_schedule sched, vo
     return LC_OK;
 }
 
-static lc_status read_err(lc_ctx *c, cudaStream_t s) {
-    int err = 0;
-    LC_TRY(cudaMemcpyAsync(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    LC_TRY(cudaStreamSynchronize(s));
-    if (err & kErrNonfinite) return LC_ERR_NONFINITE;
-    if (err & kErrTimeout) return LC_ERR_TIMEOUT;
-    return LC_OK;
-}
 
 lc_status lc_energy_virial(lc_ctx *c, double *u_pot, double *k_kin, double *virial, int64_t *npairs, void *stream) {
     if (!c) return LC_ERR_INVALID_ARG;
     if (!c->have_state) return LC_ERR_STATE;
     if ((u_pot || virial || npairs) && !c->forces_valid) return LC_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
+    if (c->nbox > 0) {   // a batch: sums over its boxes
+        double *u = (double *)malloc(sizeof(double) * 4 * (size_t)c->nbox);
+        if (!u) return LC_ERR_OOM;
+        double *k = u + c->nbox, *w = u + 2 * c->nbox;
+        int64_t *p = (int64_t *)(u + 3 * c->nbox);
+        lc_status st = lc_batch_energies(c, u, k, w, p, stream);
+        if (st == LC_OK) {
+            double su = 0, sk = 0, sw = 0;
+            int64_t sp = 0;
+            for (int b = 0; b < c->nbox; ++b) { su += u[b]; sk += k[b]; sw += w[b]; sp += p[b]; }
+            if (u_pot) *u_pot = su;
+            if (k_kin) *k_kin = sk;
+            if (virial) *virial = sw;
+            if (npairs) *npairs = sp;
+        }
+        free(u);
+        return st;
+    }
     LC_TRY(launch_kinetic(c, s));
     double r[4];
     long long np = 0;
@@ -374,7 +519,7 @@ lc_status lc_get(lc_ctx *c, lc_get_what what, void *dst, int on_device, void *st
         case LC_GET_CELL_COUNT: if (!c->binned) return LC_ERR_STATE; src = c->d_count; bytes = 4 * NC; break;
         case LC_GET_CELL_START: if (!c->binned) return LC_ERR_STATE; src = c->d_start; bytes = 4 * NC; break;
         case LC_GET_PERM: if (!c->binned) return LC_ERR_STATE; src = c->cur.id; bytes = 4 * N; break;
-        case LC_GET_COLOUR: src = c->d_colour; bytes = NC; break;
+        case LC_GET_COLOUR: if (c->nbox > 0) return LC_ERR_INVALID_ARG; src = c->d_colour; bytes = NC; break;
         case LC_GET_FORCES:
         case LC_GET_POS:
         case LC_GET_VEL: {
@@ -405,7 +550,7 @@ lc_status lc_grid(const lc_ctx *c, int32_t nc[3], int32_t *ncolours, int32_t *np
 }
 
 lc_status lc_schedule_check(lc_ctx *c, lc_schedule sched, int64_t *conflicts, int64_t *coverage_errors, void *stream) {
-    if (!c || sched < LC_SCHED_COLOUR || sched > LC_SCHED_FULLSHELL) return LC_ERR_INVALID_ARG;
+    if (!c || sched < LC_SCHED_COLOUR || sched > LC_SCHED_FULLSHELL || c->nbox > 0) return LC_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     LC_TRY(launch_schedule_check(c, sched, s));
     unsigned long long cnt[4];

@@ -25,15 +25,20 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-__global__ void k_cellid(Grid g, int n, const double *__restrict__ x, const double *__restrict__ y,
-                         const double *__restrict__ z, int *__restrict__ cell, int *__restrict__ rank,
-                         int *__restrict__ count, int *__restrict__ err) {
+// BATCHED: slot s belongs to box slot_box[s] (boxes keep their slot ranges),
+// whose grid gives the local cell; the global cell adds the box's offset.
+template <bool BATCHED>
+__global__ void k_cellid(Grid g1, const BoxDev *__restrict__ boxes, const unsigned short *__restrict__ slot_box, int n,
+                         const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+                         int *__restrict__ cell, int *__restrict__ rank, int *__restrict__ count, int *__restrict__ err) {
     const int lane = threadIdx.x & 31;
     for (int s0 = blockIdx.x * blockDim.x; s0 < n; s0 += gridDim.x * blockDim.x) {
         const int s = s0 + threadIdx.x;
         const bool act = s < n;
         int c = 0;
         if (act) {
+            const BoxDev *bd = BATCHED ? &boxes[slot_box[s]] : nullptr;
+            const Grid &g = BATCHED ? bd->g : g1;
             const double X[3] = {x[s], y[s], z[s]};
             int cc[3];
             bool fast = true;
@@ -52,6 +57,7 @@ __global__ void k_cellid(Grid g, int n, const double *__restrict__ x, const doub
             } else {
                 atomicOr(err, kErrNonfinite);
             }
+            if (BATCHED) c += bd->cell_off;
         }
         // lanes of a warp mostly share cells (the previous order is cell
         // sorted): one atomic per distinct cell, ranks by lane order
@@ -167,7 +173,9 @@ __global__ void k_scatter(int n, const int *__restrict__ cell, const int *__rest
 // One thread per slot t of the new order.  Rank = number of the cell's
 // particles with a smaller ID (IDs are unique), so slot = start + rank is
 // stable by ID whatever order the atomics were served in.
-__global__ void k_rank_gather(Grid g, int n, int write_p4, const int *__restrict__ start,
+template <bool BATCHED>
+__global__ void k_rank_gather(Grid g1, const BoxDev *__restrict__ boxes, const unsigned short *__restrict__ slot_box,
+                              int n, int write_p4, const int *__restrict__ start,
                               const int *__restrict__ count, const int *__restrict__ cell,
                               const int *__restrict__ src, const int *__restrict__ key, State in, State out,
                               float4 *__restrict__ p4) {
@@ -179,10 +187,13 @@ __global__ void k_rank_gather(Grid g, int n, int write_p4, const int *__restrict
         int r = 0;
         for (int k = 0; k < cnt; ++k) r += (key[base + k] < my_id) ? 1 : 0;
         const int dst = base + r;
+        const BoxDev *bd = BATCHED ? &boxes[slot_box[t]] : nullptr;
+        const Grid &g = BATCHED ? bd->g : g1;
+        const int cl = BATCHED ? c - bd->cell_off : c;
         int cc[3];
-        cc[0] = c % g.nc[0];
-        cc[1] = (c / g.nc[0]) % g.nc[1];
-        cc[2] = c / (g.nc[0] * g.nc[1]);
+        cc[0] = cl % g.nc[0];
+        cc[1] = (cl / g.nc[0]) % g.nc[1];
+        cc[2] = cl / (g.nc[0] * g.nc[1]);
         double X[3] = {in.x[s], in.y[s], in.z[s]};
         Split sp[3];
         bool fast = true;
@@ -248,8 +259,12 @@ cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches) {
     cudaError_t e = cudaMemsetAsync(c->d_count, 0, sizeof(int) * (size_t)ncell, s);
     if (e) return e;
     if (n > 0) {
-        k_cellid<<<grid_n, 256, 0, s>>>(c->g, n, c->cur.x, c->cur.y, c->cur.z, c->d_cell, c->d_rank,
-                                        c->d_count, c->d_err);
+        if (c->nbox > 0)
+            k_cellid<true><<<grid_n, 256, 0, s>>>(c->g, c->d_boxes, c->d_slot_box, n, c->cur.x, c->cur.y, c->cur.z,
+                                                  c->d_cell, c->d_rank, c->d_count, c->d_err);
+        else
+            k_cellid<false><<<grid_n, 256, 0, s>>>(c->g, nullptr, nullptr, n, c->cur.x, c->cur.y, c->cur.z, c->d_cell,
+                                                   c->d_rank, c->d_count, c->d_err);
         ++*launches;
     }
     k_scan_tiles<<<ntiles, kScanThreads, 0, s>>>(ncell, c->d_count, c->d_start, c->d_blocksums);
@@ -258,8 +273,14 @@ cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches) {
     *launches += 3;
     if (n > 0) {
         k_scatter<<<grid_n, 256, 0, s>>>(n, c->d_cell, c->d_rank, c->d_start, c->cur.id, c->d_src, c->d_key);
-        k_rank_gather<<<grid_n, 256, 0, s>>>(c->g, n, c->prec == LC_PREC_MIXED, c->d_start, c->d_count, c->d_cell,
-                                             c->d_src, c->d_key, c->cur, c->nxt, c->d_p4);
+        if (c->nbox > 0)
+            k_rank_gather<true><<<grid_n, 256, 0, s>>>(c->g, c->d_boxes, c->d_slot_box, n, c->prec == LC_PREC_MIXED,
+                                                       c->d_start, c->d_count, c->d_cell, c->d_src, c->d_key, c->cur,
+                                                       c->nxt, c->d_p4);
+        else
+            k_rank_gather<false><<<grid_n, 256, 0, s>>>(c->g, nullptr, nullptr, n, c->prec == LC_PREC_MIXED, c->d_start,
+                                                        c->d_count, c->d_cell, c->d_src, c->d_key, c->cur, c->nxt,
+                                                        c->d_p4);
         *launches += 2;
     }
     e = cudaGetLastError();
@@ -281,10 +302,12 @@ __global__ void k_iota(int n, int *id) {
 }
 
 // dst[id[s]] = (a[s], b[s], c[s]); wrap != 0 wraps positions into [0, L).
-__global__ void k_unsort_vec(int n, Grid g, int wrap, const int *__restrict__ id, const double *__restrict__ a,
+__global__ void k_unsort_vec(int n, Grid g1, const BoxDev *__restrict__ boxes, const unsigned short *__restrict__ slot_box,
+                             int wrap, const int *__restrict__ id, const double *__restrict__ a,
                              const double *__restrict__ b, const double *__restrict__ cc, double *__restrict__ dst) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         double va = a[s], vb = b[s], vc = cc[s];
+        const Grid &g = boxes ? boxes[slot_box[s]].g : g1;
         if (wrap) {
             va = wrap_coord(va, g.L[0]); vb = wrap_coord(vb, g.L[1]); vc = wrap_coord(vc, g.L[2]);
         }
@@ -313,7 +336,8 @@ cudaError_t launch_unsort_vec(Ctx *c, const double *a, const double *b, const do
                               cudaStream_t s, int wrap) {
     const int n = (int)c->n;
     if (n == 0) return cudaSuccess;
-    k_unsort_vec<<<c->num_sms * 8, 256, 0, s>>>(n, c->g, wrap, c->cur.id, a, b, cc, dst);
+    k_unsort_vec<<<c->num_sms * 8, 256, 0, s>>>(n, c->g, c->nbox > 0 ? c->d_boxes : nullptr, c->d_slot_box, wrap,
+                                                 c->cur.id, a, b, cc, dst);
     return cudaGetLastError();
 }
 

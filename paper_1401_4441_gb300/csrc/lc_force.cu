@@ -59,14 +59,24 @@ struct ForceArgs {
     int stats;                  // accumulate energy, virial and pair count
     float sh[27][3];            // o * h rounded to FP32, offset index (ox+1) + 3 (oy+1) + 9 (oz+1)
     float sl[27][3];            // o * h - sh, rounded to FP32
+    // batch of boxes (BATCHED kernels): per-box grids, box of every global
+    // cell, per-box statistics accumulators
+    const BoxDev *boxes;
+    const unsigned short *cell_box;
+    double *box_acc;
+    unsigned long long *box_pairs;
 };
 
 // ---------------------------------------------------------------- tasks ----
 struct TaskCells {
-    int A;            // centre cell
-    int cA[3];        // its coordinates
+    int A;            // centre cell (global index)
+    int cA[3];        // its coordinates in its box
     int nnb;          // neighbour cells listed (self first when present)
     bool self;        // intra-cell interaction included
+    const Grid *g;    // the box's grid
+    const float (*sh)[3], (*sl)[3];   // the box's shift tables
+    int cell_off;     // first global cell of the box
+    int box;
 };
 
 __device__ __forceinline__ void cell_xyz(const Grid &g, int c, int out[3]) {
@@ -109,9 +119,10 @@ __device__ __forceinline__ void task_offset(int group, int k, bool self, int o[3
     }
 }
 
+// Single-box task t: the cell (colour schedule: the t-th cell of the phase's
+// colour) and its neighbour count; used by the force and check kernels.
 template <int MODE>
-__device__ __forceinline__ TaskCells make_task(const Grid &g, int group, int colour, int t) {
-    TaskCells tc;
+__device__ __forceinline__ void single_task(const Grid &g, int group, int colour, int t, TaskCells &tc) {
     if (MODE == kColour) {
         tc.A = colour_task_cell(g, colour, t, tc.cA);
         tc.self = (group == 0);
@@ -121,6 +132,24 @@ __device__ __forceinline__ TaskCells make_task(const Grid &g, int group, int col
         cell_xyz(g, t, tc.cA);
         tc.self = true;
         tc.nnb = (MODE == kFullShell) ? 27 : 14;
+    }
+}
+
+template <int MODE, bool BATCHED>
+__device__ __forceinline__ TaskCells make_task(const ForceArgs &a, int t) {
+    TaskCells tc;
+    if constexpr (BATCHED) {
+        // task t = global cell t of the batch (atomic and full-shell schedules)
+        const int box = a.cell_box[t];
+        const BoxDev &bd = a.boxes[box];
+        tc.g = &bd.g; tc.sh = bd.sh; tc.sl = bd.sl; tc.cell_off = bd.cell_off; tc.box = box;
+        tc.A = t;
+        cell_xyz(bd.g, t - bd.cell_off, tc.cA);
+        tc.self = true;
+        tc.nnb = (MODE == kFullShell) ? 27 : 14;
+    } else {
+        tc.g = &a.g; tc.sh = a.sh; tc.sl = a.sl; tc.cell_off = 0; tc.box = 0;
+        single_task<MODE>(a.g, a.group, a.colour, t, tc);
     }
     return tc;
 }
@@ -227,12 +256,12 @@ __device__ __forceinline__ void write_force(const ForceArgs &a, int slot, T vx, 
 }
 
 // Exact FP64 cutoff decision, the definition's arithmetic (each op rounded once).
-__device__ __forceinline__ bool exact_inside(const ForceArgs &a, int si, int sj, const double sL[3]) {
+__device__ __forceinline__ bool exact_inside(const ForceArgs &a, double rc2, int si, int sj, const double sL[3]) {
     double dx = __dsub_rn(__dsub_rn(a.x[si], a.x[sj]), sL[0]);
     double dy = __dsub_rn(__dsub_rn(a.y[si], a.y[sj]), sL[1]);
     double dz = __dsub_rn(__dsub_rn(a.z[si], a.z[sj]), sL[2]);
     double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    return r2 < a.g.rc2;
+    return r2 < rc2;
 }
 
 // --------------------------------------------------------- the kernel -----
@@ -271,7 +300,7 @@ __device__ __forceinline__ JLoad load_j(const ForceArgs &a, const int *jl, int e
 template <bool MIXED, int MODE>
 __device__ __forceinline__ void setup_neighbours(const ForceArgs &a, WarpSmem<typename std::conditional<MIXED, float, double>::type> &sm,
                                                  const TaskCells &tc, int lane) {
-    const Grid &g = a.g;
+    const Grid &g = *tc.g;
     // neighbour table: lane k fills entry k (no FP64: shifts come from the
     // per-offset tables, the periodic image is kept as a code)
     if (lane < tc.nnb) {
@@ -288,11 +317,11 @@ __device__ __forceinline__ void setup_neighbours(const ForceArgs &a, WarpSmem<ty
         }
         const int oi = (o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1);
         for (int d = 0; d < 3; ++d) {
-            sm.nb_sh[lane][d] = a.sh[oi][d];
-            sm.nb_sl[lane][d] = a.sl[oi][d];
+            sm.nb_sh[lane][d] = tc.sh[oi][d];
+            sm.nb_sl[lane][d] = tc.sl[oi][d];
         }
         sm.nb_img[lane] = img;
-        const int B = c[0] + g.nc[0] * (c[1] + g.nc[1] * c[2]);
+        const int B = tc.cell_off + c[0] + g.nc[0] * (c[1] + g.nc[1] * c[2]);
         sm.nb_start[lane] = a.start[B];
         sm.nb_count[lane] = a.count[B];
     }
@@ -403,10 +432,26 @@ __device__ __forceinline__ float staged(const float4 *arr, int k, int comp) {
 
 // Mixed precision: FP32 pair arithmetic, two centre-cell particles per
 // packed f32x2 operation (the lane's j is the same for both).
-template <int NI, int MODE, bool STATS>
+// Per-box statistics of one i chunk (batched kernels): warp sums, one set
+// of FP64 / integer atomics per chunk into the box's accumulators.
+__device__ __forceinline__ void box_stats(const ForceArgs &a, int box, double s6, double s12, long long np) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        s6 += __shfl_xor_sync(kFull, s6, m);
+        s12 += __shfl_xor_sync(kFull, s12, m);
+        np += __shfl_xor_sync(kFull, np, m);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(a.box_acc + 2 * box + 0, s6);
+        atomicAdd(a.box_acc + 2 * box + 1, s12);
+        atomicAdd(a.box_pairs + box, (unsigned long long)np);
+    }
+}
+
+template <int NI, int MODE, bool STATS, bool BATCHED>
 __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const TaskCells &tc, int lane, LaneEnergy &le) {
     constexpr bool N3 = (MODE != kFullShell);
-    const Grid &g = a.g;
+    const Grid &g = *tc.g;
     setup_neighbours<true, MODE>(a, sm, tc, lane);
     const int a0 = a.start[tc.A];
     const int na = a.count[tc.A];
@@ -486,7 +531,7 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
                         const float dy = (staged(sm.ipa, k, 1) - pj[1]) - lj[1];
                         const float dz = (staged(sm.ipb, k, 0) - pj[2]) - lj[2];
                         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        if (valid && ok && r2 < rc2hi && !(r2 < rc2lo) && exact_inside(a, si, sj, sL)) {
+                        if (valid && ok && r2 < rc2hi && !(r2 < rc2lo) && exact_inside(a, g.rc2, si, sj, sL)) {
                             const float inv = rcp_nr(r2);
                             const float s6 = inv * inv * inv;
                             const float f = (s6 * inv) * fmaf(48.0f, s6, -24.0f);
@@ -513,18 +558,23 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
         }
         write_i_chunk<true, NI, MODE>(a, sm, ax, ay, az, a0, i0, na, lane);
         if (STATS) {
-            kahan_add(le.s6, e6.x + e6.y);
-            kahan_add(le.s12, e12.x + e12.y);
-            le.pairs += npair;
+            if constexpr (BATCHED) {
+                box_stats(a, tc.box, f32_to_f64_bits(e6.x) + f32_to_f64_bits(e6.y),
+                          f32_to_f64_bits(e12.x) + f32_to_f64_bits(e12.y), npair);
+            } else {
+                kahan_add(le.s6, e6.x + e6.y);
+                kahan_add(le.s12, e12.x + e12.y);
+                le.pairs += npair;
+            }
         }
     }
 }
 
 // FP64: the definition's arithmetic in double precision throughout.
-template <int NI, int MODE>
+template <int NI, int MODE, bool BATCHED>
 __device__ void run_task_fp64(const ForceArgs &a, WarpSmem<double> &sm, const TaskCells &tc, int lane, LaneEnergy &le) {
     constexpr bool N3 = (MODE != kFullShell);
-    const Grid &g = a.g;
+    const Grid &g = *tc.g;
     setup_neighbours<false, MODE>(a, sm, tc, lane);
     const int a0 = a.start[tc.A];
     const int na = a.count[tc.A];
@@ -586,13 +636,17 @@ __device__ void run_task_fp64(const ForceArgs &a, WarpSmem<double> &sm, const Ta
             __syncwarp();
         }
         write_i_chunk<false, NI, MODE>(a, sm, ax, ay, az, a0, i0, na, lane);
-        le.d6 += e6;
-        le.d12 += e12;
-        le.pairs += npair;
+        if constexpr (BATCHED) {
+            box_stats(a, tc.box, e6, e12, npair);
+        } else {
+            le.d6 += e6;
+            le.d12 += e12;
+            le.pairs += npair;
+        }
     }
 }
 
-template <bool MIXED, int NI, int MODE, bool STATS>
+template <bool MIXED, int NI, int MODE, bool STATS, bool BATCHED>
 __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
     using T = typename std::conditional<MIXED, float, double>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -607,9 +661,9 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
     le.d6 = le.d12 = 0.0;
     le.pairs = 0;
     for (int t = w; t < a.ntasks; t += W) {
-        TaskCells tc = make_task<MODE>(a.g, a.group, a.colour, t);
-        if constexpr (MIXED) run_task_mixed<NI, MODE, STATS>(a, sm, tc, lane, le);
-        else run_task_fp64<NI, MODE>(a, sm, tc, lane, le);
+        TaskCells tc = make_task<MODE, BATCHED>(a, t);
+        if constexpr (MIXED) run_task_mixed<NI, MODE, STATS, BATCHED>(a, sm, tc, lane, le);
+        else run_task_fp64<NI, MODE, BATCHED>(a, sm, tc, lane, le);
     }
     // warp reduction of the energy partials in FP64, fixed order
     double s6 = MIXED ? (f32_to_f64_bits(le.s6.x) - f32_to_f64_bits(le.s6.y)) : le.d6;
@@ -621,7 +675,7 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
         s12 += __shfl_xor_sync(kFull, s12, m);
         np += __shfl_xor_sync(kFull, np, m);
     }
-    if (STATS && lane == 0) {
+    if (STATS && !BATCHED && lane == 0) {
         a.warp_acc[4 * w + 0] += s6;
         a.warp_acc[4 * w + 1] += s12;
         a.warp_pairs[w] += np;
@@ -647,7 +701,8 @@ template <int MODE>
 __global__ void k_check(Grid g, int group, int colour, int ntasks, int phase, int *stamp,
                         unsigned long long *visit, unsigned long long *counters) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntasks; t += gridDim.x * blockDim.x) {
-        TaskCells tc = make_task<MODE>(g, group, colour, t);
+        TaskCells tc;
+        single_task<MODE>(g, group, colour, t, tc);
         for (int k = 0; k < tc.nnb; ++k) {
             int o[3];
             task_offset<MODE>(group, k, tc.self, o);
@@ -693,13 +748,13 @@ static size_t smem_bytes(int warps) {
 }
 
 // One resident wave: SMs x the blocks that fit on an SM (cached per shape).
-template <bool MIXED, int NI, int MODE, bool STATS>
+template <bool MIXED, int NI, int MODE, bool STATS, bool BATCHED>
 static int force_blocks(Ctx *c) {
     static int cache[17] = {0};
     const int warps = c->warps;
     if (!cache[warps]) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force<MIXED, NI, MODE, STATS>, warps * 32,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force<MIXED, NI, MODE, STATS, BATCHED>, warps * 32,
                                                       smem_bytes<MIXED, NI>(warps));
         if (per_sm < 1) per_sm = 1;
         cache[warps] = per_sm;
@@ -709,20 +764,27 @@ static int force_blocks(Ctx *c) {
     return blocks < maxb ? blocks : maxb;
 }
 
-template <bool MIXED, int NI, int MODE, bool STATS>
+template <bool MIXED, int NI, int MODE, bool STATS, bool BATCHED>
 static cudaError_t launch_one(Ctx *c, ForceArgs &a, cudaStream_t s) {
     const int warps = c->warps;
     const size_t sm = smem_bytes<MIXED, NI>(warps);
-    const int blocks = force_blocks<MIXED, NI, MODE, STATS>(c);
-    k_force<MIXED, NI, MODE, STATS><<<blocks, warps * 32, sm, s>>>(a);
+    const int blocks = force_blocks<MIXED, NI, MODE, STATS, BATCHED>(c);
+    k_force<MIXED, NI, MODE, STATS, BATCHED><<<blocks, warps * 32, sm, s>>>(a);
     return cudaGetLastError();
 }
 
 template <bool MIXED, int NI, int MODE>
 static cudaError_t launch_mode(Ctx *c, ForceArgs &a, cudaStream_t s, bool stats) {
-    // the FP64 comparator always accumulates its statistics
-    if (!MIXED || stats) return launch_one<MIXED, NI, MODE, true>(c, a, s);
-    return launch_one<MIXED, NI, MODE, (MIXED ? false : true)>(c, a, s);
+    // the FP64 comparator always accumulates its statistics; batches run
+    // the centre-cell tile of 16 (atomic and full-shell schedules)
+    if constexpr (MODE != kColour && NI == 16) {
+        if (c->nbox > 0) {
+            if (!MIXED || stats) return launch_one<MIXED, NI, MODE, true, true>(c, a, s);
+            return launch_one<MIXED, NI, MODE, (MIXED ? false : true), true>(c, a, s);
+        }
+    }
+    if (!MIXED || stats) return launch_one<MIXED, NI, MODE, true, false>(c, a, s);
+    return launch_one<MIXED, NI, MODE, (MIXED ? false : true), false>(c, a, s);
 }
 
 template <bool MIXED, int NI>
@@ -737,6 +799,10 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
     a.warp_acc = c->d_warp_acc; a.warp_pairs = c->d_warp_pairs;
     a.group = 0; a.colour = 0;
     a.stats = stats ? 1 : 0;
+    a.boxes = c->d_boxes;
+    a.cell_box = c->d_cell_box;
+    a.box_acc = c->d_box_acc;
+    a.box_pairs = c->d_box_pairs;
     for (int oi = 0; oi < 27; ++oi) {
         const int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, oi / 9 - 1};
         for (int d = 0; d < 3; ++d) {
@@ -773,7 +839,7 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
     } else if (sched == LC_SCHED_ATOMIC) {
         e = cudaMemsetAsync(c->fx, 0, 3 * nbytes, s);
         if (e) return e;
-        a.ntasks = c->g.ncell;
+        a.ntasks = c->g.ncell;   // a batch: the total cell count of all boxes
         e = launch_mode<MIXED, NI, kAtomic>(c, a, s, stats);
         ++*launches;
     } else {
@@ -791,14 +857,22 @@ cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launch
     const bool mixed = (c->prec == LC_PREC_MIXED);
     if (!mixed) stats = true;
     if (stats) {
-        if ((e = cudaMemsetAsync(c->d_warp_acc, 0, sizeof(double) * 4 * (size_t)c->nwarp_max, s))) return e;
-        if ((e = cudaMemsetAsync(c->d_warp_pairs, 0, sizeof(long long) * (size_t)c->nwarp_max, s))) return e;
+        if (c->nbox > 0) {
+            if ((e = cudaMemsetAsync(c->d_box_acc, 0, sizeof(double) * 2 * (size_t)c->nbox, s))) return e;
+            if ((e = cudaMemsetAsync(c->d_box_pairs, 0, sizeof(unsigned long long) * (size_t)c->nbox, s))) return e;
+        } else {
+            if ((e = cudaMemsetAsync(c->d_warp_acc, 0, sizeof(double) * 4 * (size_t)c->nwarp_max, s))) return e;
+            if ((e = cudaMemsetAsync(c->d_warp_pairs, 0, sizeof(long long) * (size_t)c->nwarp_max, s))) return e;
+        }
     }
-    if (c->ni == 8) e = mixed ? launch_sched<true, 8>(c, sched, s, launches, stats) : launch_sched<false, 8>(c, sched, s, launches, stats);
-    else e = mixed ? launch_sched<true, 16>(c, sched, s, launches, stats) : launch_sched<false, 16>(c, sched, s, launches, stats);
+    if (c->ni == 8 && c->nbox == 0)
+        e = mixed ? launch_sched<true, 8>(c, sched, s, launches, stats) : launch_sched<false, 8>(c, sched, s, launches, stats);
+    else
+        e = mixed ? launch_sched<true, 16>(c, sched, s, launches, stats) : launch_sched<false, 16>(c, sched, s, launches, stats);
     if (e) return e;
     if (stats) {
-        e = launch_energy_reduce(c, s, sched == LC_SCHED_FULLSHELL);
+        c->stats_full = (sched == LC_SCHED_FULLSHELL);
+        e = c->nbox > 0 ? launch_box_energy(c, s, sched == LC_SCHED_FULLSHELL) : launch_energy_reduce(c, s, sched == LC_SCHED_FULLSHELL);
         ++*launches;
     }
     return e;
@@ -833,10 +907,15 @@ cudaError_t launch_schedule_check(Ctx *c, lc_schedule sched, cudaStream_t s) {
 template <bool MIXED, int NI, bool STATS>
 static cudaError_t attrs_for() {
     cudaError_t e;
-    const int bytes = (int)smem_bytes<MIXED, NI>(16);
-    if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kColour, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
-    if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kAtomic, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
-    return cudaFuncSetAttribute(k_force<MIXED, NI, kFullShell, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const int bytes = (int)smem_bytes<MIXED, NI>(8);
+    if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kColour, STATS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kAtomic, STATS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kFullShell, STATS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    if constexpr (NI == 16) {
+        if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kAtomic, STATS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+        if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kFullShell, STATS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    }
+    return cudaSuccess;
 }
 
 // Opt the force kernels into the shared memory of the largest tile shape

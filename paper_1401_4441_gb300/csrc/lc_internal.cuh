@@ -57,6 +57,18 @@ struct Stencil {
 void make_stencil(Stencil *s);
 void make_grid(Grid *g, const double box[3], double rc);
 
+// One box of a batch: its grid, the FP32 shift tables of its 27 offsets,
+// and where its cells and particles sit in the batch's global numbering
+// (boxes are concatenated: box b owns cells [cell_off, cell_off + ncell)
+// and slots [part_off, part_off + n)).
+struct BoxDev {
+    Grid g;
+    float sh[27][3];   // o * h rounded to FP32, offset index (ox+1) + 3 (oy+1) + 9 (oz+1)
+    float sl[27][3];   // o * h - sh, rounded to FP32
+    int cell_off, part_off, n, pad;
+};
+void make_box(BoxDev *b, const double box[3], double rc, int cell_off, int part_off, int n);
+
 // Double-buffered particle state in cell-sorted order.
 struct State {
     double *x, *y, *z;     // wrapped positions
@@ -98,6 +110,16 @@ struct Ctx {
     // status
     bool have_state, binned, forces_valid;
     int launches_force, launches_step;
+    // batch of independent boxes (nbox > 0); single box: nbox == 0
+    int nbox;
+    BoxDev *h_boxes;          // host copy
+    BoxDev *d_boxes;
+    unsigned short *d_cell_box;   // box of each global cell
+    unsigned short *d_slot_box;   // box of each slot
+    double *d_box_acc;        // [nbox][2] sums of r^-6 and r^-12 (pairs once)
+    unsigned long long *d_box_pairs;
+    double *d_box_out;        // [nbox][4] U, W, pairs, K
+    int stats_full;           // last statistics came from the full shell
     // graphs of two Verlet steps: one per (schedule, state-buffer parity)
     cudaGraphExec_t graph[6];
     double graph_dt[6];
@@ -111,6 +133,8 @@ cudaError_t launch_kick_drift(Ctx *c, double dt, cudaStream_t s);
 cudaError_t launch_kick(Ctx *c, double dt, cudaStream_t s);
 cudaError_t launch_kinetic(Ctx *c, cudaStream_t s);
 cudaError_t launch_energy_reduce(Ctx *c, cudaStream_t s, int full);
+cudaError_t launch_box_energy(Ctx *c, cudaStream_t s, int full);
+cudaError_t launch_box_kinetic(Ctx *c, cudaStream_t s);
 cudaError_t launch_colour(Ctx *c, cudaStream_t s);
 cudaError_t upload_stencil(const Stencil &st);
 int kinetic_blocks(const Ctx *c);

@@ -100,6 +100,47 @@ __global__ void __launch_bounds__(kRedThreads) k_final_kin(int nb, const double 
     if (threadIdx.x == 0) out[3] = 0.5 * r[0];
 }
 
+// Per-box statistics of a batch: U, W and pair count from the box
+// accumulators of the force kernel (full shell: each pair seen twice).
+__global__ void k_box_energy(int nbox, int full, const double *__restrict__ acc,
+                             const unsigned long long *__restrict__ pairs, double *__restrict__ out) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
+        const double scale = full ? 0.5 : 1.0;
+        const double s6 = acc[2 * b], s12 = acc[2 * b + 1];
+        out[4 * b + 0] = scale * 4.0 * (s12 - s6);
+        out[4 * b + 1] = scale * 24.0 * (2.0 * s12 - s6);
+        out[4 * b + 2] = (double)(full ? pairs[b] / 2 : pairs[b]);
+    }
+}
+
+// Kinetic energy per box: one block per box over its slot range, fixed order.
+__global__ void __launch_bounds__(256) k_box_kinetic(const BoxDev *__restrict__ boxes, State st, double *__restrict__ out) {
+    __shared__ double red[256];
+    const BoxDev &bd = boxes[blockIdx.x];
+    double acc = 0.0;
+    for (int s = bd.part_off + threadIdx.x; s < bd.part_off + bd.n; s += blockDim.x) {
+        const double vx = st.vx[s], vy = st.vy[s], vz = st.vz[s];
+        acc += vx * vx + vy * vy + vz * vz;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int m = 128; m > 0; m >>= 1) {
+        if (threadIdx.x < m) red[threadIdx.x] += red[threadIdx.x + m];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[4 * blockIdx.x + 3] = 0.5 * red[0];
+}
+
+cudaError_t launch_box_energy(Ctx *c, cudaStream_t s, int full) {
+    k_box_energy<<<(c->nbox + 255) / 256, 256, 0, s>>>(c->nbox, full, c->d_box_acc, c->d_box_pairs, c->d_box_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_box_kinetic(Ctx *c, cudaStream_t s) {
+    k_box_kinetic<<<c->nbox, 256, 0, s>>>(c->d_boxes, c->cur, c->d_box_out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_kick_drift(Ctx *c, double dt, cudaStream_t s) {
     if (c->n == 0) return cudaSuccess;
     k_kick_drift<<<c->num_sms * 8, 256, 0, s>>>((int)c->n, 0.5 * dt, dt, c->cur, c->fx, c->fy, c->fz);

@@ -184,11 +184,18 @@ WORKLOADS = {
     "fcc4k": dict(n=4000, rho=0.8442, T=0.72, rc=2.5, jitter=0.0),
     "liquid1m": dict(n=1_048_576, rho=0.8442, T=0.72, rc=2.5, jitter=0.05),
     "fcc16m": dict(n=16_777_216, rho=0.8442, T=0.72, rc=2.5, jitter=0.0),
+    "slab2m": dict(n=2_000_000, rho=None, T=0.85, rc=3.0, jitter=0.0, kind="slab"),
 }
 
 
 def workload(name, seed=DEFAULT_SEED):
     w = WORKLOADS[name]
+    if w.get("kind") == "slab":
+        b = slab_box(n=w["n"], T=w["T"], seed=seed)
+        b["rc"] = w["rc"]
+        b["name"] = name
+        b["rho"] = None
+        return b
     b = fcc_box(w["n"], w["rho"], w["T"], seed=seed, jitter=w["jitter"])
     b["rc"] = w["rc"]
     b["name"] = name

@@ -53,6 +53,9 @@ def _load():
         "lc_schedule_check": ([vp, ctypes.c_int, lp, lp, vp], ctypes.c_int),
         "lc_set_tile": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "lc_launch_counts": ([vp, ip, ip], ctypes.c_int),
+        "lc_batch_create": ([ctypes.c_int32, dp, dp, lp, ctypes.c_int, ctx_pp], ctypes.c_int),
+        "lc_batch_energies": ([vp, dp, dp, dp, lp, vp], ctypes.c_int),
+        "lc_batch_info": ([vp, ip, lp, lp], ctypes.c_int),
         "lc_destroy": ([vp], None),
         "lc_status_str": ([ctypes.c_int], ctypes.c_char_p),
     }
@@ -161,11 +164,16 @@ class Box:
         _check(self._lib.lc_grid(self._h, nc, ctypes.byref(ncol), ctypes.byref(nph)), "lc_grid")
         return np.array(list(nc), np.int32), ncol.value, nph.value
 
+    def ncell(self):
+        nb, np_, nc = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        _check(self._lib.lc_batch_info(self._h, ctypes.byref(nb), ctypes.byref(np_), ctypes.byref(nc)),
+               "lc_batch_info")
+        return int(nc.value)
+
     def get(self, what, out=None, stream=None):
         """Copy an array out; returns a numpy array unless `out` (host
         numpy array or CUDA torch tensor of the right size) is given."""
-        nc, _, _ = self.grid()
-        ncell = int(nc.prod())
+        ncell = self.ncell()
         shapes = {"cell_count": ((ncell,), np.int32), "cell_start": ((ncell,), np.int32),
                   "perm": ((self.n,), np.int32), "colour": ((ncell,), np.int8),
                   "forces": ((self.n, 3), np.float64), "pos": ((self.n, 3), np.float64),
@@ -192,3 +200,36 @@ class Box:
         a, b = ctypes.c_int32(), ctypes.c_int32()
         _check(self._lib.lc_launch_counts(self._h, ctypes.byref(a), ctypes.byref(b)), "lc_launch_counts")
         return a.value, b.value
+
+
+class Batch(Box):
+    """Independent periodic boxes in one context (lc_batch_create): particles
+    numbered box after box; atomic or full-shell schedule."""
+
+    def __init__(self, boxes, rcs, ns, precision="mixed"):
+        self._lib = _load()
+        boxes = np.ascontiguousarray(np.asarray(boxes, np.float64).reshape(-1, 3))
+        rcs = np.ascontiguousarray(np.broadcast_to(np.asarray(rcs, np.float64), (boxes.shape[0],)))
+        ns = np.ascontiguousarray(np.asarray(ns, np.int64))
+        self.nbox = boxes.shape[0]
+        self.ns = ns
+        self.offsets = np.concatenate([[0], np.cumsum(ns)])
+        self.n = int(ns.sum())
+        self.box = boxes
+        self.precision = precision
+        h = ctypes.c_void_p()
+        _check(self._lib.lc_batch_create(self.nbox, boxes.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         rcs.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                         PREC[precision], ctypes.byref(h)), "lc_batch_create")
+        self._h = h
+
+    def energies(self, stream=None):
+        """Per-box (U, K, W, npairs) arrays."""
+        u, k, w = (np.zeros(self.nbox) for _ in range(3))
+        p = np.zeros(self.nbox, np.int64)
+        dp = ctypes.POINTER(ctypes.c_double)
+        _check(self._lib.lc_batch_energies(self._h, u.ctypes.data_as(dp), k.ctypes.data_as(dp), w.ctypes.data_as(dp),
+                                           p.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _stream(stream)),
+               "lc_batch_energies")
+        return u, k, w, p

@@ -303,3 +303,19 @@ def test_half_shell_is_a_half():
     for o in hs:
         assert tuple(-x for x in o) not in hs
     assert set(hs) | {tuple(-x for x in o) for o in hs} == set(itertools.product((-1, 0, 1), repeat=3)) - {(0, 0, 0)}
+
+
+def test_force_scale():
+    """S_i = sum_j |F_ij|: equals |F| for an isolated pair, the shell sum
+    z |F(r_s)| on a perfect FCC lattice, and bounds |F_i| everywhere."""
+    p, L = two(1.05)
+    s = oracle.force_scale(p[:, 0], p[:, 1], p[:, 2], L, RC)
+    assert s == pytest.approx([abs(lj_du(1.05))] * 2, rel=1e-12)
+    b = inputs.fcc_box(4000, 0.8442, 0.72, jitter=0.0)
+    s = oracle.force_scale(b["pos"][:, 0], b["pos"][:, 1], b["pos"][:, 2], b["box"], RC)
+    shells = fcc_shells(b["box"][0] / 10)
+    assert np.allclose(s, sum(z * abs(lj_du(r)) for z, r in shells), rtol=1e-12)
+    q, Lq = jittered(4000)
+    f, _, _, _ = oracle.lc_forces(q[:, 0], q[:, 1], q[:, 2], Lq, RC)
+    s = oracle.force_scale(q[:, 0], q[:, 1], q[:, 2], Lq, RC)
+    assert np.all(np.sqrt((f ** 2).sum(1)) <= s * (1 + 1e-12))
