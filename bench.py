@@ -149,6 +149,25 @@ def half_shell_candidates(counts, nc):
     return total
 
 
+def measured_traffic(workload, sched):
+    """DRAM bytes (read + write) of one force evaluation from the committed ncu
+    summary profiles/k_force_<workload>.md, or None when the force kernel's
+    source changed since that capture (or there is none)."""
+    import hashlib
+    import re
+    src = os.path.join(ROOT, "paper_1401_4441_gb300", "csrc", "lc_force.cu")
+    path = os.path.join(ROOT, "profiles", f"k_force_{workload}.md")
+    try:
+        cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        for line in open(path):
+            m = re.match(r"traffic_bytes (\w+) (\d+) sha256 ([0-9a-f]+)", line.strip())
+            if m and m.group(1) == sched and m.group(3) == cur:
+                return int(m.group(2))
+    except OSError:
+        pass
+    return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -268,7 +287,7 @@ def run_batch(args, dist):
     g = lc.Batch([b["box"] for b in boxes], RC, [b["pos"].shape[0] for b in boxes], args.precision)
     dpos, dvel = torch.from_numpy(pos).to(dev), torch.from_numpy(vel).to(dev)
     sched_ms = {}
-    for sch in ("atomic", "fullshell"):
+    for sch in ("atomic", "fullshell", "buffer"):
         g.set_state(dpos, dvel)
         g.forces(sch)
         ts = []
@@ -440,7 +459,7 @@ def run_gb300(args, dist):
     sm_clock = 2070.0
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_clock * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": measured_traffic(args.workload, sched),
                 "kernel": f"k_force ({sched}, {args.precision}): one force evaluation",
                 "flops_per_eval": flops, "candidates": cand, "pairs": npairs_now,
                 "eval_ms": t_force * 1e3,
@@ -482,18 +501,71 @@ def run_gb300(args, dist):
         print(json.dumps(line), flush=True)
 
 
+def run_dag(args, dist):
+    """The force sweep as the paper's task program on the device (Sec. III,
+    Sec. V, Sec. VI Strategy 2): the DAG of each task-creation order executed
+    by the dependency-counted device queue, next to the atomic schedule.
+    Prints one JSON line (an auxiliary measurement, not the headline)."""
+    import torch
+    from paper_1401_4441_gb300 import build
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    if dist.rank == 0:
+        build.build()
+    dist.barrier()
+    from paper_1401_4441_gb300 import lc
+    b = inputs.workload(args.workload, seed=inputs.DEFAULT_SEED + 1000 * dist.rank)
+    pos, box, rc = b["pos"], b["box"], b["rc"]
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    g = lc.Box(box, rc, pos.shape[0], args.precision)
+    g.set_state(torch.from_numpy(pos).to(dev))
+
+    def timed(fn, reps=3):
+        fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream); fn(); e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        return min(ts)
+
+    g.forces("atomic")
+    _, _, _, npairs = g.energy()
+    rows = {"atomic": {"ms": timed(lambda: g.forces("atomic"))}}
+    for order in ("loopex", "cell"):
+        t, e, cp = g.dag_build(order)
+        ms = timed(lambda: g.dag_forces(order))
+        _, _, _, np_ = g.energy()
+        assert np_ == npairs
+        rows[f"dag_{order}"] = {"ms": ms, "tasks": t, "edges": e, "critical_path": cp,
+                                "speedup_bound": t / cp, "us_per_critical_task": 1e3 * ms / cp}
+    for r in rows.values():
+        r["pairs_per_s"] = npairs / (r["ms"] * 1e-3)
+    if dist.rank == 0:
+        print(json.dumps({"metric": "force evaluation time by task-DAG creation order", "unit": "ms",
+                          "higher_is_better": False, "n_gpus": dist.world, "precision": args.precision,
+                          "config": {"workload": b["name"], "particles": int(pos.shape[0]),
+                                     "l2": "flushed (512 MiB memset) before each timed call"},
+                          "pairs": int(npairs), "results": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--schedule", default="auto", choices=["auto", "colour", "atomic", "fullshell"])
+    ap.add_argument("--schedule", default="auto", choices=["auto", "colour", "atomic", "fullshell", "buffer"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--workload", default="liquid1m", choices=sorted(inputs.WORKLOADS) + ["batch512"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="only warm-up + timed steps of one schedule (for ncu captures)")
+    ap.add_argument("--dag", action="store_true",
+                    help="time the task-DAG execution of each creation order (auxiliary line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     dist = Dist()
@@ -502,6 +574,8 @@ def main():
             run_reference(args, dist)
         elif args.profile:
             run_profile(args, dist)
+        elif args.dag:
+            run_dag(args, dist)
         elif args.workload == "batch512":
             run_batch(args, dist)
         else:

@@ -18,6 +18,9 @@
  *     makes the writes of one phase disjoint (LC_SCHED_COLOUR).
  *   - Sec. VIII: commutative updates only need mutual exclusion, not an
  *     order (LC_SCHED_ATOMIC resolves the sharing with atomic adds).
+ *   - Sec. VI, Strategy 3: every task writes private buffers, one per
+ *     neighbour it serves, and a reduce step sums them afterwards, so no two
+ *     tasks write the same memory, at the price of memory (LC_SCHED_BUFFER).
  * Units are reduced Lennard-Jones units, sigma = epsilon = m = 1:
  *   U(r) = 4 (r^-12 - r^-6) for r < r_c (truncated, not shifted),
  *   F_i  = sum_j 24 (2 r^-12 - r^-6) / r^2 (r_i - r_j),
@@ -64,7 +67,12 @@ typedef enum {
 typedef enum {
     LC_SCHED_COLOUR = 0,    /* phases (offset group, colour), disjoint writes   */
     LC_SCHED_ATOMIC = 1,    /* one pass, both cells updated by atomic adds      */
-    LC_SCHED_FULLSHELL = 2  /* all 27 cells, own cell written only, no Newton-3 */
+    LC_SCHED_FULLSHELL = 2, /* all 27 cells, own cell written only, no Newton-3 */
+    LC_SCHED_BUFFER = 3     /* one pass into private per-(cell, offset) buffers,
+                               then a fixed-order reduce: no atomics, no phases,
+                               forces bit-reproducible from run to run; buffers
+                               of 15 x 3 x n floats (FP64: doubles) are
+                               allocated on the first use of the schedule    */
 } lc_schedule;
 
 typedef enum {
@@ -112,7 +120,9 @@ lc_status lc_bin(lc_ctx *ctx, void *stream);
 
 /* One force evaluation with the given schedule (bins first if the positions
  * changed since the last binning).  Also produces the potential energy,
- * the virial and the number of pairs inside r_c. */
+ * the virial and the number of pairs inside r_c.  LC_ERR_OOM if the buffers
+ * of LC_SCHED_BUFFER cannot be allocated; LC_ERR_INVALID_ARG for
+ * LC_SCHED_COLOUR on a batch of boxes. */
 lc_status lc_forces(lc_ctx *ctx, lc_schedule sched, void *stream);
 
 /* nsteps velocity-Verlet steps of size dt (m = 1): v += dt/2 F; x += dt v;
@@ -149,6 +159,51 @@ lc_status lc_grid(const lc_ctx *ctx, int32_t nc[3], int32_t *ncolours, int32_t *
  * Synchronises the stream. */
 lc_status lc_schedule_check(lc_ctx *ctx, lc_schedule sched, int64_t *conflicts,
                             int64_t *coverage_errors, void *stream);
+
+/* ---- Task DAG on the device (Sec. III, Sec. V, Sec. VI Strategy 2) --------
+ * The force sweep as the paper's task program: 14 tasks per cell (the
+ * intra-cell interaction and the 13 half-shell pairs), each declaring both
+ * of its cells inout, so a task depends on the last earlier-created task that
+ * touched either cell.  The creation order decides the DAG and with it the
+ * critical path (Eq. 1-4, Fig. 5). */
+typedef enum {
+    LC_ORDER_CELL = 0,   /* outer loop over cells (x fastest), inner loop over
+                            the stencil: intra first, then the half-shell
+                            offsets in table order (the literature order)   */
+    LC_ORDER_LOOPEX = 1  /* loop exchange + 2-strided colouring (Sec. VI,
+                            Fig. 6): stencil entries outer (intra first),
+                            then colours, then the cells of the colour      */
+} lc_order;
+
+/* Builds (once per order; host work O(cells)) the DAG of a single-box
+ * context and reports its size: tasks (14 per cell), dependency edges and
+ * the critical path counted in tasks.  Any output may be NULL.  Synchronous.
+ * LC_ERR_INVALID_ARG for a batch; LC_ERR_TOO_LARGE beyond 2^29 tasks. */
+lc_status lc_dag_build(lc_ctx *ctx, lc_order order, int64_t *ntasks, int64_t *nedges,
+                       int64_t *critical_path);
+
+/* The same DAG for a grid of nc[0] x nc[1] x nc[2] cells (each >= 3), built
+ * on the host only (no context, no GPU): tasks, edges and critical path.
+ * Eq. 1 with equal task times gives the speedup bound tasks / critical_path.
+ * LC_ERR_BOX_TOO_SMALL if some nc < 3, LC_ERR_TOO_LARGE beyond 2^29 tasks. */
+lc_status lc_dag_plan(const int32_t nc[3], lc_order order, int64_t *ntasks, int64_t *nedges,
+                      int64_t *critical_path);
+
+/* One force evaluation by executing the DAG of `order` on the device: a
+ * persistent kernel (cooperative launch, every warp resident) whose warps
+ * claim queue slots, wait for a ready task, run it with plain writes to both
+ * cells and release its successors (dependency counting).  Forces, energy,
+ * virial and pair count as lc_forces.  wait_seconds (> 0) bounds every wait
+ * for a queue slot (default 2 s when <= 0); a wait that runs out makes the
+ * call return LC_ERR_TIMEOUT with the forces invalid, the context stays
+ * usable.  trace: NULL or device int32[2 * ntasks]; entry 2t / 2t+1 receive
+ * the start / end stamp of task t (creation index) on one device-wide
+ * counter, so end(p) < start(s) for every edge p -> s.  flags: 0, or
+ * LC_DAG_WITHHOLD for a test of the bounded waits (no task is published).
+ * Synchronises the stream. */
+#define LC_DAG_WITHHOLD 1
+lc_status lc_dag_forces(lc_ctx *ctx, lc_order order, double wait_seconds, int flags, int32_t *trace,
+                        void *stream);
 
 /* Tile shape of the force kernels: ni = particles of the centre cell held
  * per warp (8 or 16), warps = warps per thread block (1 .. 8).  0 keeps

@@ -63,7 +63,7 @@ def time_forces(box, schedule, reps=3):
     return sorted(ts)[len(ts) // 2]
 
 
-def tune(box, schedules=("atomic", "fullshell", "colour"), use_cache=True):
+def tune(box, schedules=("atomic", "buffer", "fullshell", "colour"), use_cache=True):
     """Pick (schedule, tile, warps) for `box` (state already set); applies
     the tile shape and returns dict(schedule, ni, warps, ms, table)."""
     if getattr(box, "nbox", 0):

@@ -86,6 +86,13 @@ void make_grid(Grid *g, const double box[3], double rc) {
         if (present) { g->raw_of_colour[r] = raw; ++r; }
     }
     g->ncolours = r;
+    // exact division by multiplication: with M = ceil(2^64 / d) and c < 2^32,
+    // c M / 2^64 = c / d + c e / (d 2^64) with e = M d - 2^64 < d, an excess
+    // below 1 / d, so the floor is floor(c / d)
+    const unsigned long long dx = (unsigned long long)(g->nc[0] > 0 ? g->nc[0] : 1);
+    const unsigned long long dxy = dx * (unsigned long long)(g->nc[1] > 0 ? g->nc[1] : 1);
+    g->divx = ~0ull / dx + 1;
+    g->divxy = ~0ull / dxy + 1;
 }
 
 void make_box(BoxDev *b, const double box[3], double rc, int cell_off, int part_off, int n) {
@@ -126,6 +133,12 @@ static lc_status from_cuda(cudaError_t e) {
         }                                         \
     } while (0)
 
+#define LC_TRY_ST(expr)                           \
+    do {                                          \
+        lc_status _s = (expr);                    \
+        if (_s != LC_OK) return _s;               \
+    } while (0)
+
 template <typename T>
 static cudaError_t dalloc(T **p, size_t count) {
     *p = nullptr;
@@ -139,11 +152,12 @@ static void free_ctx(Ctx *c) {
                     c->d_count, c->d_start, c->d_src, c->d_key, c->d_blocksums, c->d_colour, c->d_p4, c->fx, c->kx,
                     c->d_warp_acc, c->d_warp_pairs, c->d_kin_part, c->d_result, c->d_npairs, c->d_err,
                     c->d_stamp, c->d_visit, c->d_counters, c->d_boxes, c->d_cell_box, c->d_slot_box,
-                    c->d_box_acc, c->d_box_pairs, c->d_box_out};
+                    c->d_box_acc, c->d_box_pairs, c->d_box_out, c->d_fbuf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    for (int k = 0; k < 6; ++k)
+    for (int k = 0; k < 2 * kNumSched; ++k)
         if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+    for (DagDev *d : c->dag) free_dag(d);
     free(c->h_boxes);
     delete static_cast<lc_ctx *>(c);
 }
@@ -385,7 +399,19 @@ lc_status lc_bin(lc_ctx *c, void *stream) {
     return LC_OK;
 }
 
+// The buffer schedule's private buffers, allocated on its first use (before
+// any stream capture, so that a captured step never allocates).
+static lc_status ensure_fbuf(lc_ctx *c, lc_schedule sched) {
+    if (sched != LC_SCHED_BUFFER || c->d_fbuf) return LC_OK;
+    const size_t elem = c->prec == LC_PREC_MIXED ? sizeof(float) : sizeof(double);
+    const size_t bytes = elem * 3 * (size_t)kNumFbuf * (size_t)(c->n > 0 ? c->n : 1);
+    cudaError_t e = cudaMalloc(&c->d_fbuf, bytes);
+    if (e) { cudaGetLastError(); c->d_fbuf = nullptr; return e == cudaErrorMemoryAllocation ? LC_ERR_OOM : LC_ERR_CUDA; }
+    return LC_OK;
+}
+
 static lc_status do_forces(lc_ctx *c, lc_schedule sched, cudaStream_t s, int *launches) {
+    LC_TRY_ST(ensure_fbuf(c, sched));
     if (!c->binned) {
         LC_TRY(launch_bin(c, s, launches));
         c->binned = true;
@@ -396,7 +422,7 @@ static lc_status do_forces(lc_ctx *c, lc_schedule sched, cudaStream_t s, int *la
 }
 
 lc_status lc_forces(lc_ctx *c, lc_schedule sched, void *stream) {
-    if (!c || sched < LC_SCHED_COLOUR || sched > LC_SCHED_FULLSHELL) return LC_ERR_INVALID_ARG;
+    if (!c || sched < LC_SCHED_COLOUR || sched > LC_SCHED_BUFFER) return LC_ERR_INVALID_ARG;
     if (c->nbox > 0 && sched == LC_SCHED_COLOUR) return LC_ERR_INVALID_ARG;
     if (!c->have_state) return LC_ERR_STATE;
     int launches = 0;
@@ -421,7 +447,7 @@ static cudaError_t step_launches(lc_ctx *c, double dt, lc_schedule sched, cudaSt
 }
 
 lc_status lc_verlet_step(lc_ctx *c, double dt, int nsteps, lc_schedule sched, void *stream) {
-    if (!c || nsteps < 0 || !isfinite(dt) || sched < LC_SCHED_COLOUR || sched > LC_SCHED_FULLSHELL)
+    if (!c || nsteps < 0 || !isfinite(dt) || sched < LC_SCHED_COLOUR || sched > LC_SCHED_BUFFER)
         return LC_ERR_INVALID_ARG;
     if (c->nbox > 0 && sched == LC_SCHED_COLOUR) return LC_ERR_INVALID_ARG;
     if (!c->have_state) return LC_ERR_STATE;
@@ -432,6 +458,7 @@ lc_status lc_verlet_step(lc_ctx *c, double dt, int nsteps, lc_schedule sched, vo
         if (st) return st;
     }
     if (nsteps == 0) return LC_OK;
+    LC_TRY_ST(ensure_fbuf(c, sched));
     // The step swaps the two state buffers once (in the binning), so one
     // graph holds two steps and returns the buffers to where they were; a
     // separate graph serves each buffer parity.
@@ -550,7 +577,7 @@ lc_status lc_grid(const lc_ctx *c, int32_t nc[3], int32_t *ncolours, int32_t *np
 }
 
 lc_status lc_schedule_check(lc_ctx *c, lc_schedule sched, int64_t *conflicts, int64_t *coverage_errors, void *stream) {
-    if (!c || sched < LC_SCHED_COLOUR || sched > LC_SCHED_FULLSHELL || c->nbox > 0) return LC_ERR_INVALID_ARG;
+    if (!c || sched < LC_SCHED_COLOUR || sched > LC_SCHED_BUFFER || c->nbox > 0) return LC_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     LC_TRY(launch_schedule_check(c, sched, s));
     unsigned long long cnt[4];
@@ -561,13 +588,74 @@ lc_status lc_schedule_check(lc_ctx *c, lc_schedule sched, int64_t *conflicts, in
     return cnt[0] ? LC_ERR_RACE : LC_OK;
 }
 
+static lc_status ensure_dag(lc_ctx *c, lc_order order) {
+    if (c->dag[order]) return LC_OK;
+    if (14 * (int64_t)c->g.ncell > (int64_t(1) << 29)) return LC_ERR_TOO_LARGE;
+    Stencil st;
+    memset(&st, 0, sizeof(st));
+    make_stencil(&st);
+    DagDev *d = nullptr;
+    LC_TRY(build_dag(c, st, (int)order, &d));
+    c->dag[order] = d;
+    return LC_OK;
+}
+
+lc_status lc_dag_build(lc_ctx *c, lc_order order, int64_t *ntasks, int64_t *nedges, int64_t *critical_path) {
+    if (!c || (order != LC_ORDER_CELL && order != LC_ORDER_LOOPEX) || c->nbox > 0) return LC_ERR_INVALID_ARG;
+    LC_TRY_ST(ensure_dag(c, order));
+    const DagDev *d = c->dag[order];
+    if (ntasks) *ntasks = d->ntasks;
+    if (nedges) *nedges = d->nedges;
+    if (critical_path) *critical_path = d->critical_path;
+    return LC_OK;
+}
+
+lc_status lc_dag_plan(const int32_t nc[3], lc_order order, int64_t *ntasks, int64_t *nedges, int64_t *critical_path) {
+    if (!nc || (order != LC_ORDER_CELL && order != LC_ORDER_LOOPEX)) return LC_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; ++d)
+        if (nc[d] < 3) return LC_ERR_BOX_TOO_SMALL;
+    if (14 * (int64_t)nc[0] * nc[1] * nc[2] > (int64_t(1) << 29)) return LC_ERR_TOO_LARGE;
+    const int n3[3] = {nc[0], nc[1], nc[2]};
+    const int64_t cp = dag_plan_host(n3, (int)order, ntasks, nedges);
+    if (critical_path) *critical_path = cp;
+    return LC_OK;
+}
+
+lc_status lc_dag_forces(lc_ctx *c, lc_order order, double wait_seconds, int flags, int32_t *trace, void *stream) {
+    if (!c || (order != LC_ORDER_CELL && order != LC_ORDER_LOOPEX) || c->nbox > 0 || !(wait_seconds == wait_seconds) ||
+        (flags & ~LC_DAG_WITHHOLD))
+        return LC_ERR_INVALID_ARG;
+    if (!c->have_state) return LC_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    LC_TRY_ST(ensure_dag(c, order));
+    int launches = 0;
+    if (!c->binned) {
+        LC_TRY(launch_bin(c, s, &launches));
+        c->binned = true;
+    }
+    LC_TRY_ST(read_err(c, s));                 // a non-finite input stops here
+    c->forces_valid = false;
+    const double ws = wait_seconds > 0 ? (wait_seconds < 60.0 ? wait_seconds : 60.0) : 2.0;
+    LC_TRY(launch_forces_dag(c, c->dag[order], (long long)(ws * 1e9), flags & LC_DAG_WITHHOLD, trace, s, &launches));
+    lc_status st = read_err(c, s);
+    if (st == LC_ERR_TIMEOUT) {                // clear the flag: the context stays usable
+        LC_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
+        LC_TRY(cudaStreamSynchronize(s));
+        return st;
+    }
+    if (st) return st;
+    c->launches_force = launches;
+    c->forces_valid = true;
+    return LC_OK;
+}
+
 lc_status lc_set_tile(lc_ctx *c, int ni, int warps) {
     if (!c) return LC_ERR_INVALID_ARG;
     if (ni && ni != 8 && ni != 16) return LC_ERR_INVALID_ARG;
     if (warps < 0 || warps > 8) return LC_ERR_INVALID_ARG;   // 256-thread launch bound
     if (ni) c->ni = ni;
     if (warps) c->warps = warps;
-    for (int k = 0; k < 6; ++k)
+    for (int k = 0; k < 2 * kNumSched; ++k)
         if (c->graph[k]) { cudaGraphExecDestroy(c->graph[k]); c->graph[k] = nullptr; }
     return LC_OK;
 }

@@ -214,7 +214,8 @@ __global__ void k_rank_gather(Grid g1, const BoxDev *__restrict__ boxes, const u
             // double-float arithmetic (TwoProduct / TwoSum) from the hi + lo
             // split of x; the rounding residual of each offset (|r| <= 2^-23
             // for |offset| < 4) is kept as a 10-bit signed fraction of 2^-23
-            // in the spare fourth word.
+            // in the spare fourth word (offset + residual equals
+            // x - (c + 1/2) h to ~2e-10).
             float hi[3];
             unsigned w = 0;
 #pragma unroll
@@ -229,7 +230,7 @@ __global__ void k_rank_gather(Grid g1, const BoxDev *__restrict__ boxes, const u
                 const float tt = sum + rest;
                 const float res = rest - (tt - sum);
                 hi[d] = tt;
-                int q = __float2int_rn(res * (float)kLoScale);
+                int q = __float2int_rn(res * kLoScale);
                 q = q > 511 ? 511 : (q < -511 ? -511 : q);
                 w |= (unsigned)(q + 512) << (10 * d);
             }

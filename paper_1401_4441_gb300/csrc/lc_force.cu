@@ -31,6 +31,7 @@
 // reduced in FP64.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <type_traits>
 
@@ -40,18 +41,21 @@ namespace lc {
 
 __constant__ Stencil c_st;
 
-enum Mode : int { kColour = 0, kAtomic = 1, kFullShell = 2 };
+enum Mode : int { kColour = 0, kAtomic = 1, kFullShell = 2, kBuffer = 3, kDag = 4 };
 
 constexpr int kJCap = 512;      // neighbour slots listed per batch (per warp)
 constexpr int kMaxNb = 27;      // neighbour cells per task
 
 struct ForceArgs {
     Grid g;
-    const float4 *p4;
+    const float4 *p4;           // FP32 cell-centre offsets + packed rounding residuals
     const double *x, *y, *z;
     const int *start, *count;
     double *fx, *fy, *fz;
     float2 *kx, *ky, *kz;
+    float *bf;                  // buffer schedule, mixed: [15][3][n] private partial forces
+    double *bd;                 // buffer schedule, FP64: [15][3][n]
+    size_t n;                   // particles (buffer stride)
     double *warp_acc;           // [W][4]
     long long *warp_pairs;      // [W]
     int group, colour;          // colour phase
@@ -73,6 +77,7 @@ struct TaskCells {
     int cA[3];        // its coordinates in its box
     int nnb;          // neighbour cells listed (self first when present)
     bool self;        // intra-cell interaction included
+    int group;        // colour: the phase's offset group; DAG: the offset index
     const Grid *g;    // the box's grid
     const float (*sh)[3], (*sl)[3];   // the box's shift tables
     int cell_off;     // first global cell of the box
@@ -80,10 +85,11 @@ struct TaskCells {
 };
 
 __device__ __forceinline__ void cell_xyz(const Grid &g, int c, int out[3]) {
-    out[0] = c % g.nc[0];
-    int r = c / g.nc[0];
-    out[1] = r % g.nc[1];
-    out[2] = r / g.nc[1];
+    const int q1 = (int)__umul64hi((unsigned long long)(unsigned)c, g.divx);    // c / nc_x
+    const int q2 = (int)__umul64hi((unsigned long long)(unsigned)c, g.divxy);   // c / (nc_x nc_y)
+    out[0] = c - q1 * g.nc[0];
+    out[1] = q1 - q2 * g.nc[1];
+    out[2] = q2;
 }
 
 // Task t of a colour phase: the t-th cell (x fastest) of colour `colour`.
@@ -111,8 +117,10 @@ __device__ __forceinline__ void task_offset(int group, int k, bool self, int o[3
     }
     if (MODE == kFullShell) {            // all 27 offsets, centre first
         o[0] = c_st.full[k + 1][0]; o[1] = c_st.full[k + 1][1]; o[2] = c_st.full[k + 1][2];
-    } else if (MODE == kAtomic) {
+    } else if (MODE == kAtomic || MODE == kBuffer) {
         o[0] = c_st.hs[k][0]; o[1] = c_st.hs[k][1]; o[2] = c_st.hs[k][2];
+    } else if (MODE == kDag) {           // one neighbour: half-shell offset `group`
+        o[0] = c_st.hs[group][0]; o[1] = c_st.hs[group][1]; o[2] = c_st.hs[group][2];
     } else {
         int kk = c_st.group_list[c_st.group_first[group] + k];
         o[0] = c_st.hs[kk][0]; o[1] = c_st.hs[kk][1]; o[2] = c_st.hs[kk][2];
@@ -123,6 +131,7 @@ __device__ __forceinline__ void task_offset(int group, int k, bool self, int o[3
 // colour) and its neighbour count; used by the force and check kernels.
 template <int MODE>
 __device__ __forceinline__ void single_task(const Grid &g, int group, int colour, int t, TaskCells &tc) {
+    tc.group = group;
     if (MODE == kColour) {
         tc.A = colour_task_cell(g, colour, t, tc.cA);
         tc.self = (group == 0);
@@ -145,6 +154,7 @@ __device__ __forceinline__ TaskCells make_task(const ForceArgs &a, int t) {
         tc.g = &bd.g; tc.sh = bd.sh; tc.sl = bd.sl; tc.cell_off = bd.cell_off; tc.box = box;
         tc.A = t;
         cell_xyz(bd.g, t - bd.cell_off, tc.cA);
+        tc.group = 0;
         tc.self = true;
         tc.nnb = (MODE == kFullShell) ? 27 : 14;
     } else {
@@ -158,15 +168,17 @@ __device__ __forceinline__ TaskCells make_task(const ForceArgs &a, int t) {
 template <typename T>
 struct alignas(16) WarpSmem {
     float4 ipa[16];             // mixed: particles 2m, 2m+1 as (x, x', y, y')
-    float4 ipb[16];             // mixed: (z, z', slot bits, slot' bits)
+    float4 ipb[16];             // mixed: (z, z', rz, rz') with r the rounding residual
+    float4 ipc[16];             // mixed: (rx, rx', ry, ry')
+    int2 islot2[16];            // mixed: (slot, slot')
     float corr[32][3];          // mixed: i-side forces of near-r_c pairs
     T ix[32], iy[32], iz[32];   // FP64: centre-cell particles
     int islot[32];
     int jl[kJCap];              // slot | (neighbour index << 26)
     int nb_start[kMaxNb], nb_count[kMaxNb];
     int nb_img[kMaxNb];         // periodic image s_d in {-1,0,1} as (s+1) in 2-bit fields
-    float nb_sh[kMaxNb][3];     // o * h rounded to FP32 (mixed)
-    float nb_sl[kMaxNb][3];     // o * h - nb_sh, rounded to FP32
+    float4 nb_sh[kMaxNb];       // o * h rounded to FP32 (mixed), w unused
+    float4 nb_sl[kMaxNb];       // o * h - nb_sh, rounded to FP32
 };
 
 __device__ __forceinline__ double image_shift(const Grid &g, int img, int d) {
@@ -255,6 +267,41 @@ __device__ __forceinline__ void write_force(const ForceArgs &a, int slot, T vx, 
     }
 }
 
+// Buffer schedule (Sec. VI, Strategy 3): a task's partial force on a particle
+// goes to the buffer of the role it plays there -- buffer 0: the j side of
+// an intra-cell pair, 1..13: the j side of half-shell offset 1..13, 14: the
+// i side -- and every (buffer, particle) entry has exactly one writing task,
+// so plain stores suffice.  `add`: a later centre-cell chunk of the same
+// task adds to its own earlier store (same lane, program order).
+constexpr int kIBuf = kNumFbuf - 1;
+
+template <typename T>
+__device__ __forceinline__ T *fbuf(const ForceArgs &a) {
+    if constexpr (std::is_same<T, float>::value) return a.bf;
+    else return a.bd;
+}
+
+template <typename T>
+__device__ __forceinline__ void buffer_store(const ForceArgs &a, int buf, int slot, bool add, T vx, T vy, T vz) {
+    T *p = fbuf<T>(a) + (size_t)buf * 3 * a.n + slot;
+    if (add) { vx += p[0]; vy += p[a.n]; vz += p[2 * a.n]; }
+    p[0] = vx; p[a.n] = vy; p[2 * a.n] = vz;
+}
+
+// Fixed-order reduce of the buffer schedule: F = sum over the 15 buffers in
+// buffer order, in FP64 (deterministic; the FP32 partials convert exactly).
+template <typename T>
+__global__ void k_buffer_reduce(size_t n, const T *buf, double *fx, double *fy, double *fz) {
+    for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < n; s += (size_t)gridDim.x * blockDim.x) {
+        double f[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int b = 0; b < kNumFbuf; ++b)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) f[d] += (double)buf[((size_t)b * 3 + d) * n + s];
+        fx[s] = f[0]; fy[s] = f[1]; fz[s] = f[2];
+    }
+}
+
 // Exact FP64 cutoff decision, the definition's arithmetic (each op rounded once).
 __device__ __forceinline__ bool exact_inside(const ForceArgs &a, double rc2, int si, int sj, const double sL[3]) {
     double dx = __dsub_rn(__dsub_rn(a.x[si], a.x[sj]), sL[0]);
@@ -275,7 +322,7 @@ struct LaneEnergy {
 // A neighbour slot as loaded for one lane (prefetched one chunk ahead).
 struct JLoad {
     int w;            // slot | neighbour index << 26, or -1 past the list
-    float4 p;         // mixed: packed FP32 offsets + residuals
+    float4 p;         // mixed: FP32 offsets + packed residuals
     double x, y, z;   // FP64 path
 };
 
@@ -305,7 +352,7 @@ __device__ __forceinline__ void setup_neighbours(const ForceArgs &a, WarpSmem<ty
     // per-offset tables, the periodic image is kept as a code)
     if (lane < tc.nnb) {
         int o[3];
-        task_offset<MODE>(a.group, lane, tc.self, o);
+        task_offset<MODE>(tc.group, lane, tc.self, o);
         int c[3];
         int img = 0;
         for (int d = 0; d < 3; ++d) {
@@ -316,14 +363,60 @@ __device__ __forceinline__ void setup_neighbours(const ForceArgs &a, WarpSmem<ty
             img |= (sgn + 1) << (2 * d);
         }
         const int oi = (o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1);
-        for (int d = 0; d < 3; ++d) {
-            sm.nb_sh[lane][d] = tc.sh[oi][d];
-            sm.nb_sl[lane][d] = tc.sl[oi][d];
-        }
+        sm.nb_sh[lane] = make_float4(tc.sh[oi][0], tc.sh[oi][1], tc.sh[oi][2], 0.f);
+        sm.nb_sl[lane] = make_float4(tc.sl[oi][0], tc.sl[oi][1], tc.sl[oi][2], 0.f);
         sm.nb_img[lane] = img;
         const int B = tc.cell_off + c[0] + g.nc[0] * (c[1] + g.nc[1] * c[2]);
         sm.nb_start[lane] = a.start[B];
         sm.nb_count[lane] = a.count[B];
+    }
+    __syncwarp();
+}
+
+// Neighbour metadata of a task held in registers (lane b: entry b), so a
+// warp can issue the loads of its next task before computing the current one.
+struct NbPre {
+    int start, count;   // of neighbour entry `lane`
+    int img, oi;        // its periodic image code and offset index
+    int a0, na;         // the centre cell's first slot and count
+};
+
+template <int MODE>
+__device__ __forceinline__ NbPre load_neighbours(const ForceArgs &a, const TaskCells &tc, int lane) {
+    NbPre p;
+    p.start = 0; p.count = 0; p.img = 0; p.oi = 13;
+    if (lane < tc.nnb) {
+        const Grid &g = *tc.g;
+        int o[3];
+        task_offset<MODE>(tc.group, lane, tc.self, o);
+        int c[3];
+        int img = 0;
+        for (int d = 0; d < 3; ++d) {
+            c[d] = tc.cA[d] + o[d];
+            int sgn = 0;
+            if (c[d] >= g.nc[d]) { c[d] -= g.nc[d]; sgn = 1; }
+            else if (c[d] < 0) { c[d] += g.nc[d]; sgn = -1; }
+            img |= (sgn + 1) << (2 * d);
+        }
+        p.oi = (o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1);
+        p.img = img;
+        const int B = tc.cell_off + c[0] + g.nc[0] * (c[1] + g.nc[1] * c[2]);
+        p.start = a.start[B];
+        p.count = a.count[B];
+    }
+    p.a0 = a.start[tc.A];
+    p.na = a.count[tc.A];
+    return p;
+}
+
+template <typename S>
+__device__ __forceinline__ void commit_neighbours(S &sm, const TaskCells &tc, const NbPre &p, int lane) {
+    if (lane < tc.nnb) {
+        sm.nb_sh[lane] = make_float4(tc.sh[p.oi][0], tc.sh[p.oi][1], tc.sh[p.oi][2], 0.f);
+        sm.nb_sl[lane] = make_float4(tc.sl[p.oi][0], tc.sl[p.oi][1], tc.sl[p.oi][2], 0.f);
+        sm.nb_img[lane] = p.img;
+        sm.nb_start[lane] = p.start;
+        sm.nb_count[lane] = p.count;
     }
     __syncwarp();
 }
@@ -346,6 +439,28 @@ __device__ __forceinline__ int fill_batch(S &sm, int nnb, int &b, int &kin, int 
     return nj;
 }
 
+// The task's whole neighbour list in one pass: lane b (< nnb) writes the
+// entries of neighbour b at its exclusive prefix of the counts.  Returns the
+// total; the list is written only if it fits (total <= kJCap), otherwise
+// the caller walks it in batches with fill_batch.
+template <typename S>
+__device__ __forceinline__ int list_all(S &sm, const NbPre &pre, int nnb, int lane) {
+    const int cnt = lane < nnb ? pre.count : 0;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < kWarp; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(kFull, incl, kWarp - 1);
+    if (total <= kJCap) {
+        const int base = incl - cnt;
+        for (int k = 0; k < cnt; ++k) sm.jl[base + k] = (pre.start + k) | (lane << 26);
+    }
+    __syncwarp();
+    return total;
+}
+
 // Reduce-scatter the i chunk's per-lane partials and let the owner lanes
 // write them (plus the near-r_c corrections of the mixed path).
 template <bool MIXED, int NI, int MODE, typename T, typename S>
@@ -362,7 +477,8 @@ __device__ __forceinline__ void write_i_chunk(const ForceArgs &a, S &sm, T (&ax)
             if constexpr (MIXED) {
                 ax[0] += sm.corr[elem][0]; ay[0] += sm.corr[elem][1]; az[0] += sm.corr[elem][2];
             }
-            write_force<MODE, MIXED, T>(a, a0 + ii, ax[0], ay[0], az[0]);
+            if constexpr (MODE == kBuffer) buffer_store<T>(a, kIBuf, a0 + ii, false, ax[0], ay[0], az[0]);
+            else write_force<MODE, MIXED, T>(a, a0 + ii, ax[0], ay[0], az[0]);
         }
     }
     __syncwarp();
@@ -386,15 +502,17 @@ __device__ __forceinline__ void pair_loop(const WarpSmem<float> &sm, const float
     for (int m = 0; m < NI / 2; ++m) {
         const float4 A = lds4(&sm.ipa[m]);
         const float4 B = lds4(&sm.ipb[m]);
+        const float4 C = lds4(&sm.ipc[m]);
         bool oka = true, okb = true;
         if (SELF) {
-            const int sa = __float_as_int(B.z), sb = __float_as_int(B.w);
-            oka = N3 ? (sa < jlim) : (sa != jexcl);
-            okb = N3 ? (sb < jlim) : (sb != jexcl);
+            const int2 sl = sm.islot2[m];
+            oka = N3 ? (sl.x < jlim) : (sl.x != jexcl);
+            okb = N3 ? (sl.y < jlim) : (sl.y != jexcl);
         }
-        const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), npx), nlx);
-        const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), npy), nly);
-        const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), npz), nlz);
+        // d = (x_i - x_j,hi) + (r_i - x_j,lo): both residuals carried
+        const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), npx), __fadd2_rn(make_float2(C.x, C.y), nlx));
+        const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), npy), __fadd2_rn(make_float2(C.z, C.w), nly));
+        const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), npz), __fadd2_rn(make_float2(B.z, B.w), nlz));
         const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
         const bool neara = oka && (r2.x < rc2hi), nearb = okb && (r2.y < rc2hi);
         const bool hita = neara && (r2.x < rc2lo), hitb = nearb && (r2.y < rc2lo);
@@ -449,13 +567,14 @@ __device__ __forceinline__ void box_stats(const ForceArgs &a, int box, double s6
 }
 
 template <int NI, int MODE, bool STATS, bool BATCHED>
-__device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const TaskCells &tc, int lane, LaneEnergy &le) {
+__device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const TaskCells &tc, const NbPre &pre,
+                               int lane, LaneEnergy &le) {
     constexpr bool N3 = (MODE != kFullShell);
     const Grid &g = *tc.g;
-    setup_neighbours<true, MODE>(a, sm, tc, lane);
-    const int a0 = a.start[tc.A];
-    const int na = a.count[tc.A];
+    const int a0 = pre.a0;
+    const int na = pre.na;
     const float rc2lo = g.rc2f_lo, rc2hi = g.rc2f_hi;
+    const int total = list_all(sm, pre, tc.nnb, lane);   // reused by every i chunk
 
     for (int i0 = 0; i0 < na; i0 += NI) {
         if (lane < NI) {   // stage the i chunk (far-away sentinels past the end)
@@ -464,11 +583,17 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
             if (ii < na) p = a.p4[a0 + ii];
             float *A = reinterpret_cast<float *>(sm.ipa);
             float *B = reinterpret_cast<float *>(sm.ipb);
+            float *C = reinterpret_cast<float *>(sm.ipc);
+            int *S = reinterpret_cast<int *>(sm.islot2);
             const int m = lane >> 1, h = lane & 1;
+            const unsigned q = ii < na ? __float_as_uint(p.w) : 0x20080200u;   // all three residuals zero
             A[4 * m + h] = p.x;
             A[4 * m + 2 + h] = p.y;
             B[4 * m + h] = p.z;
-            B[4 * m + 2 + h] = __int_as_float(ii < na ? a0 + ii : 0x7fffffff);
+            B[4 * m + 2 + h] = lo_residual(q, 2);
+            C[4 * m + h] = lo_residual(q, 0);
+            C[4 * m + 2 + h] = lo_residual(q, 1);
+            S[2 * m + h] = ii < na ? a0 + ii : 0x7fffffff;
             sm.corr[lane][0] = sm.corr[lane][1] = sm.corr[lane][2] = 0.f;
         }
         float2 ax2[NI / 2], ay2[NI / 2], az2[NI / 2];
@@ -480,7 +605,9 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
 
         int b = 0, kin = 0;
         while (b < tc.nnb) {
-            const int nj = fill_batch(sm, tc.nnb, b, kin, lane);
+            int nj = total;
+            if (total <= kJCap) b = tc.nnb;                  // listed once above
+            else nj = fill_batch(sm, tc.nnb, b, kin, lane);  // long lists: in batches
             JLoad nxt = load_j<true>(a, sm.jl, lane, nj);
             for (int jc = 0; jc < nj; jc += kWarp) {
                 const JLoad cur = nxt;
@@ -496,16 +623,17 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
                 // plus the stored rounding residual
                 float pj[3] = {-1.0e15f, -1.0e15f, -1.0e15f}, lj[3] = {0.f, 0.f, 0.f};
                 if (valid) {
-                    const unsigned q = __float_as_uint(cur.p.w);
+                    const float4 Sh4 = sm.nb_sh[nb], Sl4 = sm.nb_sl[nb];
                     const float pin[3] = {cur.p.x, cur.p.y, cur.p.z};
+                    const unsigned q = __float_as_uint(cur.p.w);
+                    const float res[3] = {lo_residual(q, 0), lo_residual(q, 1), lo_residual(q, 2)};
+                    const float Sh[3] = {Sh4.x, Sh4.y, Sh4.z}, Sl[3] = {Sl4.x, Sl4.y, Sl4.z};
 #pragma unroll
                     for (int d = 0; d < 3; ++d) {
-                        const float Sh = sm.nb_sh[nb][d];
-                        const float sum = Sh + pin[d];
-                        const float err = pin[d] - (sum - Sh);
-                        const float res = (float)((int)((q >> (10 * d)) & 1023u) - 512) * kLoUnit;
+                        const float sum = Sh[d] + pin[d];
+                        const float err = pin[d] - (sum - Sh[d]);
                         pj[d] = sum;
-                        lj[d] = (err + res) + sm.nb_sl[nb][d];
+                        lj[d] = (err + res[d]) + Sl[d];
                     }
                 }
                 float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;   // sum of f d over the i's (j gets -g)
@@ -525,11 +653,11 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
                     for (int d = 0; d < 3; ++d) sL[d] = image_shift(g, sm.nb_img[nb], d);
 #pragma unroll 1
                     for (int k = 0; k < NI; ++k) {
-                        const int si = __float_as_int(staged(sm.ipb, k, 1));
+                        const int si = reinterpret_cast<const int *>(sm.islot2)[k];
                         const bool ok = N3 ? (si < jlim) : (si != jexcl);
-                        const float dx = (staged(sm.ipa, k, 0) - pj[0]) - lj[0];
-                        const float dy = (staged(sm.ipa, k, 1) - pj[1]) - lj[1];
-                        const float dz = (staged(sm.ipb, k, 0) - pj[2]) - lj[2];
+                        const float dx = (staged(sm.ipa, k, 0) + -pj[0]) + (staged(sm.ipc, k, 0) + -lj[0]);
+                        const float dy = (staged(sm.ipa, k, 1) + -pj[1]) + (staged(sm.ipc, k, 1) + -lj[1]);
+                        const float dz = (staged(sm.ipb, k, 0) + -pj[2]) + (staged(sm.ipb, k, 1) + -lj[2]);
                         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                         if (valid && ok && r2 < rc2hi && !(r2 < rc2lo) && exact_inside(a, g.rc2, si, sj, sL)) {
                             const float inv = rcp_nr(r2);
@@ -545,7 +673,10 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
                         }
                     }
                 }
-                if (N3 && valid) write_force<MODE, true, float>(a, sj, fjx, fjy, fjz);
+                if (N3 && valid) {
+                    if constexpr (MODE == kBuffer) buffer_store<float>(a, nb, sj, i0 > 0, fjx, fjy, fjz);
+                    else write_force<MODE, true, float>(a, sj, fjx, fjy, fjz);
+                }
             }
             __syncwarp();
         }
@@ -631,7 +762,10 @@ __device__ void run_task_fp64(const ForceArgs &a, WarpSmem<double> &sm, const Ta
                     e12 += s6 * s6;
                     npair += hit ? 1 : 0;
                 }
-                if (N3 && valid) write_force<MODE, false, double>(a, sj, fjx, fjy, fjz);
+                if (N3 && valid) {
+                    if constexpr (MODE == kBuffer) buffer_store<double>(a, nb, sj, i0 > 0, fjx, fjy, fjz);
+                    else write_force<MODE, false, double>(a, sj, fjx, fjy, fjz);
+                }
             }
             __syncwarp();
         }
@@ -660,10 +794,18 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
     le.s12 = make_float2(0.f, 0.f);
     le.d6 = le.d12 = 0.0;
     le.pairs = 0;
-    for (int t = w; t < a.ntasks; t += W) {
-        TaskCells tc = make_task<MODE, BATCHED>(a, t);
-        if constexpr (MIXED) run_task_mixed<NI, MODE, STATS, BATCHED>(a, sm, tc, lane, le);
-        else run_task_fp64<NI, MODE, BATCHED>(a, sm, tc, lane, le);
+    if constexpr (MIXED) {
+        for (int t = w; t < a.ntasks; t += W) {
+            const TaskCells tc = make_task<MODE, BATCHED>(a, t);
+            const NbPre pre = load_neighbours<MODE>(a, tc, lane);
+            commit_neighbours(sm, tc, pre, lane);
+            run_task_mixed<NI, MODE, STATS, BATCHED>(a, sm, tc, pre, lane, le);
+        }
+    } else {
+        for (int t = w; t < a.ntasks; t += W) {
+            TaskCells tc = make_task<MODE, BATCHED>(a, t);
+            run_task_fp64<NI, MODE, BATCHED>(a, sm, tc, lane, le);
+        }
     }
     // warp reduction of the energy partials in FP64, fixed order
     double s6 = MIXED ? (f32_to_f64_bits(le.s6.x) - f32_to_f64_bits(le.s6.y)) : le.d6;
@@ -676,6 +818,124 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
         np += __shfl_xor_sync(kFull, np, m);
     }
     if (STATS && !BATCHED && lane == 0) {
+        a.warp_acc[4 * w + 0] += s6;
+        a.warp_acc[4 * w + 1] += s12;
+        a.warp_pairs[w] += np;
+    }
+}
+
+// ------------------------------------------------ device task DAG ----
+// Sec. VI, Strategy 2 and Sec. III / V: the tasks of one creation order run
+// as a dependency-counted DAG.  A persistent warp claims the next queue slot,
+// waits (bounded) until a ready task is published there, runs it -- one
+// cell-cell interaction, exclusive plain writes to both cells, which the DAG
+// orders -- and then decrements its successors' counters; the warp that
+// drops a counter to zero publishes that task.
+struct DagArgs {
+    const int *task, *succ_start, *succ;
+    int *cnt, *queue, *ctrl, *err;
+    int32_t *trace;              // optional [2T]: start and end stamps of each task
+    int ntasks;
+    long long wait_ns;           // limit of one wait for a queue slot
+};
+
+constexpr unsigned kDagMaxSpins = 1u << 24;   // second bound on one wait
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Task (A, k): k = 0 the intra-cell interaction of A, k = 1..13 the pair
+// (A, A + half-shell offset k - 1).
+__device__ __forceinline__ TaskCells dag_task(const ForceArgs &a, int A, int k) {
+    TaskCells tc;
+    tc.g = &a.g; tc.sh = a.sh; tc.sl = a.sl; tc.cell_off = 0; tc.box = 0;
+    tc.A = A;
+    cell_xyz(a.g, A, tc.cA);
+    tc.self = (k == 0);
+    tc.group = k > 0 ? k - 1 : 0;
+    tc.nnb = 1;
+    return tc;
+}
+
+template <bool MIXED, int NI>
+__global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force_dag(ForceArgs a, DagArgs d) {
+    using T = typename std::conditional<MIXED, float, double>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    WarpSmem<T> &sm = reinterpret_cast<WarpSmem<T> *>(smem_raw)[wib];
+    const int w = blockIdx.x * (blockDim.x >> 5) + wib;
+    LaneEnergy le;
+    le.s6 = make_float2(0.f, 0.f);
+    le.s12 = make_float2(0.f, 0.f);
+    le.d6 = le.d12 = 0.0;
+    le.pairs = 0;
+    for (;;) {
+        int pos = 0;
+        if (lane == 0) pos = atomicAdd(d.ctrl + 0, 1);
+        pos = __shfl_sync(kFull, pos, 0);
+        if (pos >= d.ntasks) break;
+        int tid = -1;
+        if (lane == 0) {
+            const unsigned long long t0 = global_ns();
+            bool gave_up = true;
+            for (unsigned it = 0; it < kDagMaxSpins; ++it) {
+                tid = ld_acquire(d.queue + pos);
+                if (tid >= 0) { gave_up = false; break; }
+                if ((it & 15) == 15) {
+                    if (ld_acquire(d.err) & kErrTimeout) break;              // another warp gave up
+                    if ((long long)(global_ns() - t0) > d.wait_ns) break;
+                }
+                __nanosleep(200);
+            }
+            if (gave_up) { atomicOr(d.err, kErrTimeout); tid = -1; }
+        }
+        tid = __shfl_sync(kFull, tid, 0);
+        __syncwarp();                   // order the lanes' reads after lane 0's acquire
+        if (tid < 0) break;
+        if (d.trace && lane == 0) d.trace[2 * tid] = atomicAdd(d.ctrl + 2, 1);
+        const int code = d.task[tid];
+        const TaskCells tc = dag_task(a, code >> 4, code & 15);
+        if constexpr (MIXED) {
+            const NbPre pre = load_neighbours<kDag>(a, tc, lane);
+            commit_neighbours(sm, tc, pre, lane);
+            run_task_mixed<NI, kDag, true, false>(a, sm, tc, pre, lane, le);
+        } else {
+            run_task_fp64<NI, kDag, false>(a, sm, tc, lane, le);
+        }
+        __threadfence();                // each lane: its force writes before the release
+        __syncwarp();
+        if (d.trace && lane == 0) d.trace[2 * tid + 1] = atomicAdd(d.ctrl + 2, 1);
+        const int e1 = d.succ_start[tid + 1];
+        for (int e = d.succ_start[tid] + lane; e < e1; e += kWarp) {
+            const int sc = d.succ[e];
+            if (atomicSub(d.cnt + sc, 1) == 1) {
+                const int p = atomicAdd(d.ctrl + 1, 1);
+                st_release(d.queue + p, sc);
+            }
+        }
+    }
+    double s6 = MIXED ? (f32_to_f64_bits(le.s6.x) - f32_to_f64_bits(le.s6.y)) : le.d6;
+    double s12 = MIXED ? (f32_to_f64_bits(le.s12.x) - f32_to_f64_bits(le.s12.y)) : le.d12;
+    long long np = le.pairs;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        s6 += __shfl_xor_sync(kFull, s6, m);
+        s12 += __shfl_xor_sync(kFull, s12, m);
+        np += __shfl_xor_sync(kFull, np, m);
+    }
+    if (lane == 0) {
         a.warp_acc[4 * w + 0] += s6;
         a.warp_acc[4 * w + 1] += s12;
         a.warp_pairs[w] += np;
@@ -787,6 +1047,19 @@ static cudaError_t launch_mode(Ctx *c, ForceArgs &a, cudaStream_t s, bool stats)
     return launch_one<MIXED, NI, MODE, (MIXED ? false : true), false>(c, a, s);
 }
 
+// FP32 shift tables o * h = sh + sl for the 27 offsets.
+static void fill_shift_tables(const Ctx *c, ForceArgs &a) {
+    for (int oi = 0; oi < 27; ++oi) {
+        const int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, oi / 9 - 1};
+        for (int d = 0; d < 3; ++d) {
+            const double S = (double)o[d] * c->g.h[d];
+            const float Sh = (float)S;
+            a.sh[oi][d] = Sh;
+            a.sl[oi][d] = (float)(S - (double)Sh);
+        }
+    }
+}
+
 template <bool MIXED, int NI>
 static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *launches, bool stats) {
     ForceArgs a;
@@ -803,15 +1076,10 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
     a.cell_box = c->d_cell_box;
     a.box_acc = c->d_box_acc;
     a.box_pairs = c->d_box_pairs;
-    for (int oi = 0; oi < 27; ++oi) {
-        const int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, oi / 9 - 1};
-        for (int d = 0; d < 3; ++d) {
-            const double S = (double)o[d] * c->g.h[d];
-            const float Sh = (float)S;
-            a.sh[oi][d] = Sh;
-            a.sl[oi][d] = (float)(S - (double)Sh);
-        }
-    }
+    a.bf = static_cast<float *>(c->d_fbuf);
+    a.bd = static_cast<double *>(c->d_fbuf);
+    a.n = (size_t)c->n;
+    fill_shift_tables(c, a);
     cudaError_t e = cudaSuccess;
     const size_t nbytes = sizeof(double) * (size_t)c->n;
     if (sched == LC_SCHED_COLOUR) {
@@ -842,6 +1110,17 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
         a.ntasks = c->g.ncell;   // a batch: the total cell count of all boxes
         e = launch_mode<MIXED, NI, kAtomic>(c, a, s, stats);
         ++*launches;
+    } else if (sched == LC_SCHED_BUFFER) {
+        // every buffer entry is written by its one task: no clearing
+        using T = typename std::conditional<MIXED, float, double>::type;
+        a.ntasks = c->g.ncell;
+        e = launch_mode<MIXED, NI, kBuffer>(c, a, s, stats);
+        ++*launches;
+        if (e) return e;
+        k_buffer_reduce<T><<<c->num_sms * 8, 256, 0, s>>>((size_t)c->n, static_cast<const T *>(c->d_fbuf),
+                                                         c->fx, c->fy, c->fz);
+        ++*launches;
+        e = cudaGetLastError();
     } else {
         a.ntasks = c->g.ncell;
         e = launch_mode<MIXED, NI, kFullShell>(c, a, s, stats);
@@ -851,6 +1130,71 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
 }
 
 int force_grid_warps(const Ctx *c) { return c->nwarp_max; }
+
+template <bool MIXED>
+static cudaError_t launch_dag(Ctx *c, const DagDev *dd, long long wait_ns, int32_t *trace, cudaStream_t s) {
+    ForceArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = c->g;
+    a.p4 = c->d_p4;
+    a.x = c->cur.x; a.y = c->cur.y; a.z = c->cur.z;
+    a.start = c->d_start; a.count = c->d_count;
+    a.fx = c->fx; a.fy = c->fy; a.fz = c->fz;
+    a.kx = c->kx; a.ky = c->ky; a.kz = c->kz;
+    a.warp_acc = c->d_warp_acc; a.warp_pairs = c->d_warp_pairs;
+    a.stats = 1;
+    fill_shift_tables(c, a);
+    DagArgs d;
+    d.task = dd->task; d.succ_start = dd->succ_start; d.succ = dd->succ;
+    d.cnt = dd->cnt; d.queue = dd->queue; d.ctrl = dd->ctrl; d.err = c->d_err;
+    d.trace = trace;
+    d.ntasks = dd->ntasks;
+    d.wait_ns = wait_ns;
+    const int warps = c->warps;
+    const size_t smem = smem_bytes<MIXED, 16>(warps);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_dag<MIXED, 16>, warps * 32, smem);
+    if (e) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int blocks = c->num_sms * per_sm;
+    if (blocks > c->nwarp_max / warps) blocks = c->nwarp_max / warps;
+    // every warp may wait for another one: all of them must be resident
+    void *args[] = {&a, &d};
+    return cudaLaunchCooperativeKernel((const void *)k_force_dag<MIXED, 16>, dim3(blocks), dim3(warps * 32), args,
+                                      smem, s);
+}
+
+cudaError_t launch_forces_dag(Ctx *c, const DagDev *d, long long wait_ns, int withhold, int32_t *trace,
+                              cudaStream_t s, int *launches) {
+    cudaError_t e;
+    const bool mixed = (c->prec == LC_PREC_MIXED);
+    if ((e = cudaMemsetAsync(c->d_warp_acc, 0, sizeof(double) * 4 * (size_t)c->nwarp_max, s))) return e;
+    if ((e = cudaMemsetAsync(c->d_warp_pairs, 0, sizeof(long long) * (size_t)c->nwarp_max, s))) return e;
+    if (mixed) e = cudaMemsetAsync(c->kx, 0, 3 * sizeof(float2) * (size_t)c->n, s);
+    else e = cudaMemsetAsync(c->fx, 0, 3 * sizeof(double) * (size_t)c->n, s);
+    if (e) return e;
+    if ((e = cudaMemcpyAsync(d->cnt, d->pred_count, sizeof(int) * (size_t)d->ntasks, cudaMemcpyDeviceToDevice, s)))
+        return e;
+    if ((e = cudaMemcpyAsync(d->queue, d->queue_init, sizeof(int) * (size_t)d->ntasks, cudaMemcpyDeviceToDevice, s)))
+        return e;
+    if ((e = cudaMemcpyAsync(d->ctrl, d->ctrl_init, sizeof(int) * 4, cudaMemcpyDeviceToDevice, s))) return e;
+    if (withhold) {   // nothing published: every wait for a queue slot runs out
+        if ((e = cudaMemsetAsync(d->queue, 0xff, sizeof(int) * (size_t)d->ntasks, s))) return e;
+        if ((e = cudaMemsetAsync(d->ctrl + 1, 0, sizeof(int), s))) return e;
+    }
+    e = mixed ? launch_dag<true>(c, d, wait_ns, trace, s) : launch_dag<false>(c, d, wait_ns, trace, s);
+    if (e) return e;
+    ++*launches;
+    if (mixed) {
+        k_kahan_finalize<<<c->num_sms * 8, 256, 0, s>>>((int)c->n, c->kx, c->ky, c->kz, c->fx, c->fy, c->fz);
+        ++*launches;
+        if ((e = cudaGetLastError())) return e;
+    }
+    c->stats_full = 0;
+    e = launch_energy_reduce(c, s, 0);
+    ++*launches;
+    return e;
+}
 
 cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launches, bool stats) {
     cudaError_t e;
@@ -895,7 +1239,7 @@ cudaError_t launch_schedule_check(Ctx *c, lc_schedule sched, cudaStream_t s) {
                          c->g.class_count[2][raw / 9];
                 k_check<kColour><<<blocks, 256, 0, s>>>(c->g, g, k, nt, phase, c->d_stamp, c->d_visit, c->d_counters);
             }
-    } else if (sched == LC_SCHED_ATOMIC) {
+    } else if (sched == LC_SCHED_ATOMIC || sched == LC_SCHED_BUFFER) {
         k_check<kAtomic><<<blocks, 256, 0, s>>>(c->g, 0, 0, c->g.ncell, 0, c->d_stamp, c->d_visit, c->d_counters);
     } else {
         k_check<kFullShell><<<blocks, 256, 0, s>>>(c->g, 0, 0, c->g.ncell, 0, c->d_stamp, c->d_visit, c->d_counters);
@@ -911,9 +1255,11 @@ static cudaError_t attrs_for() {
     if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kColour, STATS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
     if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kAtomic, STATS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
     if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kFullShell, STATS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kBuffer, STATS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
     if constexpr (NI == 16) {
         if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kAtomic, STATS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
         if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kFullShell, STATS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+        if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kBuffer, STATS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
     }
     return cudaSuccess;
 }
@@ -922,6 +1268,11 @@ static cudaError_t attrs_for() {
 // (called once per context, before any stream capture).
 cudaError_t init_force_kernels() {
     cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_force_dag<true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_bytes<true, 16>(8))) ||
+        (e = cudaFuncSetAttribute(k_force_dag<false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_bytes<false, 16>(8))))
+        return e;
     if ((e = attrs_for<true, 8, true>()) || (e = attrs_for<true, 16, true>()) || (e = attrs_for<true, 8, false>()) ||
         (e = attrs_for<true, 16, false>()) || (e = attrs_for<false, 8, true>()) || (e = attrs_for<false, 16, true>()))
         return e;

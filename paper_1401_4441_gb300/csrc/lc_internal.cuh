@@ -17,10 +17,17 @@ constexpr int64_t kMaxParticles = int64_t(1) << 26;
 // below 1e-6 relative for cell-local coordinates; see lc_force.cu).
 constexpr float kCutBand = 4.0e-6f;
 
-// Rounding residuals of the FP32 cell-local coordinates are stored as
+constexpr int kNumSched = 4;     // colour, atomic, full shell, buffer
+constexpr int kNumFbuf = 15;     // buffer schedule: intra j side, 13 offsets, i side
+
+// Rounding residuals of the FP32 cell-local offsets are stored as
 // q = rint(r * kLoScale), |q| <= 511, i.e. in units of 2^-23 / 511.
-constexpr double kLoScale = 511.0 * 8388608.0;
+constexpr float kLoScale = (float)(511.0 * 8388608.0);
 constexpr float kLoUnit = (float)(1.0 / (511.0 * 8388608.0));
+
+__device__ __forceinline__ float lo_residual(unsigned w, int d) {
+    return (float)((int)((w >> (10 * d)) & 1023u) - 512) * kLoUnit;
+}
 
 // Error flags raised on the device (bit mask in Ctx::d_err).
 enum : int { kErrNonfinite = 1, kErrTimeout = 2 };
@@ -43,6 +50,9 @@ struct Grid {
     int class_count[3][3];   // cells of colour class a along dimension d
     int colour_of_raw[27];   // raw colour cx + 3 cy + 9 cz -> colour rank (-1 absent)
     int raw_of_colour[27];   // inverse
+    // ceil(2^64 / nc_x) and ceil(2^64 / (nc_x nc_y)): the high word of
+    // c * div is the exact quotient for every 32-bit cell index c
+    unsigned long long divx, divxy;
 };
 
 // Offsets of the 27-cell stencil and the phase groups, in constant memory.
@@ -76,6 +86,24 @@ struct State {
     int *id;               // particle ID of each slot
 };
 
+// Task DAG of one task-creation order (Sec. III, Sec. V, Sec. VI Strategy 2):
+// tasks are cell-cell interactions (cell A, k) with k = 0 intra-cell and
+// k = 1..13 half-shell offset k - 1; a task depends on the last earlier task
+// that touched either of its cells (both are inout).
+struct DagDev {
+    int ntasks, nroots;
+    int64_t nedges, critical_path;
+    int *task;          // [T] creation order: A << 4 | k
+    int *succ_start;    // [T + 1] CSR of the successors
+    int *succ;          // [E]
+    int *pred_count;    // [T] predecessors of each task
+    int *cnt;           // [T] unfinished predecessors (reset per evaluation)
+    int *queue;         // [T] ready tasks in publication order, -1 = not yet
+    int *queue_init;    // [T] the roots in creation order, then -1
+    int *ctrl;          // [4] next slot to claim, next slot to publish, trace clock, spare
+    int *ctrl_init;     // [4] 0, nroots, 0, 0
+};
+
 struct Ctx {
     Grid g;
     int64_t n;
@@ -92,7 +120,7 @@ struct Ctx {
     int *d_key;            // slot -> particle ID (before the final ranking)
     int *d_blocksums;      // scan partials
     int8_t *d_colour;      // [ncell]
-    float4 *d_p4;          // FP32 cell-centre-local coordinates, sorted
+    float4 *d_p4;          // FP32 cell-centre offsets (sorted) + packed residuals
     // forces
     double *fx, *fy, *fz;  // FP64 forces in sorted order
     float2 *kx, *ky, *kz;  // Kahan (sum, compensation) accumulators, colour + mixed
@@ -120,9 +148,13 @@ struct Ctx {
     unsigned long long *d_box_pairs;
     double *d_box_out;        // [nbox][4] U, W, pairs, K
     int stats_full;           // last statistics came from the full shell
+    DagDev *dag[2];        // per task-creation order, built on first use
+    // buffer schedule: per-(cell, offset) private force buffers [15][3][n]
+    // (float for the mixed path, double for FP64), allocated on first use
+    void *d_fbuf;
     // graphs of two Verlet steps: one per (schedule, state-buffer parity)
-    cudaGraphExec_t graph[6];
-    double graph_dt[6];
+    cudaGraphExec_t graph[2 * kNumSched];
+    double graph_dt[2 * kNumSched];
     double *state_a;       // cur.x of buffer set A (parity reference)
 };
 
@@ -134,6 +166,16 @@ cudaError_t launch_kick(Ctx *c, double dt, cudaStream_t s);
 cudaError_t launch_kinetic(Ctx *c, cudaStream_t s);
 cudaError_t launch_energy_reduce(Ctx *c, cudaStream_t s, int full);
 cudaError_t launch_box_energy(Ctx *c, cudaStream_t s, int full);
+// Forces by executing a task DAG on the device (dependency counting, bounded
+// waits); trace: optional [2T] start / end stamps.
+// withhold != 0 publishes no ready task (a test of the bounded waits).
+cudaError_t launch_forces_dag(Ctx *c, const DagDev *d, long long wait_ns, int withhold, int32_t *trace,
+                              cudaStream_t s, int *launches);
+void make_stencil(Stencil *s);
+cudaError_t build_dag(const Ctx *c, const Stencil &st, int order, DagDev **out);
+void free_dag(DagDev *d);
+// Host-only DAG of a grid of nc cells (no device work): returns the critical path.
+int64_t dag_plan_host(const int nc[3], int order, int64_t *ntasks, int64_t *nedges);
 cudaError_t launch_box_kinetic(Ctx *c, cudaStream_t s);
 cudaError_t launch_colour(Ctx *c, cudaStream_t s);
 cudaError_t upload_stencil(const Stencil &st);

@@ -13,8 +13,10 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "liblc.so")
 
-SCHED = {"colour": 0, "atomic": 1, "fullshell": 2}
+SCHED = {"colour": 0, "atomic": 1, "fullshell": 2, "buffer": 3}
 PREC = {"fp64": 0, "mixed": 1}
+ORDER = {"cell": 0, "loopex": 1}
+DAG_WITHHOLD = 1
 GET = {"cell_count": 0, "cell_start": 1, "perm": 2, "colour": 3, "forces": 4, "pos": 5, "vel": 6}
 STATUS = {0: "LC_OK", 1: "LC_ERR_INVALID_ARG", 2: "LC_ERR_BOX_TOO_SMALL", 3: "LC_ERR_CUDA",
           4: "LC_ERR_OOM", 5: "LC_ERR_NONFINITE", 6: "LC_ERR_TIMEOUT", 7: "LC_ERR_STATE",
@@ -56,6 +58,9 @@ def _load():
         "lc_batch_create": ([ctypes.c_int32, dp, dp, lp, ctypes.c_int, ctx_pp], ctypes.c_int),
         "lc_batch_energies": ([vp, dp, dp, dp, lp, vp], ctypes.c_int),
         "lc_batch_info": ([vp, ip, lp, lp], ctypes.c_int),
+        "lc_dag_build": ([vp, ctypes.c_int, lp, lp, lp], ctypes.c_int),
+        "lc_dag_forces": ([vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, vp], ctypes.c_int),
+        "lc_dag_plan": ([ip, ctypes.c_int, lp, lp, lp], ctypes.c_int),
         "lc_destroy": ([vp], None),
         "lc_status_str": ([ctypes.c_int], ctypes.c_char_p),
     }
@@ -97,6 +102,16 @@ def _ptr(a):
     if hasattr(a, "data_ptr"):
         return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
     raise TypeError(f"unsupported array type {type(a)}")
+
+
+def dag_plan(nc, order="loopex"):
+    """(tasks, edges, critical path) of the task DAG of a grid of nc cells,
+    built on the host by the library (no GPU needed)."""
+    lib_ = _load()
+    arr = (ctypes.c_int32 * 3)(*[int(x) for x in nc])
+    t, e, cp = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib_.lc_dag_plan(arr, ORDER[order], ctypes.byref(t), ctypes.byref(e), ctypes.byref(cp)), "lc_dag_plan")
+    return t.value, e.value, cp.value
 
 
 class Box:
@@ -192,6 +207,22 @@ class Box:
         if code not in (0, 8):
             _check(code, "lc_schedule_check")
         return conflicts.value, cover.value
+
+    def dag_build(self, order="loopex"):
+        """(tasks, edges, critical path) of the task DAG of a creation order."""
+        t, e, cp = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(self._lib.lc_dag_build(self._h, ORDER[order], ctypes.byref(t), ctypes.byref(e), ctypes.byref(cp)),
+               "lc_dag_build")
+        return t.value, e.value, cp.value
+
+    def dag_forces(self, order="loopex", trace=None, wait_seconds=0.0, withhold=False, stream=None):
+        """Forces by running the task DAG on the device; trace: None or a CUDA
+        int32 tensor of 2 * tasks (start / end stamps)."""
+        tp, dev = _ptr(trace)
+        if trace is not None and not dev:
+            raise TypeError("trace must be a CUDA tensor")
+        _check(self._lib.lc_dag_forces(self._h, ORDER[order], float(wait_seconds), DAG_WITHHOLD if withhold else 0,
+                                       tp, _stream(stream)), "lc_dag_forces")
 
     def set_tile(self, ni=0, warps=0):
         _check(self._lib.lc_set_tile(self._h, int(ni), int(warps)), "lc_set_tile")

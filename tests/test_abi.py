@@ -49,3 +49,22 @@ def test_host_side_argument_checks(so):
     assert so.lc_create(box, -1.0, 10, 1, ctypes.byref(h)) == 1
     assert so.lc_create(box, 2.5, -1, 1, ctypes.byref(h)) == 1
     assert h.value is None
+
+
+def test_binding_enums_match_header():
+    """The Python binding's schedule, precision, array and status codes are
+    the values include/lc.h gives them."""
+    text = open(os.path.join(ROOT, "include", "lc.h")).read()
+    vals = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(LC_[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    from paper_1401_4441_gb300 import lc
+    for name, v in lc.SCHED.items():
+        assert vals[f"LC_SCHED_{name.upper()}"] == v
+    for name, v in lc.PREC.items():
+        assert vals[f"LC_PREC_{name.upper()}"] == v
+    for name, v in lc.GET.items():
+        assert vals[f"LC_GET_{name.upper()}"] == v
+    for name, v in lc.ORDER.items():
+        assert vals[f"LC_ORDER_{name.upper()}"] == v
+    for v, name in lc.STATUS.items():
+        assert vals[name] == v
+    assert len([k for k in vals if k.startswith("LC_SCHED_")]) == len(lc.SCHED)

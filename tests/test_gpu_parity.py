@@ -16,7 +16,7 @@ from paper_1401_4441_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 RC = 2.5
-SCHEDS = ["colour", "atomic", "fullshell"]
+SCHEDS = ["colour", "atomic", "fullshell", "buffer"]
 TOL = {"fp64": 1e-10, "mixed": 1e-5}
 
 
@@ -169,6 +169,27 @@ def test_forces_1m_mixed(lc, sched):
     b = inputs.workload("liquid1m")
     err = forces_case(lc, b["pos"], b["box"], "mixed", sched)
     print(f"1M {sched}: max |dF|/rms = {err:.3e}")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_buffer_schedule_reproducible(lc, prec):
+    """Buffer schedule (Sec. VI, Strategy 3): every partial force has its own
+    buffer entry and the reduce sums them in a fixed order, so repeated
+    evaluations and a fresh context give bit-identical forces and energies
+    (the atomic schedule's FP64 atomics make no such promise)."""
+    b = inputs.fcc_box(200_000, 0.8442, 0.72, seed=5, jitter=0.05)
+    runs = []
+    for _ in range(2):
+        with make(lc, b["pos"], b["box"], prec) as g:
+            for _ in range(2):
+                g.forces("buffer")
+                runs.append((g.get("forces"), g.energy()))
+    for f, e in runs[1:]:
+        assert np.array_equal(f, runs[0][0])
+        assert e == runs[0][1]
+    fref, U, W, npairs = oracle.lc_forces(b["pos"][:, 0], b["pos"][:, 1], b["pos"][:, 2], b["box"], RC)
+    err, _ = rel_force_err(runs[0][0], fref)
+    assert err <= TOL[prec]
 
 
 @pytest.mark.parametrize("sched", SCHEDS)
