@@ -183,18 +183,25 @@ __global__ void k_rank_gather(Grid g1, const BoxDev *__restrict__ boxes, const u
         const int s = src[t];
         const int my_id = key[t];
         const int c = cell[s];
+        // the particle's state is loaded before the rank loop so that its
+        // latency overlaps the key loads
+        double X[3] = {in.x[s], in.y[s], in.z[s]};
+        const double V[3] = {in.vx[s], in.vy[s], in.vz[s]};
         const int base = start[c], cnt = count[c];
-        int r = 0;
-        for (int k = 0; k < cnt; ++k) r += (key[base + k] < my_id) ? 1 : 0;
+        // four independent loads in flight per step (the keys are L1 hits
+        // shared with the cell's other slots; the loop is latency-bound)
+        int r = 0, k = 0;
+        for (; k + 4 <= cnt; k += 4) {
+            const int k0 = key[base + k], k1 = key[base + k + 1], k2 = key[base + k + 2], k3 = key[base + k + 3];
+            r += (k0 < my_id ? 1 : 0) + (k1 < my_id ? 1 : 0) + (k2 < my_id ? 1 : 0) + (k3 < my_id ? 1 : 0);
+        }
+        for (; k < cnt; ++k) r += (key[base + k] < my_id) ? 1 : 0;
         const int dst = base + r;
         const BoxDev *bd = BATCHED ? &boxes[slot_box[t]] : nullptr;
         const Grid &g = BATCHED ? bd->g : g1;
         const int cl = BATCHED ? c - bd->cell_off : c;
         int cc[3];
-        cc[0] = cl % g.nc[0];
-        cc[1] = (cl / g.nc[0]) % g.nc[1];
-        cc[2] = cl / (g.nc[0] * g.nc[1]);
-        double X[3] = {in.x[s], in.y[s], in.z[s]};
+        cell_coords(g, cl, cc);
         Split sp[3];
         bool fast = true;
 #pragma unroll
@@ -207,7 +214,7 @@ __global__ void k_rank_gather(Grid g1, const BoxDev *__restrict__ boxes, const u
             }
         }
         out.x[dst] = X[0]; out.y[dst] = X[1]; out.z[dst] = X[2];
-        out.vx[dst] = in.vx[s]; out.vy[dst] = in.vy[s]; out.vz[dst] = in.vz[s];
+        out.vx[dst] = V[0]; out.vy[dst] = V[1]; out.vz[dst] = V[2];
         out.id[dst] = my_id;
         if (write_p4) {
             // FP32 offset from the cell centre (c + 1/2) h, formed in

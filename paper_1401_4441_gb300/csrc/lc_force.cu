@@ -45,6 +45,7 @@ enum Mode : int { kColour = 0, kAtomic = 1, kFullShell = 2, kBuffer = 3, kDag = 
 
 constexpr int kJCap = 512;      // neighbour slots listed per batch (per warp)
 constexpr int kMaxNb = 27;      // neighbour cells per task
+constexpr int kJdCap = 256;     // pruned neighbours whose data is kept in shared memory
 
 struct ForceArgs {
     Grid g;
@@ -84,13 +85,7 @@ struct TaskCells {
     int box;
 };
 
-__device__ __forceinline__ void cell_xyz(const Grid &g, int c, int out[3]) {
-    const int q1 = (int)__umul64hi((unsigned long long)(unsigned)c, g.divx);    // c / nc_x
-    const int q2 = (int)__umul64hi((unsigned long long)(unsigned)c, g.divxy);   // c / (nc_x nc_y)
-    out[0] = c - q1 * g.nc[0];
-    out[1] = q1 - q2 * g.nc[1];
-    out[2] = q2;
-}
+__device__ __forceinline__ void cell_xyz(const Grid &g, int c, int out[3]) { cell_coords(g, c, out); }
 
 // Task t of a colour phase: the t-th cell (x fastest) of colour `colour`.
 __device__ __forceinline__ int colour_task_cell(const Grid &g, int colour, int t, int cA[3]) {
@@ -175,6 +170,8 @@ struct alignas(16) WarpSmem {
     T ix[32], iy[32], iz[32];   // FP64: centre-cell particles
     int islot[32];
     int jl[kJCap];              // slot | (neighbour index << 26)
+    int jk[kJCap];              // mixed: the entries of jl within r_c of the i chunk's box
+    float4 jd[kJdCap];          // mixed: their FP32 offsets + residuals (the first kJdCap)
     int nb_start[kMaxNb], nb_count[kMaxNb];
     int nb_img[kMaxNb];         // periodic image s_d in {-1,0,1} as (s+1) in 2-bit fields
     float4 nb_sh[kMaxNb];       // o * h rounded to FP32 (mixed), w unused
@@ -289,15 +286,37 @@ __device__ __forceinline__ void buffer_store(const ForceArgs &a, int buf, int sl
 }
 
 // Fixed-order reduce of the buffer schedule: F = sum over the 15 buffers in
-// buffer order, in FP64 (deterministic; the FP32 partials convert exactly).
+// buffer order (deterministic).  FP32 partials are summed as an unevaluated
+// pair hi + lo with Knuth's TwoSum (every rounding error kept, no FP64 pipe:
+// GB300 runs FP64 at a small fraction of the FP32 rate); FP64 partials of
+// the FP64 path are added in FP64.
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float v) {
+    const float s = hi + v;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (v - bb);
+    hi = s;
+    lo += e;
+}
+
 template <typename T>
 __global__ void k_buffer_reduce(size_t n, const T *buf, double *fx, double *fy, double *fz) {
     for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < n; s += (size_t)gridDim.x * blockDim.x) {
-        double f[3] = {0.0, 0.0, 0.0};
+        double f[3];
+        if constexpr (std::is_same<T, float>::value) {
+            float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int b = 0; b < kNumFbuf; ++b)
+            for (int b = 0; b < kNumFbuf; ++b)
 #pragma unroll
-            for (int d = 0; d < 3; ++d) f[d] += (double)buf[((size_t)b * 3 + d) * n + s];
+                for (int d = 0; d < 3; ++d) two_sum_add(hi[d], lo[d], buf[((size_t)b * 3 + d) * n + s]);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) f[d] = f32_to_f64_bits(hi[d]) + f32_to_f64_bits(lo[d]);
+        } else {
+            f[0] = f[1] = f[2] = 0.0;
+#pragma unroll
+            for (int b = 0; b < kNumFbuf; ++b)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) f[d] += buf[((size_t)b * 3 + d) * n + s];
+        }
         fx[s] = f[0]; fy[s] = f[1]; fz[s] = f[2];
     }
 }
@@ -338,6 +357,18 @@ __device__ __forceinline__ JLoad load_j(const ForceArgs &a, const int *jl, int e
         } else {
             r.x = a.x[sj]; r.y = a.y[sj]; r.z = a.z[sj];
         }
+    }
+    return r;
+}
+
+// Mixed: entry e of a pruned list, its data from shared memory when the
+// prune staged it (jdata != nullptr), else from global memory.
+__device__ __forceinline__ JLoad load_j_staged(const ForceArgs &a, const int *jl, const float4 *jdata, int e, int nj) {
+    JLoad r;
+    r.w = -1;
+    if (e < nj) {
+        r.w = jl[e];
+        r.p = jdata ? jdata[e] : a.p4[r.w & ((1 << 26) - 1)];
     }
     return r;
 }
@@ -461,6 +492,72 @@ __device__ __forceinline__ int list_all(S &sm, const NbPre &pre, int nnb, int la
     return total;
 }
 
+// Keeps the entries of sm.jl[0 .. total) whose particle lies within r_c of
+// the box [bmin, bmax] spanned by the staged centre particles (FP32, with a
+// relative margin of 1e-4 on r_c^2, so no pair inside r_c is dropped) and
+// compacts them, in list order, into sm.jk.  Returns how many were kept.
+// Buffer schedule: a dropped neighbour's entry for this task is zero and is
+// written as such by the first centre chunk.
+template <int MODE>
+__device__ __forceinline__ void prune_test(const ForceArgs &a, const WarpSmem<float> &sm, int e, int total,
+                                           float3 bmin, float3 bmax, float keep2, bool first_chunk, int &w,
+                                           float4 &p, bool &keep) {
+    keep = false;
+    if (e < total) {
+        const int sj = w & ((1 << 26) - 1);
+        const float4 sh = sm.nb_sh[w >> 26];
+        const float px = p.x + sh.x, py = p.y + sh.y, pz = p.z + sh.z;
+        const float dx = fmaxf(fmaxf(bmin.x - px, px - bmax.x), 0.f);
+        const float dy = fmaxf(fmaxf(bmin.y - py, py - bmax.y), 0.f);
+        const float dz = fmaxf(fmaxf(bmin.z - pz, pz - bmax.z), 0.f);
+        keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < keep2;
+        if constexpr (MODE == kBuffer) {
+            if (!keep && first_chunk) buffer_store<float>(a, w >> 26, sj, false, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
+// Keeps the entries of sm.jl[0 .. total) whose particle lies within r_c of
+// the box [bmin, bmax] spanned by the staged centre particles (FP32, with a
+// relative margin of 1e-4 on r_c^2, so no pair inside r_c is dropped) and
+// compacts them, in list order, into sm.jk, their data into sm.jd (the
+// first kJdCap).  Returns how many were kept.  Buffer schedule: a dropped
+// neighbour's entry for this task is zero and is written as such by the
+// first centre chunk.
+template <int MODE>
+__device__ __forceinline__ int prune_list(const ForceArgs &a, WarpSmem<float> &sm, int total, float3 bmin,
+                                          float3 bmax, float keep2, bool first_chunk, int lane) {
+    int nk = 0;
+    const unsigned below = (1u << lane) - 1u;
+    for (int e0 = 0; e0 < total; e0 += 2 * kWarp) {
+        // two rounds per step: both loads in flight before either test
+        const int ea = e0 + lane, eb = e0 + kWarp + lane;
+        int wa = 0, wb = 0;
+        float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa;
+        if (ea < total) { wa = sm.jl[ea]; pa = a.p4[wa & ((1 << 26) - 1)]; }
+        if (eb < total) { wb = sm.jl[eb]; pb = a.p4[wb & ((1 << 26) - 1)]; }
+        bool ka, kb;
+        prune_test<MODE>(a, sm, ea, total, bmin, bmax, keep2, first_chunk, wa, pa, ka);
+        prune_test<MODE>(a, sm, eb, total, bmin, bmax, keep2, first_chunk, wb, pb, kb);
+        const unsigned ma = __ballot_sync(kFull, ka);
+        if (ka) {
+            const int pos = nk + __popc(ma & below);
+            sm.jk[pos] = wa;
+            if (pos < kJdCap) sm.jd[pos] = pa;
+        }
+        nk += __popc(ma);
+        const unsigned mb = __ballot_sync(kFull, kb);
+        if (kb) {
+            const int pos = nk + __popc(mb & below);
+            sm.jk[pos] = wb;
+            if (pos < kJdCap) sm.jd[pos] = pb;
+        }
+        nk += __popc(mb);
+    }
+    __syncwarp();
+    return nk;
+}
+
 // Reduce-scatter the i chunk's per-lane partials and let the owner lanes
 // write them (plus the near-r_c corrections of the mixed path).
 template <bool MIXED, int NI, int MODE, typename T, typename S>
@@ -577,10 +674,16 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
     const int total = list_all(sm, pre, tc.nnb, lane);   // reused by every i chunk
 
     for (int i0 = 0; i0 < na; i0 += NI) {
+        // bounding box of the chunk's particles (FP32 offsets), from the staging loads
+        float3 bmin = make_float3(1.0e30f, 1.0e30f, 1.0e30f), bmax = make_float3(-1.0e30f, -1.0e30f, -1.0e30f);
         if (lane < NI) {   // stage the i chunk (far-away sentinels past the end)
             const int ii = i0 + lane;
             float4 p = make_float4(1.0e15f, 1.0e15f, 1.0e15f, 0.f);
-            if (ii < na) p = a.p4[a0 + ii];
+            if (ii < na) {
+                p = a.p4[a0 + ii];
+                bmin = make_float3(p.x, p.y, p.z);
+                bmax = bmin;
+            }
             float *A = reinterpret_cast<float *>(sm.ipa);
             float *B = reinterpret_cast<float *>(sm.ipb);
             float *C = reinterpret_cast<float *>(sm.ipc);
@@ -596,6 +699,15 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
             S[2 * m + h] = ii < na ? a0 + ii : 0x7fffffff;
             sm.corr[lane][0] = sm.corr[lane][1] = sm.corr[lane][2] = 0.f;
         }
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) {
+            bmin.x = fminf(bmin.x, __shfl_xor_sync(kFull, bmin.x, m));
+            bmin.y = fminf(bmin.y, __shfl_xor_sync(kFull, bmin.y, m));
+            bmin.z = fminf(bmin.z, __shfl_xor_sync(kFull, bmin.z, m));
+            bmax.x = fmaxf(bmax.x, __shfl_xor_sync(kFull, bmax.x, m));
+            bmax.y = fmaxf(bmax.y, __shfl_xor_sync(kFull, bmax.y, m));
+            bmax.z = fmaxf(bmax.z, __shfl_xor_sync(kFull, bmax.z, m));
+        }
         float2 ax2[NI / 2], ay2[NI / 2], az2[NI / 2];
 #pragma unroll
         for (int k = 0; k < NI / 2; ++k) ax2[k] = ay2[k] = az2[k] = make_float2(0.f, 0.f);
@@ -606,12 +718,19 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
         int b = 0, kin = 0;
         while (b < tc.nnb) {
             int nj = total;
-            if (total <= kJCap) b = tc.nnb;                  // listed once above
-            else nj = fill_batch(sm, tc.nnb, b, kin, lane);  // long lists: in batches
-            JLoad nxt = load_j<true>(a, sm.jl, lane, nj);
+            const int *list = sm.jk;
+            if (total <= kJCap) {                            // listed once above: prune it
+                b = tc.nnb;
+                nj = prune_list<MODE>(a, sm, total, bmin, bmax, g.rc2f_hi * 1.0001f, i0 == 0, lane);
+            } else {                                         // long lists: in batches, unpruned
+                nj = fill_batch(sm, tc.nnb, b, kin, lane);
+                list = sm.jl;
+            }
+            const float4 *jdata = (list == sm.jk && nj <= kJdCap) ? sm.jd : nullptr;   // staged by the prune
+            JLoad nxt = load_j_staged(a, list, jdata, lane, nj);
             for (int jc = 0; jc < nj; jc += kWarp) {
                 const JLoad cur = nxt;
-                nxt = load_j<true>(a, sm.jl, jc + kWarp + lane, nj);   // prefetch
+                nxt = load_j_staged(a, list, jdata, jc + kWarp + lane, nj);   // prefetch
                 const bool valid = cur.w >= 0;
                 const int sj = valid ? (cur.w & ((1 << 26) - 1)) : 0x7fffffff;
                 const int nb = valid ? (cur.w >> 26) : 0;
@@ -1029,6 +1148,7 @@ static cudaError_t launch_one(Ctx *c, ForceArgs &a, cudaStream_t s) {
     const int warps = c->warps;
     const size_t sm = smem_bytes<MIXED, NI>(warps);
     const int blocks = force_blocks<MIXED, NI, MODE, STATS, BATCHED>(c);
+    if (blocks * warps > c->nwarp_used) c->nwarp_used = blocks * warps;
     k_force<MIXED, NI, MODE, STATS, BATCHED><<<blocks, warps * 32, sm, s>>>(a);
     return cudaGetLastError();
 }
@@ -1158,6 +1278,7 @@ static cudaError_t launch_dag(Ctx *c, const DagDev *dd, long long wait_ns, int32
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int blocks = c->num_sms * per_sm;
     if (blocks > c->nwarp_max / warps) blocks = c->nwarp_max / warps;
+    c->nwarp_used = blocks * warps;
     // every warp may wait for another one: all of them must be resident
     void *args[] = {&a, &d};
     return cudaLaunchCooperativeKernel((const void *)k_force_dag<MIXED, 16>, dim3(blocks), dim3(warps * 32), args,
@@ -1209,6 +1330,7 @@ cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launch
             if ((e = cudaMemsetAsync(c->d_warp_pairs, 0, sizeof(long long) * (size_t)c->nwarp_max, s))) return e;
         }
     }
+    c->nwarp_used = 0;
     if (c->ni == 8 && c->nbox == 0)
         e = mixed ? launch_sched<true, 8>(c, sched, s, launches, stats) : launch_sched<false, 8>(c, sched, s, launches, stats);
     else

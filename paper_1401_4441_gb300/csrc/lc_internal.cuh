@@ -55,6 +55,16 @@ struct Grid {
     unsigned long long divx, divxy;
 };
 
+// Cell coordinates of a cell index, the quotients by multiply-high with the
+// grid's precomputed ceil(2^64 / d) (exact for every 32-bit index).
+__device__ __forceinline__ void cell_coords(const Grid &g, int c, int out[3]) {
+    const int q1 = (int)__umul64hi((unsigned long long)(unsigned)c, g.divx);    // c / nc_x
+    const int q2 = (int)__umul64hi((unsigned long long)(unsigned)c, g.divxy);   // c / (nc_x nc_y)
+    out[0] = c - q1 * g.nc[0];
+    out[1] = q1 - q2 * g.nc[1];
+    out[2] = q2;
+}
+
 // Offsets of the 27-cell stencil and the phase groups, in constant memory.
 struct Stencil {
     int hs[13][3];      // forward half-shell, (z, y, x) lexicographic
@@ -131,6 +141,7 @@ struct Ctx {
     long long *d_npairs;
     int *d_err;
     int nwarp_max;
+    int nwarp_used;        // warps of the last force evaluation (their partials are reduced)
     // check buffers
     int *d_stamp;
     unsigned long long *d_visit;

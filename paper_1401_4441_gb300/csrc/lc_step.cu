@@ -11,6 +11,7 @@
 namespace lc {
 
 constexpr int kRedThreads = 1024;
+static_assert(kRedThreads == 32 * 32, "k_final_pot reduces one value per warp in a single warp");
 
 __global__ void k_kick_drift(int n, double half, double dt, State st, const double *__restrict__ fx,
                              const double *__restrict__ fy, const double *__restrict__ fz) {
@@ -56,31 +57,39 @@ __global__ void __launch_bounds__(256) k_kinetic(int n, State st, double *__rest
 __global__ void __launch_bounds__(kRedThreads) k_final_pot(int nw, const double *__restrict__ warp_acc,
                                                            const long long *__restrict__ warp_pairs, int full,
                                                            double *__restrict__ out, long long *__restrict__ npairs) {
-    __shared__ double r6[kRedThreads], r12[kRedThreads];
-    __shared__ long long rp[kRedThreads];
+    // per thread, then butterfly within each warp, then over the warps:
+    // a fixed order, so the sums are reproducible
+    __shared__ double r6[kRedThreads / 32], r12[kRedThreads / 32];
+    __shared__ long long rp[kRedThreads / 32];
     double a6 = 0.0, a12 = 0.0;
     long long ap = 0;
+#pragma unroll 4
     for (int w = threadIdx.x; w < nw; w += kRedThreads) {
         a6 += warp_acc[4 * w + 0];
         a12 += warp_acc[4 * w + 1];
         ap += warp_pairs[w];
     }
-    r6[threadIdx.x] = a6; r12[threadIdx.x] = a12; rp[threadIdx.x] = ap;
+    for (int m = 16; m >= 1; m >>= 1) {
+        a6 += __shfl_xor_sync(0xffffffffu, a6, m);
+        a12 += __shfl_xor_sync(0xffffffffu, a12, m);
+        ap += __shfl_xor_sync(0xffffffffu, ap, m);
+    }
+    if ((threadIdx.x & 31) == 0) { r6[threadIdx.x >> 5] = a6; r12[threadIdx.x >> 5] = a12; rp[threadIdx.x >> 5] = ap; }
     __syncthreads();
-    for (int m = kRedThreads / 2; m > 0; m >>= 1) {
-        if (threadIdx.x < m) {
-            r6[threadIdx.x] += r6[threadIdx.x + m];
-            r12[threadIdx.x] += r12[threadIdx.x + m];
-            rp[threadIdx.x] += rp[threadIdx.x + m];
+    if (threadIdx.x < 32) {
+        a6 = r6[threadIdx.x]; a12 = r12[threadIdx.x]; ap = rp[threadIdx.x];
+        for (int m = 16; m >= 1; m >>= 1) {
+            a6 += __shfl_xor_sync(0xffffffffu, a6, m);
+            a12 += __shfl_xor_sync(0xffffffffu, a12, m);
+            ap += __shfl_xor_sync(0xffffffffu, ap, m);
         }
-        __syncthreads();
     }
     if (threadIdx.x == 0) {
-        double s6 = r6[0], s12 = r12[0];
+        double s6 = a6, s12 = a12;
         double scale = full ? 0.5 : 1.0;       // the full shell sees each pair twice
         out[0] = scale * 4.0 * (s12 - s6);      // U = 4 sum (r^-12 - r^-6)
         out[1] = scale * 24.0 * (2.0 * s12 - s6);  // W = sum r.F = 24 sum (2 r^-12 - r^-6)
-        long long p = full ? rp[0] / 2 : rp[0];
+        long long p = full ? ap / 2 : ap;
         out[2] = (double)p;
         *npairs = p;
     }
@@ -164,7 +173,8 @@ cudaError_t launch_kinetic(Ctx *c, cudaStream_t s) {
 }
 
 cudaError_t launch_energy_reduce(Ctx *c, cudaStream_t s, int full) {
-    k_final_pot<<<1, kRedThreads, 0, s>>>(c->nwarp_max, c->d_warp_acc, c->d_warp_pairs, full,
+    const int nw = c->nwarp_used > 0 ? c->nwarp_used : c->nwarp_max;   // the rest are zero
+    k_final_pot<<<1, kRedThreads, 0, s>>>(nw, c->d_warp_acc, c->d_warp_pairs, full,
                                           c->d_result, c->d_npairs);
     return cudaGetLastError();
 }
