@@ -134,12 +134,12 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def half_shell_candidates(counts, nc):
+def half_shell_candidates(counts, nc, dims=3):
     """Candidate pairs of the half-shell sweep: intra n(n-1)/2 plus n_A n_B
-    over the 13 forward neighbour cells (periodic)."""
+    over the forward neighbour cells (periodic; 13 in 3D, 4 in 2D)."""
     c = counts.reshape(nc[2], nc[1], nc[0]).astype(np.int64)
     total = int((c * (c - 1) // 2).sum())
-    for oz in (-1, 0, 1):
+    for oz in ((0,) if dims == 2 else (-1, 0, 1)):
         for oy in (-1, 0, 1):
             for ox in (-1, 0, 1):
                 if not (oz > 0 or (oz == 0 and oy > 0) or (oz == 0 and oy == 0 and ox > 0)):
@@ -176,7 +176,16 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(pos, box, budget_s=12.0):
+def oracle_box(w):
+    """Box for the FP64 oracle: 2D workloads lie in the z = 0 plane of a box
+    whose z side is 3 r_c (no z image within r_c), which the oracle's 3D
+    routines turn into the 2D system."""
+    if w.get("dims", 3) == 2:
+        return np.array([w["box"][0], w["box"][1], 3.0 * w["rc"]])
+    return w["box"]
+
+
+def cpu_baseline(pos, box, rc, budget_s=12.0):
     """The FP64 oracle (as it stands) on this host: repeated link-cell force
     evaluations of the same box for about budget_s seconds, one core."""
     import oracle
@@ -184,7 +193,7 @@ def cpu_baseline(pos, box, budget_s=12.0):
     t0 = time.perf_counter()
     evals, pairs = 0, 0
     while True:
-        _, _, _, npairs = oracle.lc_forces(x, y, z, box, RC)
+        _, _, _, npairs = oracle.lc_forces(x, y, z, box, rc)
         evals += 1
         pairs += npairs
         if time.perf_counter() - t0 > budget_s or evals >= 8:
@@ -201,16 +210,16 @@ def run_reference(args, dist):
         return
     import oracle
     w = inputs.workload(args.workload)
-    pos, vel, box = w["pos"], w["vel"], w["box"]
-    f0, U, W, npairs0 = oracle.lc_forces(pos[:, 0], pos[:, 1], pos[:, 2], box, RC)
+    pos, vel, box, rc = w["pos"], w["vel"], oracle_box(w), w["rc"]
+    f0, U, W, npairs0 = oracle.lc_forces(pos[:, 0], pos[:, 1], pos[:, 2], box, rc)
     x, v, f = pos, vel, f0
     for _ in range(args.warmup):
-        x, v, f, e = oracle.verlet(x, v, box, RC, DT, 1, f=f)
+        x, v, f, e = oracle.verlet(x, v, box, rc, DT, 1, f=f)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        x, v, f, e = oracle.verlet(x, v, box, RC, DT, 1, f=f)
+        x, v, f, e = oracle.verlet(x, v, box, rc, DT, 1, f=f)
     elapsed = time.perf_counter() - t0
-    _, _, _, npairs1 = oracle.lc_forces(x[:, 0], x[:, 1], x[:, 2], box, RC)
+    _, _, _, npairs1 = oracle.lc_forces(x[:, 0], x[:, 1], x[:, 2], box, rc)
     pairs = 0.5 * (npairs0 + npairs1) * args.steps
     value = pairs / elapsed
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -226,7 +235,11 @@ def run_reference(args, dist):
 def workload_config(args, w):
     rc = w["rc"]
     nc = [int(math.floor(L / rc)) for L in w["box"]]
-    if inputs.WORKLOADS[args.workload].get("kind") == "slab":
+    if w.get("dims", 3) == 2:
+        desc = (f"{args.workload}: N={w['pos'].shape[0]} 2D triangular lattice + jitter "
+                f"{inputs.WORKLOADS[args.workload]['jitter']}, area density {w['rho']}, T={w['T']}, rc={rc}, "
+                f"periodic {w['box'][0]:.2f} x {w['box'][1]:.2f}, cells {nc[0]}x{nc[1]}, dt={DT}")
+    elif inputs.WORKLOADS[args.workload].get("kind") == "slab":
         desc = (f"{args.workload}: N={w['pos'].shape[0]} liquid slab 0.80 in x < Lx/3, vapour 0.02 elsewhere, "
                 f"uniform random positions, box {w['box'][0]:.2f} x {w['box'][1]:.2f} x {w['box'][2]:.2f}, "
                 f"rc={rc}, cells {nc[0]}x{nc[1]}x{nc[2]}; step = binning + one force evaluation")
@@ -249,7 +262,7 @@ def run_profile(args, dist):
     build.build()
     from paper_1401_4441_gb300 import lc
     w = inputs.workload(args.workload)
-    g = lc.Box(w["box"], w["rc"], w["pos"].shape[0], args.precision)
+    g = lc.Box(w["box"], w["rc"], w["pos"].shape[0], args.precision, dims=w.get("dims", 3))
     g.set_state(torch.from_numpy(w["pos"]).cuda(), torch.from_numpy(w["vel"]).cuda())
     sched = "atomic" if args.schedule == "auto" else args.schedule
     g.forces(sched)
@@ -374,7 +387,7 @@ def run_gb300(args, dist):
     n = pos.shape[0]
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    g = lc.Box(box, rc, n, args.precision)
+    g = lc.Box(box, rc, n, args.precision, dims=w.get("dims", 3))
     dpos = torch.from_numpy(pos).to(dev)
     dvel = torch.from_numpy(vel).to(dev)
     g.set_state(dpos, dvel)
@@ -442,7 +455,7 @@ def run_gb300(args, dist):
         g.forces(sched)
     counts = g.get("cell_count")
     nc, _, _ = g.grid()
-    cand = half_shell_candidates(counts, nc)
+    cand = half_shell_candidates(counts, nc, w.get("dims", 3))
     _, _, _, npairs_now = g.energy()
     flops = 8.0 * cand + 21.0 * npairs_now
     fts = []
@@ -489,7 +502,7 @@ def run_gb300(args, dist):
     g.close()
 
     if dist.rank == 0:
-        cpu = cpu_baseline(pos, box) if (dist.world == 1 and not args.no_cpu_baseline) else None
+        cpu = cpu_baseline(pos, oracle_box(w), rc) if (dist.world == 1 and not args.no_cpu_baseline) else None
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
@@ -518,7 +531,7 @@ def run_dag(args, dist):
     pos, box, rc = b["pos"], b["box"], b["rc"]
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    g = lc.Box(box, rc, pos.shape[0], args.precision)
+    g = lc.Box(box, rc, pos.shape[0], args.precision, dims=b.get("dims", 3))
     g.set_state(torch.from_numpy(pos).to(dev))
 
     def timed(fn, reps=3):

@@ -110,6 +110,17 @@ lc_status lc_create(const double box[3], double rc, int64_t n, lc_precision prec
 lc_status lc_set_state(lc_ctx *ctx, const double *pos, const double *vel, const int32_t *id,
                        int on_device, void *stream);
 
+/* A 2D context (Sec. IV, Fig. 3a: the paper's 2D link-cell case): particles in
+ * a periodic box[0] x box[1] rectangle, cells of side >= rc in x and y, the
+ * 5-cell half-shell stencil (Newton-3 schedules) or 9 cells (full shell).
+ * Positions and velocities keep the [n][3] layout: the z components are
+ * ignored on input (every particle lies in one plane, vz = 0) and returned
+ * as 0.  Every call below except the batch calls accepts a 2D context; the
+ * physics is the 2D Lennard-Jones system (same potential, in-plane
+ * distances).  Errors as lc_create; LC_ERR_BOX_TOO_SMALL if box[0] or
+ * box[1] holds fewer than 3 cells. */
+lc_status lc_create_2d(const double box[2], double rc, int64_t n, lc_precision prec, lc_ctx **out);
+
 /* Counting-sort binning (link-cell construction, Sec. IV): wrap the
  * positions, compute each particle's cell, count, scan and scatter so that
  * every cell's particles are contiguous, ascending by ID inside a cell.  The
@@ -182,12 +193,25 @@ typedef enum {
 lc_status lc_dag_build(lc_ctx *ctx, lc_order order, int64_t *ntasks, int64_t *nedges,
                        int64_t *critical_path);
 
-/* The same DAG for a grid of nc[0] x nc[1] x nc[2] cells (each >= 3), built
- * on the host only (no context, no GPU): tasks, edges and critical path.
+/* The same DAG for a grid of nc[0] x nc[1] x nc[2] cells, built on the host
+ * only (no context, no GPU): tasks, edges and critical path.  nc[2] == 1
+ * means the 2D grid (stencil of 5: the cell and its 4 forward neighbours in
+ * the x-y plane, Fig. 3a); otherwise 3D (14).  perm: NULL, or the order of
+ * the stencil entries inside a cell for LC_ORDER_CELL, a permutation of
+ * 0 .. nperm-1 where entry 0 is the intra-cell task and entry k >= 1 the
+ * k-th forward offset in (z, y, x) table order (nperm = 14 in 3D, 5 in 2D).
  * Eq. 1 with equal task times gives the speedup bound tasks / critical_path.
- * LC_ERR_BOX_TOO_SMALL if some nc < 3, LC_ERR_TOO_LARGE beyond 2^29 tasks. */
-lc_status lc_dag_plan(const int32_t nc[3], lc_order order, int64_t *ntasks, int64_t *nedges,
-                      int64_t *critical_path);
+ * LC_ERR_BOX_TOO_SMALL if nc[0] or nc[1] (or, in 3D, nc[2]) < 3,
+ * LC_ERR_INVALID_ARG for a bad permutation, LC_ERR_TOO_LARGE beyond 2^29
+ * tasks. */
+lc_status lc_dag_plan(const int32_t nc[3], lc_order order, const int32_t *perm, int32_t nperm,
+                      int64_t *ntasks, int64_t *nedges, int64_t *critical_path);
+
+/* Sets the stencil order inside a cell used by LC_ORDER_CELL on this
+ * context (perm as in lc_dag_plan; NULL restores table order); the DAG of
+ * that order is rebuilt on its next use.  This is how the orderings of
+ * Fig. 5 are run on the device. */
+lc_status lc_dag_stencil_order(lc_ctx *ctx, const int32_t *perm, int32_t nperm);
 
 /* One force evaluation by executing the DAG of `order` on the device: a
  * persistent kernel (cooperative launch, every warp resident) whose warps

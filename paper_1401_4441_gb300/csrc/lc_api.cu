@@ -10,9 +10,11 @@
 
 namespace lc {
 
-void make_stencil(Stencil *s) {
+void make_stencil(Stencil *s, int dims) {
+    memset(s, 0, sizeof(*s));
+    const int zlo = dims == 2 ? 0 : -1, zhi = dims == 2 ? 0 : 1;
     int k = 0;
-    for (int oz = -1; oz <= 1; ++oz)
+    for (int oz = zlo; oz <= zhi; ++oz)
         for (int oy = -1; oy <= 1; ++oy)
             for (int ox = -1; ox <= 1; ++ox) {
                 bool fwd = oz > 0 || (oz == 0 && oy > 0) || (oz == 0 && oy == 0 && ox > 0);
@@ -20,6 +22,7 @@ void make_stencil(Stencil *s) {
                 s->hs[k][0] = ox; s->hs[k][1] = oy; s->hs[k][2] = oz;
                 ++k;
             }
+    s->nh = k;
     // Offsets with pairwise different parity patterns (|ox|,|oy|,|oz|) may
     // share a colour phase: two same-colour cells differ by an even number of
     // cells per dimension, so A + o == A' + o' forces o == o' (mod 2).
@@ -27,7 +30,7 @@ void make_stencil(Stencil *s) {
     bool used[4][8] = {};
     int cnt[4] = {0, 0, 0, 0};
     int members[4][13];
-    for (int i = 0; i < 13; ++i) {
+    for (int i = 0; i < s->nh; ++i) {
         int pat = (s->hs[i][0] != 0) + 2 * (s->hs[i][1] != 0) + 4 * (s->hs[i][2] != 0);
         int g = 0;
         while (used[g][pat]) ++g;
@@ -41,26 +44,28 @@ void make_stencil(Stencil *s) {
         for (int i = 0; i < cnt[g]; ++i) s->group_list[pos++] = members[g][i];
     }
     s->group_first[4] = pos;
-    // full shell: centre first, then the other 26 in (z, y, x) order
+    // full shell: centre first, then the others in (z, y, x) order
     s->full[0][0] = s->full[0][1] = s->full[0][2] = 0;
     int f = 1;
-    for (int oz = -1; oz <= 1; ++oz)
+    for (int oz = zlo; oz <= zhi; ++oz)
         for (int oy = -1; oy <= 1; ++oy)
             for (int ox = -1; ox <= 1; ++ox) {
                 if (!ox && !oy && !oz) continue;
                 s->full[f][0] = ox; s->full[f][1] = oy; s->full[f][2] = oz;
                 ++f;
             }
+    s->nf = f;
 }
 
-void make_grid(Grid *g, const double box[3], double rc) {
+void make_grid(Grid *g, const double box[3], double rc, int dims) {
     memset(g, 0, sizeof(*g));
+    g->dims = dims;
     g->rc = rc;
     g->rc2 = rc * rc;
     g->ncell = 1;
     for (int d = 0; d < 3; ++d) {
         g->L[d] = box[d];
-        g->nc[d] = (int)floor(box[d] / rc);
+        g->nc[d] = (dims == 2 && d == 2) ? 1 : (int)floor(box[d] / rc);   // 2D: one layer of side L_z
         g->h[d] = box[d] / (double)g->nc[d];
         g->inv[d] = (double)g->nc[d] / box[d];
         g->hf[d] = (float)g->h[d];
@@ -176,13 +181,14 @@ static cudaError_t alloc_state(State *st, int64_t n) {
 // c->g.ncell cells in total).
 static cudaError_t alloc_common(Ctx *c) {
     cudaError_t e;
-    Stencil st;
-    make_stencil(&st);
+    Stencil st, st2;
+    make_stencil(&st, 3);
+    make_stencil(&st2, 2);
     const int64_t n = c->n;
     const size_t N = (size_t)n, NC = (size_t)c->g.ncell;
     const int ntiles = (c->g.ncell + 4095) / 4096;
     c->nwarp_max = c->num_sms * 64;
-    if ((e = upload_stencil(st)) || (e = alloc_state(&c->cur, n)) || (e = alloc_state(&c->nxt, n)) ||
+    if ((e = upload_stencil(st, st2)) || (e = alloc_state(&c->cur, n)) || (e = alloc_state(&c->nxt, n)) ||
         (e = dalloc(&c->d_cell, N)) || (e = dalloc(&c->d_rank, N)) || (e = dalloc(&c->d_count, NC)) ||
         (e = dalloc(&c->d_start, NC + 1)) || (e = dalloc(&c->d_src, N)) || (e = dalloc(&c->d_key, N)) ||
         (e = dalloc(&c->d_blocksums, (size_t)ntiles + 1)) || (e = dalloc(&c->d_colour, NC)) ||
@@ -230,20 +236,22 @@ const char *lc_status_str(lc_status s) {
     return "unknown status";
 }
 
-lc_status lc_create(const double box[3], double rc, int64_t n, lc_precision prec, lc_ctx **out) {
+static lc_status create_single(const double box[3], double rc, int64_t n, lc_precision prec, int dims, lc_ctx **out) {
     if (!out) return LC_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!box || !(rc > 0.0) || n < 0 || (prec != LC_PREC_FP64 && prec != LC_PREC_MIXED)) return LC_ERR_INVALID_ARG;
+    if (!box || !(rc > 0.0) || !isfinite(rc) || n < 0 || (prec != LC_PREC_FP64 && prec != LC_PREC_MIXED))
+        return LC_ERR_INVALID_ARG;
     for (int d = 0; d < 3; ++d)
         if (!(box[d] > 0.0) || !isfinite(box[d])) return LC_ERR_INVALID_ARG;
     if (n >= kMaxParticles) return LC_ERR_TOO_LARGE;
-    for (int d = 0; d < 3; ++d)
+    for (int d = 0; d < dims; ++d)
         if (floor(box[d] / rc) < 3.0) return LC_ERR_BOX_TOO_SMALL;
-    if (floor(box[0] / rc) * floor(box[1] / rc) * floor(box[2] / rc) > 1.0e9) return LC_ERR_TOO_LARGE;
+    const double nz = dims == 2 ? 1.0 : floor(box[2] / rc);
+    if (floor(box[0] / rc) * floor(box[1] / rc) * nz > 1.0e9) return LC_ERR_TOO_LARGE;
 
     lc_ctx *c = new lc_ctx();
     memset(static_cast<Ctx *>(c), 0, sizeof(Ctx));
-    make_grid(&c->g, box, rc);
+    make_grid(&c->g, box, rc, dims);
     c->n = n;
     c->prec = prec;
     c->ni = 16;
@@ -261,6 +269,19 @@ lc_status lc_create(const double box[3], double rc, int64_t n, lc_precision prec
     }
     *out = c;
     return LC_OK;
+}
+
+lc_status lc_create(const double box[3], double rc, int64_t n, lc_precision prec, lc_ctx **out) {
+    return create_single(box, rc, n, prec, 3, out);
+}
+
+lc_status lc_create_2d(const double box[2], double rc, int64_t n, lc_precision prec, lc_ctx **out) {
+    if (!box) {
+        if (out) *out = nullptr;
+        return LC_ERR_INVALID_ARG;
+    }
+    const double b3[3] = {box[0], box[1], rc};   // one cell layer of side rc in z
+    return create_single(b3, rc, n, prec, 2, out);
 }
 
 lc_status lc_batch_create(int32_t nbox, const double *box, const double *rc, const int64_t *n, lc_precision prec,
@@ -572,7 +593,13 @@ lc_status lc_grid(const lc_ctx *c, int32_t nc[3], int32_t *ncolours, int32_t *np
     if (!c) return LC_ERR_INVALID_ARG;
     if (nc) for (int d = 0; d < 3; ++d) nc[d] = c->g.nc[d];
     if (ncolours) *ncolours = c->g.ncolours;
-    if (nphases) *nphases = 4 * c->g.ncolours;
+    if (nphases) {
+        Stencil st;
+        make_stencil(&st, c->g.dims);
+        int groups = 0;
+        for (int g = 0; g < 4; ++g) groups += (g == 0 || st.group_first[g + 1] > st.group_first[g]) ? 1 : 0;
+        *nphases = groups * c->g.ncolours;
+    }
     return LC_OK;
 }
 
@@ -592,8 +619,7 @@ static lc_status ensure_dag(lc_ctx *c, lc_order order) {
     if (c->dag[order]) return LC_OK;
     if (14 * (int64_t)c->g.ncell > (int64_t(1) << 29)) return LC_ERR_TOO_LARGE;
     Stencil st;
-    memset(&st, 0, sizeof(st));
-    make_stencil(&st);
+    make_stencil(&st, c->g.dims);
     DagDev *d = nullptr;
     LC_TRY(build_dag(c, st, (int)order, &d));
     c->dag[order] = d;
@@ -610,14 +636,40 @@ lc_status lc_dag_build(lc_ctx *c, lc_order order, int64_t *ntasks, int64_t *nedg
     return LC_OK;
 }
 
-lc_status lc_dag_plan(const int32_t nc[3], lc_order order, int64_t *ntasks, int64_t *nedges, int64_t *critical_path) {
+// perm: a permutation of 0 .. nh (nh = 13 in 3D, 4 in 2D)?
+static bool valid_stencil_perm(const int32_t *perm, int32_t nperm, int dims) {
+    Stencil st;
+    make_stencil(&st, dims);
+    if (nperm != st.nh + 1) return false;
+    bool seen[14] = {};
+    for (int q = 0; q < nperm; ++q) {
+        if (perm[q] < 0 || perm[q] > st.nh || seen[perm[q]]) return false;
+        seen[perm[q]] = true;
+    }
+    return true;
+}
+
+lc_status lc_dag_plan(const int32_t nc[3], lc_order order, const int32_t *perm, int32_t nperm, int64_t *ntasks,
+                      int64_t *nedges, int64_t *critical_path) {
     if (!nc || (order != LC_ORDER_CELL && order != LC_ORDER_LOOPEX)) return LC_ERR_INVALID_ARG;
-    for (int d = 0; d < 3; ++d)
+    const int dims = nc[2] == 1 ? 2 : 3;
+    for (int d = 0; d < dims; ++d)
         if (nc[d] < 3) return LC_ERR_BOX_TOO_SMALL;
+    if (perm && !valid_stencil_perm(perm, nperm, dims)) return LC_ERR_INVALID_ARG;
     if (14 * (int64_t)nc[0] * nc[1] * nc[2] > (int64_t(1) << 29)) return LC_ERR_TOO_LARGE;
     const int n3[3] = {nc[0], nc[1], nc[2]};
-    const int64_t cp = dag_plan_host(n3, (int)order, ntasks, nedges);
+    const int64_t cp = dag_plan_host(n3, (int)order, perm, perm ? nperm : 0, ntasks, nedges);
     if (critical_path) *critical_path = cp;
+    return LC_OK;
+}
+
+lc_status lc_dag_stencil_order(lc_ctx *c, const int32_t *perm, int32_t nperm) {
+    if (!c || c->nbox > 0) return LC_ERR_INVALID_ARG;
+    if (perm && !valid_stencil_perm(perm, nperm, c->g.dims)) return LC_ERR_INVALID_ARG;
+    c->dag_perm_n = perm ? nperm : 0;
+    for (int q = 0; q < c->dag_perm_n; ++q) c->dag_perm[q] = perm[q];
+    free_dag(c->dag[LC_ORDER_CELL]);     // rebuilt with the new order on its next use
+    c->dag[LC_ORDER_CELL] = nullptr;
     return LC_OK;
 }
 

@@ -309,7 +309,18 @@ __global__ void k_iota(int n, int *id) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) id[s] = s;
 }
 
-// dst[id[s]] = (a[s], b[s], c[s]); wrap != 0 wraps positions into [0, L).
+// 2D contexts: the particles sit at z = zval inside the single cell layer
+// (a value away from the layer's faces) with vz = 0; the z the caller gave
+// is ignored.
+__global__ void k_plane(int n, double zval, double *__restrict__ z, double *__restrict__ vz) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        z[s] = zval;
+        vz[s] = 0.0;
+    }
+}
+
+// dst[id[s]] = (a[s], b[s], c[s]); wrap != 0 wraps positions into [0, L);
+// 2D contexts report z components as 0.
 __global__ void k_unsort_vec(int n, Grid g1, const BoxDev *__restrict__ boxes, const unsigned short *__restrict__ slot_box,
                              int wrap, const int *__restrict__ id, const double *__restrict__ a,
                              const double *__restrict__ b, const double *__restrict__ cc, double *__restrict__ dst) {
@@ -319,6 +330,7 @@ __global__ void k_unsort_vec(int n, Grid g1, const BoxDev *__restrict__ boxes, c
         if (wrap) {
             va = wrap_coord(va, g.L[0]); vb = wrap_coord(vb, g.L[1]); vc = wrap_coord(vc, g.L[2]);
         }
+        if (g.dims == 2) vc = 0.0;
         int i = id[s];
         dst[3 * i + 0] = va; dst[3 * i + 1] = vb; dst[3 * i + 2] = vc;
     }
@@ -336,6 +348,7 @@ cudaError_t launch_set_state(Ctx *c, const double *pos, const double *vel, cudaS
         cudaMemsetAsync(c->cur.vy, 0, sizeof(double) * (size_t)n, s);
         cudaMemsetAsync(c->cur.vz, 0, sizeof(double) * (size_t)n, s);
     }
+    if (c->g.dims == 2) k_plane<<<grid_n, 256, 0, s>>>(n, 0.25 * c->g.L[2], c->cur.z, c->cur.vz);
     k_iota<<<grid_n, 256, 0, s>>>(n, c->cur.id);
     return cudaGetLastError();
 }

@@ -30,14 +30,17 @@ namespace {
 
 int wrap_cell(int c, int n) { return c >= n ? c - n : (c < 0 ? c + n : c); }
 
-// Creation order of the 14 * ncell tasks, each coded A << 4 | k.
-std::vector<int> creation_order(const Grid &g, const Stencil &st, int order) {
+// Creation order of the (nh + 1) * ncell tasks, each coded A << 4 | k.
+// perm: the order of the stencil entries inside a cell for LC_ORDER_CELL
+// (k values, a permutation of 0 .. nh), or empty for table order.
+std::vector<int> creation_order(const Grid &g, const Stencil &st, int order, const std::vector<int> &perm) {
     const int ncell = g.ncell;
+    const int per = st.nh + 1;
     std::vector<int> task;
-    task.reserve((size_t)ncell * 14);
+    task.reserve((size_t)ncell * per);
     if (order == LC_ORDER_CELL) {
         for (int A = 0; A < ncell; ++A)
-            for (int k = 0; k < 14; ++k) task.push_back(A << 4 | k);
+            for (int q = 0; q < per; ++q) task.push_back(A << 4 | (perm.empty() ? q : perm[q]));
     } else {
         std::vector<int> colour(ncell);
         for (int A = 0; A < ncell; ++A) {
@@ -49,12 +52,11 @@ std::vector<int> creation_order(const Grid &g, const Stencil &st, int order) {
             }
             colour[A] = g.colour_of_raw[raw];
         }
-        for (int k = 0; k < 14; ++k)
+        for (int k = 0; k < per; ++k)
             for (int col = 0; col < g.ncolours; ++col)
                 for (int A = 0; A < ncell; ++A)
                     if (colour[A] == col) task.push_back(A << 4 | k);
     }
-    (void)st;
     return task;
 }
 
@@ -67,8 +69,8 @@ struct DagHost {
     int64_t nedges = 0, critical_path = 0;
 };
 
-void plan_dag(const Grid &g, const Stencil &st, int order, DagHost &h) {
-    h.task = creation_order(g, st, order);
+void plan_dag(const Grid &g, const Stencil &st, int order, const std::vector<int> &perm, DagHost &h) {
+    h.task = creation_order(g, st, order, perm);
     const std::vector<int> &task = h.task;
     const int T = (int)task.size();
     std::vector<int> last(g.ncell, -1);
@@ -121,7 +123,9 @@ void plan_dag(const Grid &g, const Stencil &st, int order, DagHost &h) {
 cudaError_t build_dag(const Ctx *c, const Stencil &st, int order, DagDev **out) {
     *out = nullptr;
     DagHost h;
-    plan_dag(c->g, st, order, h);
+    std::vector<int> perm;
+    if (order == LC_ORDER_CELL && c->dag_perm_n > 0) perm.assign(c->dag_perm, c->dag_perm + c->dag_perm_n);
+    plan_dag(c->g, st, order, perm, h);
     const int T = (int)h.task.size();
     const int64_t E = h.nedges;
     const int nroots = h.nroots;
@@ -160,15 +164,17 @@ cudaError_t build_dag(const Ctx *c, const Stencil &st, int order, DagDev **out) 
     return cudaSuccess;
 }
 
-int64_t dag_plan_host(const int nc[3], int order, int64_t *ntasks, int64_t *nedges) {
+int64_t dag_plan_host(const int nc[3], int order, const int *perm, int nperm, int64_t *ntasks, int64_t *nedges) {
     Grid g;
+    const int dims = nc[2] == 1 ? 2 : 3;
     const double box[3] = {(double)nc[0], (double)nc[1], (double)nc[2]};
-    make_grid(&g, box, 1.0);
+    make_grid(&g, box, 1.0, dims);
     Stencil st;
-    memset(&st, 0, sizeof(st));
-    make_stencil(&st);
+    make_stencil(&st, dims);
     DagHost h;
-    plan_dag(g, st, order, h);
+    std::vector<int> p;
+    if (order == LC_ORDER_CELL && perm && nperm > 0) p.assign(perm, perm + nperm);
+    plan_dag(g, st, order, p, h);
     if (ntasks) *ntasks = (int64_t)h.task.size();
     if (nedges) *nedges = h.nedges;
     return h.critical_path;

@@ -39,7 +39,10 @@
 
 namespace lc {
 
-__constant__ Stencil c_st;
+__constant__ Stencil c_st;    // 3D stencil tables
+__constant__ Stencil c_st2;   // 2D (x-y plane) stencil tables
+
+__device__ __forceinline__ const Stencil &stencil(int dims) { return dims == 2 ? c_st2 : c_st; }
 
 enum Mode : int { kColour = 0, kAtomic = 1, kFullShell = 2, kBuffer = 3, kDag = 4 };
 
@@ -79,6 +82,7 @@ struct TaskCells {
     int nnb;          // neighbour cells listed (self first when present)
     bool self;        // intra-cell interaction included
     int group;        // colour: the phase's offset group; DAG: the offset index
+    int dims;         // 3, or 2 (stencil in the x-y plane)
     const Grid *g;    // the box's grid
     const float (*sh)[3], (*sl)[3];   // the box's shift tables
     int cell_off;     // first global cell of the box
@@ -105,20 +109,21 @@ __device__ __forceinline__ int colour_ntasks(const Grid &g, int colour) {
 
 // Neighbour k of the task (k < nnb): offset and periodic image.
 template <int MODE>
-__device__ __forceinline__ void task_offset(int group, int k, bool self, int o[3]) {
+__device__ __forceinline__ void task_offset(int group, int k, bool self, int dims, int o[3]) {
     if (self) {
         if (k == 0) { o[0] = o[1] = o[2] = 0; return; }
         --k;
     }
-    if (MODE == kFullShell) {            // all 27 offsets, centre first
-        o[0] = c_st.full[k + 1][0]; o[1] = c_st.full[k + 1][1]; o[2] = c_st.full[k + 1][2];
+    const Stencil &S = stencil(dims);
+    if (MODE == kFullShell) {            // all offsets, centre first
+        o[0] = S.full[k + 1][0]; o[1] = S.full[k + 1][1]; o[2] = S.full[k + 1][2];
     } else if (MODE == kAtomic || MODE == kBuffer) {
-        o[0] = c_st.hs[k][0]; o[1] = c_st.hs[k][1]; o[2] = c_st.hs[k][2];
+        o[0] = S.hs[k][0]; o[1] = S.hs[k][1]; o[2] = S.hs[k][2];
     } else if (MODE == kDag) {           // one neighbour: half-shell offset `group`
-        o[0] = c_st.hs[group][0]; o[1] = c_st.hs[group][1]; o[2] = c_st.hs[group][2];
+        o[0] = S.hs[group][0]; o[1] = S.hs[group][1]; o[2] = S.hs[group][2];
     } else {
-        int kk = c_st.group_list[c_st.group_first[group] + k];
-        o[0] = c_st.hs[kk][0]; o[1] = c_st.hs[kk][1]; o[2] = c_st.hs[kk][2];
+        int kk = S.group_list[S.group_first[group] + k];
+        o[0] = S.hs[kk][0]; o[1] = S.hs[kk][1]; o[2] = S.hs[kk][2];
     }
 }
 
@@ -127,15 +132,17 @@ __device__ __forceinline__ void task_offset(int group, int k, bool self, int o[3
 template <int MODE>
 __device__ __forceinline__ void single_task(const Grid &g, int group, int colour, int t, TaskCells &tc) {
     tc.group = group;
+    tc.dims = g.dims;
+    const Stencil &S = stencil(g.dims);
     if (MODE == kColour) {
         tc.A = colour_task_cell(g, colour, t, tc.cA);
         tc.self = (group == 0);
-        tc.nnb = (c_st.group_first[group + 1] - c_st.group_first[group]) + (tc.self ? 1 : 0);
+        tc.nnb = (S.group_first[group + 1] - S.group_first[group]) + (tc.self ? 1 : 0);
     } else {
         tc.A = t;
         cell_xyz(g, t, tc.cA);
         tc.self = true;
-        tc.nnb = (MODE == kFullShell) ? 27 : 14;
+        tc.nnb = (MODE == kFullShell) ? S.nf : S.nh + 1;
     }
 }
 
@@ -150,6 +157,7 @@ __device__ __forceinline__ TaskCells make_task(const ForceArgs &a, int t) {
         tc.A = t;
         cell_xyz(bd.g, t - bd.cell_off, tc.cA);
         tc.group = 0;
+        tc.dims = 3;
         tc.self = true;
         tc.nnb = (MODE == kFullShell) ? 27 : 14;
     } else {
@@ -383,7 +391,7 @@ __device__ __forceinline__ void setup_neighbours(const ForceArgs &a, WarpSmem<ty
     // per-offset tables, the periodic image is kept as a code)
     if (lane < tc.nnb) {
         int o[3];
-        task_offset<MODE>(tc.group, lane, tc.self, o);
+        task_offset<MODE>(tc.group, lane, tc.self, tc.dims, o);
         int c[3];
         int img = 0;
         for (int d = 0; d < 3; ++d) {
@@ -419,7 +427,7 @@ __device__ __forceinline__ NbPre load_neighbours(const ForceArgs &a, const TaskC
     if (lane < tc.nnb) {
         const Grid &g = *tc.g;
         int o[3];
-        task_offset<MODE>(tc.group, lane, tc.self, o);
+        task_offset<MODE>(tc.group, lane, tc.self, tc.dims, o);
         int c[3];
         int img = 0;
         for (int d = 0; d < 3; ++d) {
@@ -983,6 +991,7 @@ __device__ __forceinline__ TaskCells dag_task(const ForceArgs &a, int A, int k) 
     cell_xyz(a.g, A, tc.cA);
     tc.self = (k == 0);
     tc.group = k > 0 ? k - 1 : 0;
+    tc.dims = a.g.dims;
     tc.nnb = 1;
     return tc;
 }
@@ -1084,7 +1093,7 @@ __global__ void k_check(Grid g, int group, int colour, int ntasks, int phase, in
         single_task<MODE>(g, group, colour, t, tc);
         for (int k = 0; k < tc.nnb; ++k) {
             int o[3];
-            task_offset<MODE>(group, k, tc.self, o);
+            task_offset<MODE>(group, k, tc.self, tc.dims, o);
             int c[3];
             for (int d = 0; d < 3; ++d) {
                 c[d] = tc.cA[d] + o[d];
@@ -1114,7 +1123,8 @@ __global__ void k_check_cover(Grid g, int full, const unsigned long long *visit,
         int o[3] = {oi % 3 - 1, (oi / 3) % 3 - 1, oi / 9 - 1};
         bool fwd = (o[2] > 0) || (o[2] == 0 && o[1] > 0) || (o[2] == 0 && o[1] == 0 && o[0] > 0);
         bool centre = (o[0] == 0 && o[1] == 0 && o[2] == 0);
-        unsigned long long want = (full || fwd || centre) ? 1ull : 0ull;
+        const bool in_plane = g.dims != 2 || o[2] == 0;     // 2D: offsets in the x-y plane only
+        unsigned long long want = (in_plane && (full || fwd || centre)) ? 1ull : 0ull;
         if (visit[t] != want) atomicAdd(counters + 1, 1ull);
     }
 }
@@ -1209,7 +1219,10 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
             e = cudaMemsetAsync(c->fx, 0, 3 * nbytes, s);
         }
         if (e) return e;
-        for (int g = 0; g < 4; ++g)
+        Stencil st;
+        make_stencil(&st, c->g.dims);
+        for (int g = 0; g < 4; ++g) {
+            if (g > 0 && st.group_first[g + 1] == st.group_first[g]) continue;   // no offsets (2D)
             for (int k = 0; k < c->g.ncolours; ++k) {
                 a.group = g; a.colour = k;
                 int raw = c->g.raw_of_colour[k];
@@ -1219,6 +1232,7 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
                 if (e) return e;
                 ++*launches;
             }
+        }
         if (MIXED) {
             k_kahan_finalize<<<c->num_sms * 8, 256, 0, s>>>((int)c->n, c->kx, c->ky, c->kz, c->fx, c->fy, c->fz);
             ++*launches;
@@ -1354,13 +1368,17 @@ cudaError_t launch_schedule_check(Ctx *c, lc_schedule sched, cudaStream_t s) {
     const int blocks = c->num_sms * 4;
     if (sched == LC_SCHED_COLOUR) {
         int phase = 0;
-        for (int g = 0; g < 4; ++g)
+        Stencil st;
+        make_stencil(&st, c->g.dims);
+        for (int g = 0; g < 4; ++g) {
+            if (g > 0 && st.group_first[g + 1] == st.group_first[g]) continue;
             for (int k = 0; k < c->g.ncolours; ++k, ++phase) {
                 int raw = c->g.raw_of_colour[k];
                 int nt = c->g.class_count[0][raw % 3] * c->g.class_count[1][(raw / 3) % 3] *
                          c->g.class_count[2][raw / 9];
                 k_check<kColour><<<blocks, 256, 0, s>>>(c->g, g, k, nt, phase, c->d_stamp, c->d_visit, c->d_counters);
             }
+        }
     } else if (sched == LC_SCHED_ATOMIC || sched == LC_SCHED_BUFFER) {
         k_check<kAtomic><<<blocks, 256, 0, s>>>(c->g, 0, 0, c->g.ncell, 0, c->d_stamp, c->d_visit, c->d_counters);
     } else {
@@ -1401,8 +1419,10 @@ cudaError_t init_force_kernels() {
     return cudaSuccess;
 }
 
-cudaError_t upload_stencil(const Stencil &st) {
-    return cudaMemcpyToSymbol(c_st, &st, sizeof(Stencil));
+cudaError_t upload_stencil(const Stencil &st3, const Stencil &st2) {
+    cudaError_t e = cudaMemcpyToSymbol(c_st, &st3, sizeof(Stencil));
+    if (!e) e = cudaMemcpyToSymbol(c_st2, &st2, sizeof(Stencil));
+    return e;
 }
 
 }  // namespace lc

@@ -46,6 +46,7 @@ struct Grid {
     float Lf_lo[3];   // FP32 value below L: hi < Lf_lo implies x < L
     float cmargin[3]; // distance from a cell face below which binning is exact FP64
     float rc2f_lo, rc2f_hi;  // FP32 band around rc^2 for the mixed path
+    int dims;         // 3, or 2: one cell layer in z, positions in the x-y plane
     int ncolours;
     int class_count[3][3];   // cells of colour class a along dimension d
     int colour_of_raw[27];   // raw colour cx + 3 cy + 9 cz -> colour rank (-1 absent)
@@ -66,16 +67,18 @@ __device__ __forceinline__ void cell_coords(const Grid &g, int c, int out[3]) {
 }
 
 // Offsets of the 27-cell stencil and the phase groups, in constant memory.
+// 3D: 13 forward offsets of 26; 2D (offsets in the x-y plane): 4 of 8.
 struct Stencil {
+    int nh, nf;         // half-shell offsets (13 / 4), full-shell cells (27 / 9)
     int hs[13][3];      // forward half-shell, (z, y, x) lexicographic
     int group_of[13];   // phase group (0..3) of each half-shell offset
     int group_first[5]; // offsets of group g are group_list[group_first[g] .. group_first[g+1])
     int group_list[13];
-    int full[27][3];    // all 27 offsets, centre first
+    int full[27][3];    // all offsets, centre first
 };
 
-void make_stencil(Stencil *s);
-void make_grid(Grid *g, const double box[3], double rc);
+void make_stencil(Stencil *s, int dims = 3);
+void make_grid(Grid *g, const double box[3], double rc, int dims = 3);
 
 // One box of a batch: its grid, the FP32 shift tables of its 27 offsets,
 // and where its cells and particles sit in the batch's global numbering
@@ -160,6 +163,8 @@ struct Ctx {
     double *d_box_out;        // [nbox][4] U, W, pairs, K
     int stats_full;           // last statistics came from the full shell
     DagDev *dag[2];        // per task-creation order, built on first use
+    int dag_perm[14];      // stencil order inside a cell for the cell order
+    int dag_perm_n;        // 0: table order
     // buffer schedule: per-(cell, offset) private force buffers [15][3][n]
     // (float for the mixed path, double for FP64), allocated on first use
     void *d_fbuf;
@@ -182,14 +187,13 @@ cudaError_t launch_box_energy(Ctx *c, cudaStream_t s, int full);
 // withhold != 0 publishes no ready task (a test of the bounded waits).
 cudaError_t launch_forces_dag(Ctx *c, const DagDev *d, long long wait_ns, int withhold, int32_t *trace,
                               cudaStream_t s, int *launches);
-void make_stencil(Stencil *s);
 cudaError_t build_dag(const Ctx *c, const Stencil &st, int order, DagDev **out);
 void free_dag(DagDev *d);
 // Host-only DAG of a grid of nc cells (no device work): returns the critical path.
-int64_t dag_plan_host(const int nc[3], int order, int64_t *ntasks, int64_t *nedges);
+int64_t dag_plan_host(const int nc[3], int order, const int *perm, int nperm, int64_t *ntasks, int64_t *nedges);
 cudaError_t launch_box_kinetic(Ctx *c, cudaStream_t s);
 cudaError_t launch_colour(Ctx *c, cudaStream_t s);
-cudaError_t upload_stencil(const Stencil &st);
+cudaError_t upload_stencil(const Stencil &st3, const Stencil &st2);
 int kinetic_blocks(const Ctx *c);
 cudaError_t launch_schedule_check(Ctx *c, lc_schedule sched, cudaStream_t s);
 cudaError_t launch_unsort_vec(Ctx *c, const double *a, const double *b, const double *cc,

@@ -17,6 +17,10 @@ Workloads (reduced LJ units, sigma = epsilon = m = 1):
                 redrawn until no pair is closer than r_min.
   batch_boxes   independent cubic boxes with log-uniform N, uniform density
                 and temperature, FCC plus jitter starts.
+  tri_box       2D: triangular lattice (rows of spacing a, alternate rows
+                shifted by a/2, row pitch a sqrt(3)/2) filling a periodic
+                rectangle commensurate with it, optional jitter, 2D Maxwell
+                velocities; positions keep three components with z = 0.
 """
 import math
 
@@ -179,17 +183,62 @@ def batch_boxes(nbox=512, n_min=500, n_max=50_000, rho=(0.5, 0.9), T=(0.7, 1.2),
     return boxes
 
 
+def maxwell2d(n, T, seed, stream=120):
+    """In-plane velocities (n, 3) with vz = 0: normal with variance T per
+    component, zero total momentum, rescaled so that sum v^2 = 2 (n - 1) T."""
+    v = np.zeros((n, 3))
+    v[:, :2] = np.stack([gaussian(seed, stream + 2 * d, n) for d in range(2)], axis=1) * math.sqrt(T)
+    if n > 1:
+        v[:, :2] -= v[:, :2].mean(axis=0, keepdims=True)
+        s2 = float((v * v).sum())
+        if s2 > 0:
+            v *= math.sqrt(2.0 * (n - 1) * T / s2)
+    return v
+
+
+def tri_box(nx, ny, rho, T, seed=DEFAULT_SEED, jitter=0.0, stream=30):
+    """2D triangular lattice of nx particles per row and ny rows (ny even, so
+    the periodic box is commensurate): spacing a from the number density rho
+    (area per particle a^2 sqrt(3)/2), box (nx a, ny a sqrt(3)/2).  Jitter
+    adds U[-jitter, +jitter) to x and y.  Returns dict(pos (n, 3) with z = 0,
+    vel (n, 3) with vz = 0, box (2,))."""
+    if ny % 2:
+        raise ValueError("ny must be even for a periodic triangular lattice")
+    a = math.sqrt(2.0 / (math.sqrt(3.0) * rho))
+    h = a * math.sqrt(3.0) / 2.0
+    iy, ix = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    x = (ix + 0.5 * (iy % 2) + 0.25) * a
+    y = (iy + 0.25) * h
+    n = nx * ny
+    pos = np.zeros((n, 3))
+    pos[:, 0] = x.ravel()
+    pos[:, 1] = y.ravel()
+    if jitter > 0.0:
+        for d in range(2):
+            pos[:, d] += (2.0 * uniform(seed, stream + 1 + d, n) - 1.0) * jitter
+    return dict(pos=np.ascontiguousarray(pos), vel=maxwell2d(n, T, seed), box=np.array([nx * a, ny * h]),
+                rho=rho, T=T, seed=seed, a=a)
+
+
 # Named workloads (sizes of the single-box configurations).
 WORKLOADS = {
     "fcc4k": dict(n=4000, rho=0.8442, T=0.72, rc=2.5, jitter=0.0),
     "liquid1m": dict(n=1_048_576, rho=0.8442, T=0.72, rc=2.5, jitter=0.05),
     "fcc16m": dict(n=16_777_216, rho=0.8442, T=0.72, rc=2.5, jitter=0.0),
     "slab2m": dict(n=2_000_000, rho=None, T=0.85, rc=3.0, jitter=0.0, kind="slab"),
+    # 2D liquid: 1024 x 1024 triangular lattice at area density 0.7, jittered
+    "liquid2d": dict(n=1024 * 1024, nx=1024, ny=1024, rho=0.7, T=0.5, rc=2.5, jitter=0.05, kind="2d"),
 }
 
 
 def workload(name, seed=DEFAULT_SEED):
     w = WORKLOADS[name]
+    if w.get("kind") == "2d":
+        b = tri_box(w["nx"], w["ny"], w["rho"], w["T"], seed=seed, jitter=w["jitter"])
+        b["rc"] = w["rc"]
+        b["name"] = name
+        b["dims"] = 2
+        return b
     if w.get("kind") == "slab":
         b = slab_box(n=w["n"], T=w["T"], seed=seed)
         b["rc"] = w["rc"]

@@ -60,7 +60,9 @@ def _load():
         "lc_batch_info": ([vp, ip, lp, lp], ctypes.c_int),
         "lc_dag_build": ([vp, ctypes.c_int, lp, lp, lp], ctypes.c_int),
         "lc_dag_forces": ([vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, vp], ctypes.c_int),
-        "lc_dag_plan": ([ip, ctypes.c_int, lp, lp, lp], ctypes.c_int),
+        "lc_dag_plan": ([ip, ctypes.c_int, ip, ctypes.c_int32, lp, lp, lp], ctypes.c_int),
+        "lc_dag_stencil_order": ([vp, ip, ctypes.c_int32], ctypes.c_int),
+        "lc_create_2d": ([dp, ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctx_pp], ctypes.c_int),
         "lc_destroy": ([vp], None),
         "lc_status_str": ([ctypes.c_int], ctypes.c_char_p),
     }
@@ -104,28 +106,43 @@ def _ptr(a):
     raise TypeError(f"unsupported array type {type(a)}")
 
 
-def dag_plan(nc, order="loopex"):
-    """(tasks, edges, critical path) of the task DAG of a grid of nc cells,
-    built on the host by the library (no GPU needed)."""
+def _perm(perm):
+    if perm is None:
+        return None, 0
+    perm = [int(x) for x in perm]
+    return (ctypes.c_int32 * len(perm))(*perm), len(perm)
+
+
+def dag_plan(nc, order="loopex", perm=None):
+    """(tasks, edges, critical path) of the task DAG of a grid of nc cells
+    (nc[2] == 1 or a 2-tuple: the 2D grid), built on the host by the library
+    (no GPU needed).  perm: the stencil order inside a cell for the cell
+    order (entry 0 intra, k >= 1 the k-th forward offset)."""
     lib_ = _load()
+    nc = list(nc) + [1] * (3 - len(nc))
     arr = (ctypes.c_int32 * 3)(*[int(x) for x in nc])
+    p, np_ = _perm(perm)
     t, e, cp = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
-    _check(lib_.lc_dag_plan(arr, ORDER[order], ctypes.byref(t), ctypes.byref(e), ctypes.byref(cp)), "lc_dag_plan")
+    _check(lib_.lc_dag_plan(arr, ORDER[order], p, np_, ctypes.byref(t), ctypes.byref(e), ctypes.byref(cp)),
+           "lc_dag_plan")
     return t.value, e.value, cp.value
 
 
 class Box:
-    """One periodic box on the GPU (an lc_ctx)."""
+    """One periodic box on the GPU (an lc_ctx).  dims=2: a 2D box
+    (box = (Lx, Ly); positions keep three components, z ignored)."""
 
-    def __init__(self, box, rc, n, precision="mixed"):
+    def __init__(self, box, rc, n, precision="mixed", dims=3):
         self._lib = _load()
         self.n = int(n)
-        self.box = np.ascontiguousarray(np.broadcast_to(np.asarray(box, np.float64), (3,)))
+        self.dims = dims
+        self.box = np.ascontiguousarray(np.broadcast_to(np.asarray(box, np.float64), (dims,)))
         self.rc = float(rc)
         self.precision = precision
         h = ctypes.c_void_p()
-        _check(self._lib.lc_create(self.box.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.rc,
-                                   self.n, PREC[precision], ctypes.byref(h)), "lc_create")
+        create = self._lib.lc_create_2d if dims == 2 else self._lib.lc_create
+        _check(create(self.box.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.rc, self.n,
+                      PREC[precision], ctypes.byref(h)), "lc_create")
         self._h = h
 
     # -- lifecycle ---------------------------------------------------------
@@ -214,6 +231,12 @@ class Box:
         _check(self._lib.lc_dag_build(self._h, ORDER[order], ctypes.byref(t), ctypes.byref(e), ctypes.byref(cp)),
                "lc_dag_build")
         return t.value, e.value, cp.value
+
+    def dag_stencil_order(self, perm=None):
+        """Stencil order inside a cell for the cell creation order (None:
+        table order)."""
+        p, np_ = _perm(perm)
+        _check(self._lib.lc_dag_stencil_order(self._h, p, np_), "lc_dag_stencil_order")
 
     def dag_forces(self, order="loopex", trace=None, wait_seconds=0.0, withhold=False, stream=None):
         """Forces by running the task DAG on the device; trace: None or a CUDA

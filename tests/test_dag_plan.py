@@ -54,3 +54,36 @@ def test_plan_rejects(lcmod):
     with pytest.raises(lcmod.LCError) as e:
         lcmod.dag_plan((1000, 1000, 1000), "cell")
     assert e.value.code == 9
+
+
+# 2D: the library's stencil entries 0 intra, then (1,0), (-1,1), (0,1), (1,1)
+LIB_2D = [(0, 0), (1, 0), (-1, 1), (0, 1), (1, 1)]
+
+
+@pytest.mark.parametrize("perm", [(0, 1, 2, 3, 4), (0, 2, 3, 1, 4), (1, 0, 4, 3, 2), (4, 3, 2, 1, 0),
+                                  (2, 0, 4, 1, 3)])
+def test_plan_2d_matches_oracle(lcmod, perm):
+    dims = (20, 20)
+    t, e, cp = lcmod.dag_plan(dims, "cell", perm)
+    parents = odag.build_dag(odag.basic_order_tasks(dims, [LIB_2D[k] for k in perm]))
+    assert (t, e, cp) == (len(parents), sum(len(p) for p in parents), odag.critical_path(parents))
+
+
+def test_plan_2d_speedups_of_fig5(lcmod):
+    """Sec. V on 50 x 50 periodic cells: with the intra-cell task first the
+    speedup is n / Delta for a displacement Delta in [2, 5] (n = 5), and the
+    best order approaches Eq. 2's 4.99 without exceeding n; loop exchange with
+    colouring leaves a critical path of 9 tasks (Sec. VI)."""
+    import itertools
+    from paper_1401_4441_gb300 import lc
+    levels = [5.0 / d for d in (2, 3, 4, 5)]
+    best = 0.0
+    for perm in itertools.permutations(range(5)):
+        t, _, cp = lc.dag_plan((50, 50), "cell", perm)
+        s = t / cp
+        best = max(best, s)
+        assert s <= 5.0
+        if perm[0] == 0:
+            assert min(abs(s - l) / l for l in levels) < 0.03, (perm, s)
+    assert best == pytest.approx(odag.eq2(1, 2500, 5), rel=0.03)
+    assert lc.dag_plan((50, 50), "loopex")[2] == 9

@@ -319,3 +319,40 @@ def test_force_scale():
     f, _, _, _ = oracle.lc_forces(q[:, 0], q[:, 1], q[:, 2], Lq, RC)
     s = oracle.force_scale(q[:, 0], q[:, 1], q[:, 2], Lq, RC)
     assert np.all(np.sqrt((f ** 2).sum(1)) <= s * (1 + 1e-12))
+
+
+# ---- 2D (Sec. IV, Fig. 3a): the oracle's 3D routines on particles in the
+# z = 0 plane of a box whose z side is 3 r_c (every z image farther than
+# r_c) compute the 2D Lennard-Jones system; pinned here by 2D lattice sums.
+
+def embed_2d(pos, box2):
+    return pos, np.array([box2[0], box2[1], 3.0 * RC])
+
+
+def test_triangular_lattice_shell_sums_2d():
+    b = inputs.tri_box(16, 16, 0.7, 0.5)
+    p, L = embed_2d(b["pos"], b["box"])
+    a = b["a"]
+    # shells of the triangular lattice within r_c = 2.5: 6 at a, 6 at a sqrt(3)
+    assert math.sqrt(3.0) * a < RC < 2.0 * a
+    shells = [(6, a), (6, math.sqrt(3.0) * a)]
+    f, U, W, npairs = oracle.lc_forces(p[:, 0], p[:, 1], p[:, 2], L, RC)
+    n = p.shape[0]
+    assert np.abs(f).max() < 1e-10          # every force vanishes by symmetry
+    assert npairs == n * 12 // 2
+    u_site = 0.5 * sum(z * lj_u(r) for z, r in shells)
+    w_site = 0.5 * sum(z * (-r * lj_du(r)) for z, r in shells)
+    assert U / n == pytest.approx(u_site, rel=1e-12)
+    assert W / n == pytest.approx(w_site, rel=1e-12)
+
+
+def test_2d_forces_stay_in_plane_and_lc_equals_nsq():
+    b = inputs.tri_box(12, 10, 0.7, 0.5, jitter=0.2)
+    p, L = embed_2d(b["pos"], b["box"])
+    f1, U1, W1, n1 = oracle.lc_forces(p[:, 0], p[:, 1], p[:, 2], L, RC)
+    f2, U2, W2, n2 = oracle.nsq_forces(p[:, 0], p[:, 1], p[:, 2], L, RC)
+    rms = math.sqrt((f2 ** 2).sum(1).mean())
+    assert n1 == n2 and n1 > 0
+    assert np.abs(f1 - f2).max() < 1e-11 * rms
+    assert np.all(f1[:, 2] == 0.0)
+    assert U1 == pytest.approx(U2, rel=1e-12)
