@@ -49,6 +49,7 @@ enum Mode : int { kColour = 0, kAtomic = 1, kFullShell = 2, kBuffer = 3, kDag = 
 constexpr int kJCap = 512;      // neighbour slots listed per batch (per warp)
 constexpr int kMaxNb = 27;      // neighbour cells per task
 constexpr int kJdCap = 256;     // pruned neighbours whose data is kept in shared memory
+constexpr int kPruneRounds = 4; // neighbour rounds of 32 whose loads the prune issues together
 
 struct ForceArgs {
     Grid g;
@@ -537,30 +538,30 @@ __device__ __forceinline__ int prune_list(const ForceArgs &a, WarpSmem<float> &s
                                           float3 bmax, float keep2, bool first_chunk, int lane) {
     int nk = 0;
     const unsigned below = (1u << lane) - 1u;
-    for (int e0 = 0; e0 < total; e0 += 2 * kWarp) {
-        // two rounds per step: both loads in flight before either test
-        const int ea = e0 + lane, eb = e0 + kWarp + lane;
-        int wa = 0, wb = 0;
-        float4 pa = make_float4(0.f, 0.f, 0.f, 0.f), pb = pa;
-        if (ea < total) { wa = sm.jl[ea]; pa = a.p4[wa & ((1 << 26) - 1)]; }
-        if (eb < total) { wb = sm.jl[eb]; pb = a.p4[wb & ((1 << 26) - 1)]; }
-        bool ka, kb;
-        prune_test<MODE>(a, sm, ea, total, bmin, bmax, keep2, first_chunk, wa, pa, ka);
-        prune_test<MODE>(a, sm, eb, total, bmin, bmax, keep2, first_chunk, wb, pb, kb);
-        const unsigned ma = __ballot_sync(kFull, ka);
-        if (ka) {
-            const int pos = nk + __popc(ma & below);
-            sm.jk[pos] = wa;
-            if (pos < kJdCap) sm.jd[pos] = pa;
+    for (int e0 = 0; e0 < total; e0 += kPruneRounds * kWarp) {
+        // kPruneRounds rounds per step: all their loads in flight before any test
+        int w[kPruneRounds];
+        float4 p[kPruneRounds];
+#pragma unroll
+        for (int r = 0; r < kPruneRounds; ++r) {
+            const int e = e0 + r * kWarp + lane;
+            w[r] = 0;
+            p[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e < total) { w[r] = sm.jl[e]; p[r] = a.p4[w[r] & ((1 << 26) - 1)]; }
         }
-        nk += __popc(ma);
-        const unsigned mb = __ballot_sync(kFull, kb);
-        if (kb) {
-            const int pos = nk + __popc(mb & below);
-            sm.jk[pos] = wb;
-            if (pos < kJdCap) sm.jd[pos] = pb;
+#pragma unroll
+        for (int r = 0; r < kPruneRounds; ++r) {
+            const int e = e0 + r * kWarp + lane;
+            bool k;
+            prune_test<MODE>(a, sm, e, total, bmin, bmax, keep2, first_chunk, w[r], p[r], k);
+            const unsigned m = __ballot_sync(kFull, k);
+            if (k) {
+                const int pos = nk + __popc(m & below);
+                sm.jk[pos] = w[r];
+                if (pos < kJdCap) sm.jd[pos] = p[r];
+            }
+            nk += __popc(m);
         }
-        nk += __popc(mb);
     }
     __syncwarp();
     return nk;
