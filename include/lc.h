@@ -104,9 +104,12 @@ lc_status lc_create(const double box[3], double rc, int64_t n, lc_precision prec
 
 /* Copy the particle state in.  pos, vel: [n][3]; vel may be NULL (zero
  * velocities).  id: reserved, must be NULL (IDs are 0 .. n-1, the row index).
- * on_device != 0: the pointers are device memory, else host memory.
- * Positions may lie outside the box; they are wrapped when binned.
- * Marks the binning and the forces stale. */
+ * on_device != 0: the pointers are device memory, else host memory: page-
+ * locked, device-mapped host arrays are read in place by the set-up kernel,
+ * other host memory is first copied to the device; either way the call
+ * synchronises the stream before returning, so host arrays are the caller's
+ * again on return.  Positions may lie outside the box; they are wrapped when
+ * binned.  Marks the binning and the forces stale. */
 lc_status lc_set_state(lc_ctx *ctx, const double *pos, const double *vel, const int32_t *id,
                        int on_device, void *stream);
 

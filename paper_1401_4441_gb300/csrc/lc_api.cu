@@ -387,6 +387,17 @@ void lc_destroy(lc_ctx *ctx) {
     free_ctx(ctx);
 }
 
+// Device address of a page-locked, device-mapped host array, or nullptr.
+static const double *mapped_host(const double *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+    return static_cast<const double *>(at.devicePointer);
+}
+
 lc_status lc_set_state(lc_ctx *c, const double *pos, const double *vel, const int32_t *id, int on_device,
                        void *stream) {
     if (!c || (!pos && c->n > 0) || id) return LC_ERR_INVALID_ARG;
@@ -394,10 +405,19 @@ lc_status lc_set_state(lc_ctx *c, const double *pos, const double *vel, const in
     const size_t bytes = sizeof(double) * 3 * (size_t)c->n;
     const double *dpos = pos, *dvel = vel;
     if (c->n > 0 && !on_device) {
-        // stage through the force buffer (3n doubles) and the Kahan buffer
-        LC_TRY(cudaMemcpyAsync(c->fx, pos, bytes, cudaMemcpyHostToDevice, s));
-        dpos = c->fx;
-        if (vel) {
+        // Page-locked host arrays are read in place by the set-up kernel
+        // (device-mapped; over NVLink-C2C on GB300); other host memory is
+        // staged through the force buffer and the next-state buffer.
+        const double *mp = mapped_host(pos), *mv = vel ? mapped_host(vel) : nullptr;
+        if (mp) {
+            dpos = mp;
+        } else {
+            LC_TRY(cudaMemcpyAsync(c->fx, pos, bytes, cudaMemcpyHostToDevice, s));
+            dpos = c->fx;
+        }
+        if (vel && mv) {
+            dvel = mv;
+        } else if (vel) {
             LC_TRY(cudaMemcpyAsync(c->nxt.x, vel, bytes, cudaMemcpyHostToDevice, s));
             dvel = c->nxt.x;
         }

@@ -288,3 +288,28 @@ def test_16m_sampled(lc):
     # Newton's third law: the net force per particle vanishes (lattice
     # rounding is coherent across cells, so bound the mean, not sqrt(N))
     assert np.abs(f.sum(0)).max() < 1e-6 * pos.shape[0]
+
+
+def test_set_state_host_paths(lc):
+    """Pageable host arrays (copied), page-locked host arrays (read in place
+    by the set-up kernel) and device arrays give the same binned state and
+    forces, bit for bit."""
+    import torch
+    b = inputs.fcc_box(4000, 0.8442, 0.72, jitter=0.05)
+    pos, vel = b["pos"], b["vel"]
+    outs = []
+    for kind in ("pageable", "pinned", "device"):
+        if kind == "pageable":
+            p, v = pos, vel
+        elif kind == "pinned":
+            p, v = torch.from_numpy(pos).pin_memory(), torch.from_numpy(vel).pin_memory()
+        else:
+            p, v = torch.from_numpy(pos).cuda(), torch.from_numpy(vel).cuda()
+        with lc.Box(b["box"], RC, pos.shape[0], "mixed") as g:
+            g.set_state(p, v)
+            g.forces("buffer")
+            outs.append((g.get("perm"), g.get("forces"), g.get("vel")))
+    for perm, f, v in outs[1:]:
+        assert np.array_equal(perm, outs[0][0])
+        assert np.array_equal(f, outs[0][1])
+        assert np.array_equal(v, outs[0][2])
