@@ -155,7 +155,7 @@ static void free_ctx(Ctx *c) {
     if (!c) return;
     void *ptrs[] = {c->cur.x, c->cur.vx, c->cur.id, c->nxt.x, c->nxt.vx, c->nxt.id, c->d_cell, c->d_rank,
                     c->d_count, c->d_start, c->d_src, c->d_key, c->d_blocksums, c->d_colour, c->d_p4, c->fx, c->kx,
-                    c->d_warp_acc, c->d_warp_pairs, c->d_kin_part, c->d_result, c->d_npairs, c->d_err,
+                    c->d_warp_acc, c->d_warp_pairs, c->d_kin_part, c->d_result,
                     c->d_stamp, c->d_visit, c->d_counters, c->d_boxes, c->d_cell_box, c->d_slot_box,
                     c->d_box_acc, c->d_box_pairs, c->d_box_out, c->d_fbuf};
     for (void *p : ptrs)
@@ -163,6 +163,7 @@ static void free_ctx(Ctx *c) {
     for (int k = 0; k < 2 * kNumSched; ++k)
         if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
     for (DagDev *d : c->dag) free_dag(d);
+    if (c->h_out) cudaFreeHost(c->h_out);
     free(c->h_boxes);
     delete static_cast<lc_ctx *>(c);
 }
@@ -194,16 +195,18 @@ static cudaError_t alloc_common(Ctx *c) {
         (e = dalloc(&c->d_blocksums, (size_t)ntiles + 1)) || (e = dalloc(&c->d_colour, NC)) ||
         (e = dalloc(&c->d_p4, N)) || (e = dalloc(&c->fx, 3 * N)) || (e = dalloc(&c->kx, 3 * N)) ||
         (e = dalloc(&c->d_warp_acc, 4 * (size_t)c->nwarp_max)) || (e = dalloc(&c->d_warp_pairs, (size_t)c->nwarp_max)) ||
-        (e = dalloc(&c->d_kin_part, (size_t)c->num_sms * 2)) || (e = dalloc(&c->d_result, 4)) ||
-        (e = dalloc(&c->d_npairs, 1)) || (e = dalloc(&c->d_err, 1)) || (e = dalloc(&c->d_stamp, NC)) ||
+        (e = dalloc(&c->d_kin_part, (size_t)c->num_sms * 2)) || (e = dalloc(&c->d_result, 8)) ||
+        (e = cudaHostAlloc(&c->h_out, 64, cudaHostAllocDefault)) || (e = dalloc(&c->d_stamp, NC)) ||
         (e = dalloc(&c->d_visit, 27 * NC)) || (e = dalloc(&c->d_counters, 4)))
         return e;
+    c->d_npairs = reinterpret_cast<long long *>(c->d_result + 4);
+    c->d_err = reinterpret_cast<int *>(c->d_result + 5);
     c->state_a = c->cur.x;
     if ((e = init_force_kernels())) return e;
     c->fy = c->fx + N; c->fz = c->fx + 2 * N;
     c->ky = c->kx + N; c->kz = c->kx + 2 * N;
     cudaStream_t s = 0;
-    if ((e = cudaMemsetAsync(c->d_err, 0, sizeof(int), s)) || (e = cudaMemsetAsync(c->d_result, 0, 4 * sizeof(double), s)) ||
+    if ((e = cudaMemsetAsync(c->d_result, 0, 8 * sizeof(double), s)) ||   // energies, pair count, flags
         (e = cudaMemsetAsync(c->fx, 0, 3 * N * sizeof(double), s)))
         return e;
     return cudaSuccess;
@@ -475,15 +478,18 @@ lc_status lc_forces(lc_ctx *c, lc_schedule sched, void *stream) {
 // One Verlet step as a sequence of stream-ordered launches.  stats: the
 // force evaluation also produces energy, virial and pair count (the last
 // step of every lc_verlet_step call does, so lc_energy_virial stays valid).
+// The kick + drift that opens the step is fused into the binning's cell
+// pass; `pending`: the previous step's closing kick was left out and is
+// fused there too (same arithmetic); `close`: end with the closing kick.
 static cudaError_t step_launches(lc_ctx *c, double dt, lc_schedule sched, cudaStream_t s, int *launches,
-                                 bool stats) {
+                                 bool stats, bool pending = false, bool close = true) {
     cudaError_t e;
-    if ((e = launch_kick_drift(c, dt, s))) return e;
-    ++*launches;
-    if ((e = launch_bin(c, s, launches))) return e;
+    if ((e = launch_bin(c, s, launches, pending ? 2 : 1, dt))) return e;
     if ((e = launch_forces(c, sched, s, launches, stats))) return e;
-    if ((e = launch_kick(c, dt, s))) return e;
-    ++*launches;
+    if (close) {
+        if ((e = launch_kick(c, dt, s))) return e;
+        ++*launches;
+    }
     return cudaSuccess;
 }
 
@@ -512,8 +518,8 @@ lc_status lc_verlet_step(lc_ctx *c, double dt, int nsteps, lc_schedule sched, vo
         cudaGraph_t graph;
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         int per2 = 0;
-        if (!e) e = step_launches(c, dt, sched, cap, &per2, false);
-        if (!e) e = step_launches(c, dt, sched, cap, &per2, true);
+        if (!e) e = step_launches(c, dt, sched, cap, &per2, false, false, false);
+        if (!e) e = step_launches(c, dt, sched, cap, &per2, true, true, true);
         cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
         c->cur = saved_cur; c->nxt = saved_nxt;   // two swaps: same as before
         if (!e) e = e2;
@@ -564,12 +570,14 @@ lc_status lc_energy_virial(lc_ctx *c, double *u_pot, double *k_kin, double *viri
         return st;
     }
     LC_TRY(launch_kinetic(c, s));
-    double r[4];
-    long long np = 0;
-    LC_TRY(cudaMemcpyAsync(r, c->d_result, sizeof(r), cudaMemcpyDeviceToHost, s));
-    LC_TRY(cudaMemcpyAsync(&np, c->d_npairs, sizeof(np), cudaMemcpyDeviceToHost, s));
-    lc_status st = read_err(c, s);
-    if (st) return st;
+    // one read-back of the result block: energies, pair count, error flags
+    LC_TRY(cudaMemcpyAsync(c->h_out, c->d_result, 48, cudaMemcpyDeviceToHost, s));
+    LC_TRY(cudaStreamSynchronize(s));
+    const double *r = static_cast<const double *>(c->h_out);
+    const long long np = *reinterpret_cast<const long long *>(r + 4);
+    const int err = *reinterpret_cast<const int *>(r + 5);
+    if (err & kErrNonfinite) return LC_ERR_NONFINITE;
+    if (err & kErrTimeout) return LC_ERR_TIMEOUT;
     if (u_pot) *u_pot = r[0];
     if (virial) *virial = r[1];
     if (npairs) *npairs = (int64_t)np;

@@ -27,9 +27,19 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 
 // BATCHED: slot s belongs to box slot_box[s] (boxes keep their slot ranges),
 // whose grid gives the local cell; the global cell adds the box's offset.
-template <bool BATCHED>
+// KICKS: velocity-Verlet updates fused in front of the cell index (the
+// integrator's pass over the state and the binning's first pass become
+// one): 0 none; 1 v += h F, x += dt v (the start of a step); 2 the previous
+// step's closing v += h F first (same forces, same FMAs as two launches).
+struct Drift {
+    double half, dt;
+    double *vx, *vy, *vz;
+    const double *fx, *fy, *fz;
+};
+
+template <bool BATCHED, int KICKS>
 __global__ void k_cellid(Grid g1, const BoxDev *__restrict__ boxes, const unsigned short *__restrict__ slot_box, int n,
-                         const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+                         double *__restrict__ x, double *__restrict__ y, double *__restrict__ z, Drift dr,
                          int *__restrict__ cell, int *__restrict__ rank, int *__restrict__ count, int *__restrict__ err) {
     const int lane = threadIdx.x & 31;
     for (int s0 = blockIdx.x * blockDim.x; s0 < n; s0 += gridDim.x * blockDim.x) {
@@ -39,7 +49,19 @@ __global__ void k_cellid(Grid g1, const BoxDev *__restrict__ boxes, const unsign
         if (act) {
             const BoxDev *bd = BATCHED ? &boxes[slot_box[s]] : nullptr;
             const Grid &g = BATCHED ? bd->g : g1;
-            const double X[3] = {x[s], y[s], z[s]};
+            double X[3] = {x[s], y[s], z[s]};
+            if constexpr (KICKS > 0) {
+                double v[3] = {dr.vx[s], dr.vy[s], dr.vz[s]};
+                const double f[3] = {dr.fx[s], dr.fy[s], dr.fz[s]};
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    if (KICKS == 2) v[d] = fma(dr.half, f[d], v[d]);
+                    v[d] = fma(dr.half, f[d], v[d]);
+                    X[d] = fma(dr.dt, v[d], X[d]);
+                }
+                dr.vx[s] = v[0]; dr.vy[s] = v[1]; dr.vz[s] = v[2];
+                x[s] = X[0]; y[s] = X[1]; z[s] = X[2];
+            }
             int cc[3];
             bool fast = true;
 #pragma unroll
@@ -259,7 +281,14 @@ cudaError_t launch_colour(Ctx *c, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches) {
+template <bool BATCHED, int KICKS>
+static void cellid_launch(Ctx *c, int grid_n, const Drift &dr, cudaStream_t s) {
+    k_cellid<BATCHED, KICKS><<<grid_n, 256, 0, s>>>(c->g, BATCHED ? c->d_boxes : nullptr,
+                                                    BATCHED ? c->d_slot_box : nullptr, (int)c->n, c->cur.x, c->cur.y,
+                                                    c->cur.z, dr, c->d_cell, c->d_rank, c->d_count, c->d_err);
+}
+
+cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches, int kicks, double dt) {
     const int n = (int)c->n;
     const int ncell = c->g.ncell;
     const int ntiles = (ncell + kScanTile - 1) / kScanTile;
@@ -267,12 +296,14 @@ cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches) {
     cudaError_t e = cudaMemsetAsync(c->d_count, 0, sizeof(int) * (size_t)ncell, s);
     if (e) return e;
     if (n > 0) {
-        if (c->nbox > 0)
-            k_cellid<true><<<grid_n, 256, 0, s>>>(c->g, c->d_boxes, c->d_slot_box, n, c->cur.x, c->cur.y, c->cur.z,
-                                                  c->d_cell, c->d_rank, c->d_count, c->d_err);
-        else
-            k_cellid<false><<<grid_n, 256, 0, s>>>(c->g, nullptr, nullptr, n, c->cur.x, c->cur.y, c->cur.z, c->d_cell,
-                                                   c->d_rank, c->d_count, c->d_err);
+        Drift dr;
+        dr.half = 0.5 * dt; dr.dt = dt;
+        dr.vx = c->cur.vx; dr.vy = c->cur.vy; dr.vz = c->cur.vz;
+        dr.fx = c->fx; dr.fy = c->fy; dr.fz = c->fz;
+        const bool b = c->nbox > 0;
+        if (kicks == 0) b ? cellid_launch<true, 0>(c, grid_n, dr, s) : cellid_launch<false, 0>(c, grid_n, dr, s);
+        else if (kicks == 1) b ? cellid_launch<true, 1>(c, grid_n, dr, s) : cellid_launch<false, 1>(c, grid_n, dr, s);
+        else b ? cellid_launch<true, 2>(c, grid_n, dr, s) : cellid_launch<false, 2>(c, grid_n, dr, s);
         ++*launches;
     }
     k_scan_tiles<<<ntiles, kScanThreads, 0, s>>>(ncell, c->d_count, c->d_start, c->d_blocksums);

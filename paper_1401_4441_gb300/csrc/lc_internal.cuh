@@ -140,9 +140,12 @@ struct Ctx {
     double *d_warp_acc;    // per-warp partials: [nwarp_max][4] (s6, s12, K, spare)
     long long *d_warp_pairs;
     double *d_kin_part;    // per-block partial sums of v^2
-    double *d_result;      // [4] U, W, npairs (as double), K
-    long long *d_npairs;
-    int *d_err;
+    // one 64-byte device block, read back in one copy: U, W, pairs (as
+    // double), K, then the pair count and the error flags
+    double *d_result;      // [4] U, W, npairs (as double), K  (block + 0)
+    long long *d_npairs;   // block + 32
+    int *d_err;            // block + 40
+    void *h_out;           // page-locked host copy of the block
     int nwarp_max;
     int nwarp_used;        // warps of the last force evaluation (their partials are reduced)
     // check buffers
@@ -175,9 +178,10 @@ struct Ctx {
 };
 
 // ---- kernels / launchers (stream-ordered, return cudaError_t) -------------
-cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches);
+// Binning; kicks = 1 / 2 fuses the start of a Verlet step (kick + drift of
+// step dt) / also the previous step's closing kick into the cell pass.
+cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches, int kicks = 0, double dt = 0.0);
 cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launches, bool stats = true);
-cudaError_t launch_kick_drift(Ctx *c, double dt, cudaStream_t s);
 cudaError_t launch_kick(Ctx *c, double dt, cudaStream_t s);
 cudaError_t launch_kinetic(Ctx *c, cudaStream_t s);
 cudaError_t launch_energy_reduce(Ctx *c, cudaStream_t s, int full);

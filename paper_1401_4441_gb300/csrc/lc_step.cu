@@ -13,19 +13,6 @@ namespace lc {
 constexpr int kRedThreads = 1024;
 static_assert(kRedThreads == 32 * 32, "k_final_pot reduces one value per warp in a single warp");
 
-__global__ void k_kick_drift(int n, double half, double dt, State st, const double *__restrict__ fx,
-                             const double *__restrict__ fy, const double *__restrict__ fz) {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        double vx = fma(half, fx[s], st.vx[s]);
-        double vy = fma(half, fy[s], st.vy[s]);
-        double vz = fma(half, fz[s], st.vz[s]);
-        st.vx[s] = vx; st.vy[s] = vy; st.vz[s] = vz;
-        st.x[s] = fma(dt, vx, st.x[s]);
-        st.y[s] = fma(dt, vy, st.y[s]);
-        st.z[s] = fma(dt, vz, st.z[s]);
-    }
-}
-
 __global__ void k_kick(int n, double half, State st, const double *__restrict__ fx,
                        const double *__restrict__ fy, const double *__restrict__ fz) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
@@ -147,12 +134,6 @@ cudaError_t launch_box_energy(Ctx *c, cudaStream_t s, int full) {
 
 cudaError_t launch_box_kinetic(Ctx *c, cudaStream_t s) {
     k_box_kinetic<<<c->nbox, 256, 0, s>>>(c->d_boxes, c->cur, c->d_box_out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_kick_drift(Ctx *c, double dt, cudaStream_t s) {
-    if (c->n == 0) return cudaSuccess;
-    k_kick_drift<<<c->num_sms * 8, 256, 0, s>>>((int)c->n, 0.5 * dt, dt, c->cur, c->fx, c->fy, c->fz);
     return cudaGetLastError();
 }
 
