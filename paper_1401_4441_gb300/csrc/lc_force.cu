@@ -599,13 +599,14 @@ __device__ __forceinline__ void pair_loop(const WarpSmem<float> &sm, const float
                                           int jlim, int jexcl, float rc2lo, float rc2hi,
                                           float2 (&ax2)[NI / 2], float2 (&ay2)[NI / 2], float2 (&az2)[NI / 2],
                                           float2 &gx, float2 &gy, float2 &gz, float2 &e6, float2 &e12,
-                                          int &npair, bool &amb) {
+                                          int &npair, bool &amb, int kpairs) {
     const float2 one2 = make_float2(1.0f, 1.0f);
     const float2 c48 = make_float2(48.0f, 48.0f), cm24 = make_float2(-24.0f, -24.0f);
     const float2 npx = make_float2(-pj[0], -pj[0]), npy = make_float2(-pj[1], -pj[1]), npz = make_float2(-pj[2], -pj[2]);
     const float2 nlx = make_float2(-lj[0], -lj[0]), nly = make_float2(-lj[1], -lj[1]), nlz = make_float2(-lj[2], -lj[2]);
 #pragma unroll
     for (int m = 0; m < NI / 2; ++m) {
+        if (m >= kpairs) break;   // the rest of the tile holds only sentinels (warp-uniform)
         const float4 A = lds4(&sm.ipa[m]);
         const float4 B = lds4(&sm.ipb[m]);
         const float4 C = lds4(&sm.ipc[m]);
@@ -724,6 +725,8 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
         int npair = 0;
         __syncwarp();
 
+        // centre pairs of this chunk that hold a particle (the tile's tail is sentinels)
+        const int kpairs = (min(NI, na - i0) + 1) >> 1;
         int b = 0, kin = 0;
         while (b < tc.nnb) {
             int nj = total;
@@ -768,10 +771,10 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
                 bool amb = false;
                 if (__any_sync(kFull, is_self))
                     pair_loop<NI, N3, true, STATS>(sm, pj, lj, jlim, jexcl, rc2lo, rc2hi, ax2, ay2, az2, gx, gy, gz,
-                                                   e6, e12, npair, amb);
+                                                   e6, e12, npair, amb, kpairs);
                 else
                     pair_loop<NI, N3, false, STATS>(sm, pj, lj, jlim, jexcl, rc2lo, rc2hi, ax2, ay2, az2, gx, gy, gz,
-                                                    e6, e12, npair, amb);
+                                                    e6, e12, npair, amb, kpairs);
                 float fjx = -(gx.x + gx.y), fjy = -(gy.x + gy.y), fjz = -(gz.x + gz.y);
                 if (__any_sync(kFull, amb)) {
                     // rare: candidates within the band around r_c^2 are decided
