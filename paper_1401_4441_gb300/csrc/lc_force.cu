@@ -221,6 +221,20 @@ __device__ __forceinline__ void reduce_scatter(T (&v)[NI], int lane) {
 #pragma unroll
     for (int half = NI / 2, m = 16; half >= 1; half >>= 1, m >>= 1) {
         const bool up = (lane & m) != 0;
+        if constexpr (std::is_same<T, float>::value) {
+            if (half >= 2) {   // pairs of adjacent elements: one f32x2 add per pair
+#pragma unroll
+                for (int k = 0; k < half; k += 2) {
+                    const float2 keep = make_float2(up ? v[k + half] : v[k], up ? v[k + half + 1] : v[k + 1]);
+                    const float2 recv = make_float2(__shfl_xor_sync(kFull, up ? v[k] : v[k + half], m),
+                                                    __shfl_xor_sync(kFull, up ? v[k + 1] : v[k + half + 1], m));
+                    const float2 sum = __fadd2_rn(keep, recv);
+                    v[k] = sum.x;
+                    v[k + 1] = sum.y;
+                }
+                continue;
+            }
+        }
 #pragma unroll
         for (int k = 0; k < half; ++k) {
             T send = up ? v[k] : v[k + half];

@@ -242,13 +242,12 @@ __device__ __forceinline__ int cell_coord(double xw, double inv, int nc) {
 // infinities and NaNs keep their class.
 __device__ __forceinline__ double f32_to_f64_bits(float f) {
     const unsigned b = __float_as_uint(f);
-    const unsigned e = (b >> 23) & 0xffu;
-    const unsigned m = b & 0x7fffffu;
-    // exponent rebias 127 -> 1023 (+896), 255 -> 2047 (+1792), 0 -> 0
-    const unsigned eb = e == 0u ? 0u : (e == 0xffu ? 0x7ffu : e + 896u);
-    const unsigned hi = (b & 0x80000000u) | (eb << 20) | (e == 0u ? 0u : (m >> 3));
-    const unsigned lo = e == 0u ? 0u : (m << 29);
-    return __hiloint2double((int)hi, (int)lo);
+    const unsigned a = b & 0x7fffffffu;                          // |f|: exponent and mantissa adjacent
+    unsigned hi = (a >> 3) + (896u << 20);                       // normal: exponent 127 -> 1023 bias
+    hi = a >= 0x7f800000u ? ((a >> 3) | 0x7ff00000u) : hi;       // inf / nan: exponent all ones
+    hi = a < 0x00800000u ? 0u : hi;                              // zero and subnormals: zero
+    const unsigned lo = a < 0x00800000u ? 0u : (b << 29);        // low three mantissa bits
+    return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)lo);
 }
 
 // FP32 view of an FP64 value without the FP64 pipe: the binary64 sign,
