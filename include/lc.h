@@ -170,7 +170,8 @@ lc_status lc_grid(const lc_ctx *ctx, int32_t nc[3], int32_t *ncolours, int32_t *
  * stamped twice within one phase (*conflicts).  For every schedule each
  * cell pair of the half-shell (the full shell for LC_SCHED_FULLSHELL) must be
  * visited exactly once; *coverage_errors counts the pairs that are not.
- * Synchronises the stream. */
+ * Its buffers (27 counters per cell) are allocated on the first call
+ * (LC_ERR_OOM if they cannot be).  Synchronises the stream. */
 lc_status lc_schedule_check(lc_ctx *ctx, lc_schedule sched, int64_t *conflicts,
                             int64_t *coverage_errors, void *stream);
 

@@ -196,8 +196,7 @@ static cudaError_t alloc_common(Ctx *c) {
         (e = dalloc(&c->d_p4, N)) || (e = dalloc(&c->fx, 3 * N)) || (e = dalloc(&c->kx, 3 * N)) ||
         (e = dalloc(&c->d_warp_acc, 4 * (size_t)c->nwarp_max)) || (e = dalloc(&c->d_warp_pairs, (size_t)c->nwarp_max)) ||
         (e = dalloc(&c->d_kin_part, (size_t)c->num_sms * 2)) || (e = dalloc(&c->d_result, 8)) ||
-        (e = cudaHostAlloc(&c->h_out, 64, cudaHostAllocDefault)) || (e = dalloc(&c->d_stamp, NC)) ||
-        (e = dalloc(&c->d_visit, 27 * NC)) || (e = dalloc(&c->d_counters, 4)))
+        (e = cudaHostAlloc(&c->h_out, 64, cudaHostAllocDefault)))
         return e;
     c->d_npairs = reinterpret_cast<long long *>(c->d_result + 4);
     c->d_err = reinterpret_cast<int *>(c->d_result + 5);
@@ -633,6 +632,12 @@ lc_status lc_grid(const lc_ctx *c, int32_t nc[3], int32_t *ncolours, int32_t *np
 
 lc_status lc_schedule_check(lc_ctx *c, lc_schedule sched, int64_t *conflicts, int64_t *coverage_errors, void *stream) {
     if (!c || sched < LC_SCHED_COLOUR || sched > LC_SCHED_BUFFER || c->nbox > 0) return LC_ERR_INVALID_ARG;
+    if (!c->d_visit) {   // the check's buffers (27 counters per cell) on first use
+        const size_t NC = (size_t)c->g.ncell;
+        if (!c->d_stamp) LC_TRY(dalloc(&c->d_stamp, NC));
+        if (!c->d_counters) LC_TRY(dalloc(&c->d_counters, 4));
+        LC_TRY(dalloc(&c->d_visit, 27 * NC));
+    }
     cudaStream_t s = (cudaStream_t)stream;
     LC_TRY(launch_schedule_check(c, sched, s));
     unsigned long long cnt[4];

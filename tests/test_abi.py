@@ -68,3 +68,19 @@ def test_binding_enums_match_header():
     for v, name in lc.STATUS.items():
         assert vals[name] == v
     assert len([k for k in vals if k.startswith("LC_SCHED_")]) == len(lc.SCHED)
+
+
+def test_size_limits_are_checked_on_the_host(so):
+    """Sizes beyond the stated maxima are rejected before any device work:
+    n >= 2^26 particles, more than 1e9 cells, an invalid 2D box."""
+    h = ctypes.c_void_p()
+    so.lc_create.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+    box = (ctypes.c_double * 3)(100.0, 100.0, 100.0)
+    assert so.lc_create(box, 2.5, 1 << 26, 1, ctypes.byref(h)) == 9
+    huge = (ctypes.c_double * 3)(1.0e4, 1.0e4, 1.0e4)
+    assert so.lc_create(huge, 1.0, 10, 1, ctypes.byref(h)) == 9
+    so.lc_create_2d.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+    small2 = (ctypes.c_double * 2)(7.4, 100.0)
+    assert so.lc_create_2d(small2, 2.5, 10, 1, ctypes.byref(h)) == 2
+    assert so.lc_create_2d(None, 2.5, 10, 1, ctypes.byref(h)) == 1
+    assert h.value is None
