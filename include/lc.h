@@ -113,6 +113,21 @@ lc_status lc_create(const double box[3], double rc, int64_t n, lc_precision prec
 lc_status lc_set_state(lc_ctx *ctx, const double *pos, const double *vel, const int32_t *id,
                        int on_device, void *stream);
 
+/* Host input copied ahead, so that the copy of the next state overlaps the
+ * work on the current one.  lc_stage_state queues the copy of pos (and vel,
+ * NULL for zero velocities), [n][3] host arrays, into staging slot 0 or 1
+ * on copy_stream and returns at once: the host arrays must stay unchanged
+ * until the copy is done (copy_stream synchronised, or the slot consumed).
+ * A slot is overwritten only after its previous content was consumed.
+ * lc_set_state_staged then makes a slot the current state, as
+ * lc_set_state would, in stream order on `stream` after the slot's copy.
+ * Page-locked host arrays let the copy run concurrently with kernels.
+ * The slots (96 bytes per particle) are allocated on first use.  Errors:
+ * LC_ERR_INVALID_ARG, LC_ERR_STATE (slot never staged), LC_ERR_OOM,
+ * LC_ERR_CUDA. */
+lc_status lc_stage_state(lc_ctx *ctx, const double *pos, const double *vel, int32_t slot, void *copy_stream);
+lc_status lc_set_state_staged(lc_ctx *ctx, int32_t slot, void *stream);
+
 /* A 2D context (Sec. IV, Fig. 3a: the paper's 2D link-cell case): particles in
  * a periodic box[0] x box[1] rectangle, cells of side >= rc in x and y, the
  * 5-cell half-shell stencil (Newton-3 schedules) or 9 cells (full shell).

@@ -163,6 +163,11 @@ static void free_ctx(Ctx *c) {
     for (int k = 0; k < 2 * kNumSched; ++k)
         if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
     for (DagDev *d : c->dag) free_dag(d);
+    for (int k = 0; k < 2; ++k) {
+        if (c->d_stage[k]) cudaFree(c->d_stage[k]);
+        if (c->ev_staged[k]) cudaEventDestroy(c->ev_staged[k]);
+        if (c->ev_consumed[k]) cudaEventDestroy(c->ev_consumed[k]);
+    }
     if (c->h_out) cudaFreeHost(c->h_out);
     free(c->h_boxes);
     delete static_cast<lc_ctx *>(c);
@@ -427,6 +432,44 @@ lc_status lc_set_state(lc_ctx *c, const double *pos, const double *vel, const in
     LC_TRY(launch_set_state(c, dpos, dvel, s));
     LC_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
     if (!on_device) LC_TRY(cudaStreamSynchronize(s));  // host buffers are the caller's again on return
+    c->have_state = true;
+    c->binned = false;
+    c->forces_valid = false;
+    return LC_OK;
+}
+
+lc_status lc_stage_state(lc_ctx *c, const double *pos, const double *vel, int32_t slot, void *copy_stream) {
+    if (!c || (slot != 0 && slot != 1) || (!pos && c->n > 0)) return LC_ERR_INVALID_ARG;
+    cudaStream_t cs = (cudaStream_t)copy_stream;
+    const size_t bytes = sizeof(double) * 3 * (size_t)c->n;
+    // first use of the slot: buffers and events (each created once)
+    if (!c->d_stage[slot]) LC_TRY(dalloc(&c->d_stage[slot], 6 * (size_t)(c->n > 0 ? c->n : 1)));
+    if (!c->ev_staged[slot]) LC_TRY(cudaEventCreateWithFlags(&c->ev_staged[slot], cudaEventDisableTiming));
+    if (!c->ev_consumed[slot]) {
+        LC_TRY(cudaEventCreateWithFlags(&c->ev_consumed[slot], cudaEventDisableTiming));
+        LC_TRY(cudaEventRecord(c->ev_consumed[slot], cs));
+    }
+    // the slot's previous content must have been consumed before it is overwritten
+    LC_TRY(cudaStreamWaitEvent(cs, c->ev_consumed[slot], 0));
+    if (c->n > 0) {
+        LC_TRY(cudaMemcpyAsync(c->d_stage[slot], pos, bytes, cudaMemcpyHostToDevice, cs));
+        if (vel) LC_TRY(cudaMemcpyAsync(c->d_stage[slot] + 3 * (size_t)c->n, vel, bytes, cudaMemcpyHostToDevice, cs));
+    }
+    c->stage_has_vel[slot] = vel != nullptr;
+    LC_TRY(cudaEventRecord(c->ev_staged[slot], cs));
+    return LC_OK;
+}
+
+lc_status lc_set_state_staged(lc_ctx *c, int32_t slot, void *stream) {
+    if (!c || (slot != 0 && slot != 1)) return LC_ERR_INVALID_ARG;
+    if (!c->d_stage[slot] || !c->ev_staged[slot] || !c->ev_consumed[slot]) return LC_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    LC_TRY(cudaStreamWaitEvent(s, c->ev_staged[slot], 0));
+    const double *pos = c->d_stage[slot];
+    const double *vel = c->stage_has_vel[slot] ? c->d_stage[slot] + 3 * (size_t)c->n : nullptr;
+    LC_TRY(launch_set_state(c, pos, vel, s));
+    LC_TRY(cudaEventRecord(c->ev_consumed[slot], s));
+    LC_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
     c->have_state = true;
     c->binned = false;
     c->forces_valid = false;

@@ -165,6 +165,12 @@ struct Ctx {
     unsigned long long *d_box_pairs;
     double *d_box_out;        // [nbox][4] U, W, pairs, K
     int stats_full;           // last statistics came from the full shell
+    // two staging slots for host input copied ahead (lc_stage_state): raw
+    // [n][3] positions and velocities, allocated on first use, with events
+    // for "copy done" and "consumed"
+    double *d_stage[2];
+    cudaEvent_t ev_staged[2], ev_consumed[2];
+    bool stage_has_vel[2];
     DagDev *dag[2];        // per task-creation order, built on first use
     int dag_perm[14];      // stencil order inside a cell for the cell order
     int dag_perm_n;        // 0: table order

@@ -63,6 +63,8 @@ def _load():
         "lc_dag_plan": ([ip, ctypes.c_int, ip, ctypes.c_int32, lp, lp, lp], ctypes.c_int),
         "lc_dag_stencil_order": ([vp, ip, ctypes.c_int32], ctypes.c_int),
         "lc_create_2d": ([dp, ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctx_pp], ctypes.c_int),
+        "lc_stage_state": ([vp, vp, vp, ctypes.c_int32, vp], ctypes.c_int),
+        "lc_set_state_staged": ([vp, ctypes.c_int32, vp], ctypes.c_int),
         "lc_destroy": ([vp], None),
         "lc_status_str": ([ctypes.c_int], ctypes.c_char_p),
     }
@@ -171,6 +173,21 @@ class Box:
         p, dev = _ptr(pos)
         v, _ = _ptr(vel)
         _check(self._lib.lc_set_state(self._h, p, v, None, dev, _stream(stream)), "lc_set_state")
+
+    def stage_state(self, pos, vel=None, slot=0, copy_stream=None):
+        """Queue the copy of a later state (host arrays, page-locked to
+        overlap) into staging slot 0 or 1 on copy_stream; returns at once."""
+        if isinstance(pos, np.ndarray):
+            raise TypeError("stage_state needs page-locked host tensors (torch .pin_memory())")
+        p, dev = _ptr(pos)
+        v, _ = _ptr(vel)
+        if dev:
+            raise TypeError("stage_state takes host memory")
+        _check(self._lib.lc_stage_state(self._h, p, v, int(slot), _stream(copy_stream)), "lc_stage_state")
+
+    def set_state_staged(self, slot=0, stream=None):
+        """Make staging slot `slot` the current state, after its copy."""
+        _check(self._lib.lc_set_state_staged(self._h, int(slot), _stream(stream)), "lc_set_state_staged")
 
     def bin(self, stream=None):
         _check(self._lib.lc_bin(self._h, _stream(stream)), "lc_bin")

@@ -313,3 +313,32 @@ def test_set_state_host_paths(lc):
         assert np.array_equal(perm, outs[0][0])
         assert np.array_equal(f, outs[0][1])
         assert np.array_equal(v, outs[0][2])
+
+
+def test_staged_host_input(lc):
+    """Host input staged ahead on a copy stream (two slots) gives the same
+    state and forces as lc_set_state, and slots can be refilled while the
+    other one is in use."""
+    import torch
+    b1 = inputs.fcc_box(4000, 0.8442, 0.72, jitter=0.05)
+    b2 = inputs.fcc_box(4000, 0.8442, 0.72, seed=9, jitter=0.05)
+    h = [(torch.from_numpy(b["pos"]).pin_memory(), torch.from_numpy(b["vel"]).pin_memory()) for b in (b1, b2)]
+    ref = []
+    with lc.Box(b1["box"], RC, 4000, "mixed") as g:
+        for p, v in h:
+            g.set_state(p, v)
+            g.forces("buffer")
+            ref.append((g.get("forces"), g.get("vel")))
+    cs = torch.cuda.Stream()
+    with lc.Box(b1["box"], RC, 4000, "mixed") as g:
+        with pytest.raises(lc.LCError):
+            g.set_state_staged(1)                 # never staged
+        g.stage_state(*h[0], slot=0, copy_stream=cs.cuda_stream)
+        for k in range(4):
+            g.set_state_staged(k % 2)
+            g.stage_state(*h[(k + 1) % 2], slot=(k + 1) % 2, copy_stream=cs.cuda_stream)
+            g.forces("buffer")
+            f, v = g.get("forces"), g.get("vel")
+            assert np.array_equal(f, ref[k % 2][0])
+            assert np.array_equal(v, ref[k % 2][1])
+        torch.cuda.synchronize()
