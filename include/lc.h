@@ -68,11 +68,17 @@ typedef enum {
     LC_SCHED_COLOUR = 0,    /* phases (offset group, colour), disjoint writes   */
     LC_SCHED_ATOMIC = 1,    /* one pass, both cells updated by atomic adds      */
     LC_SCHED_FULLSHELL = 2, /* all 27 cells, own cell written only, no Newton-3 */
-    LC_SCHED_BUFFER = 3     /* one pass into private per-(cell, offset) buffers,
+    LC_SCHED_BUFFER = 3,    /* one pass into private per-(cell, offset) buffers,
                                then a fixed-order reduce: no atomics, no phases,
                                forces bit-reproducible from run to run; buffers
                                of 15 x 3 x n floats (FP64: doubles) are
                                allocated on the first use of the schedule    */
+    LC_SCHED_LIST = 4       /* not in the paper: Verlet neighbour lists with a
+                               skin (lc_set_skin), built from link cells of
+                               side >= rc + skin and reused across steps; one
+                               thread per particle over its own full list, so
+                               no write is shared.  Mixed precision, single
+                               box only (2D included)                        */
 } lc_schedule;
 
 typedef enum {
@@ -150,8 +156,11 @@ lc_status lc_bin(lc_ctx *ctx, void *stream);
 /* One force evaluation with the given schedule (bins first if the positions
  * changed since the last binning).  Also produces the potential energy,
  * the virial and the number of pairs inside r_c.  LC_ERR_OOM if the buffers
- * of LC_SCHED_BUFFER cannot be allocated; LC_ERR_INVALID_ARG for
- * LC_SCHED_COLOUR on a batch of boxes. */
+ * of LC_SCHED_BUFFER or the lists of LC_SCHED_LIST cannot be allocated;
+ * LC_ERR_INVALID_ARG for LC_SCHED_COLOUR on a batch of boxes, and for
+ * LC_SCHED_LIST on a batch or an FP64 context.  LC_SCHED_LIST bins on the
+ * list grid and builds the lists first (the first build also sizes them,
+ * which synchronises the stream). */
 lc_status lc_forces(lc_ctx *ctx, lc_schedule sched, void *stream);
 
 /* nsteps velocity-Verlet steps of size dt (m = 1): v += dt/2 F; x += dt v;
@@ -159,8 +168,39 @@ lc_status lc_forces(lc_ctx *ctx, lc_schedule sched, void *stream);
  * The step's kernels are captured once into a CUDA graph per (schedule, dt)
  * and replayed.  Potential energy, virial and pair count are accumulated in
  * the last step of the call (lc_energy_virial reports them); the other
- * steps skip that accumulation. */
+ * steps skip that accumulation.  LC_SCHED_LIST: see the list section below
+ * (steps between builds do no binning). */
 lc_status lc_verlet_step(lc_ctx *ctx, double dt, int nsteps, lc_schedule sched, void *stream);
+
+/* ---- Verlet neighbour lists (LC_SCHED_LIST) ------------------------------
+ * Not part of the paper's method, which sweeps the link cells every step
+ * (Sec. IV); an extension that trades memory for fewer candidates per pair.
+ * A list build bins the particles on a list grid of cells of side >= rc + skin
+ * and records for every particle all partners within rc + skin (both
+ * directions).  While no particle has moved by skin / 2 since the build,
+ * every pair inside rc is on the lists.  lc_forces(LC_SCHED_LIST) builds
+ * and evaluates; lc_verlet_step(LC_SCHED_LIST) reuses the lists and rebuilds
+ * when a particle's displacement since the build exceeds skin / 2, a
+ * decision taken on the device inside the step's CUDA graph (a conditional
+ * node), so the host never waits.  Positions stay unwrapped between builds
+ * (lc_get wraps them).  The binning of the other schedules is stale after
+ * list calls (LC_GET_CELL_* return LC_ERR_STATE until the next lc_bin).
+ *
+ * lc_set_skin: skin >= 0 (default 0.3); kmax = entries per particle kept in
+ * the list (0: sized from the first build, 1.25 x the longest row + 8).
+ * A row longer than kmax is still exact: its partners are swept from the
+ * cells.  Frees the current lists (allocated again on next use: 4 kmax + 36
+ * bytes per particle).  LC_ERR_INVALID_ARG for a negative or non-finite skin
+ * or kmax < 0; LC_ERR_BOX_TOO_SMALL if some box edge holds fewer than 3 cells
+ * of side rc + skin (checked on first use). */
+lc_status lc_set_skin(lc_ctx *ctx, double skin, int32_t kmax);
+
+/* Counters of the lists since the last lc_set_skin: builds, rows longer
+ * than kmax over all builds, the longest row seen, steps whose displacement
+ * check asked for a rebuild, and the row capacity kmax.  Any output may be
+ * NULL.  Synchronises the stream. */
+lc_status lc_list_info(lc_ctx *ctx, int64_t *builds, int64_t *long_rows, int64_t *longest_row,
+                       int64_t *rebuild_steps, int32_t *kmax, void *stream);
 
 /* Energies of the current state, FP64: potential U and virial W of the last
  * force evaluation, kinetic K = 1/2 sum v^2 of the current velocities, and the

@@ -157,12 +157,15 @@ static void free_ctx(Ctx *c) {
                     c->d_count, c->d_start, c->d_src, c->d_key, c->d_blocksums, c->d_colour, c->d_p4, c->fx, c->kx,
                     c->d_warp_acc, c->d_warp_pairs, c->d_kin_part, c->d_result,
                     c->d_stamp, c->d_visit, c->d_counters, c->d_boxes, c->d_cell_box, c->d_slot_box,
-                    c->d_box_acc, c->d_box_pairs, c->d_box_out, c->d_fbuf};
+                    c->d_box_acc, c->d_box_pairs, c->d_box_out, c->d_fbuf, c->d_nbr, c->d_nn, c->d_q4,
+                    c->d_list_stats};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k < 2 * kNumSched; ++k)
         if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
     for (DagDev *d : c->dag) free_dag(d);
+    for (cudaGraphExec_t gx : c->list_graph)
+        if (gx) cudaGraphExecDestroy(gx);
     for (int k = 0; k < 2; ++k) {
         if (c->d_stage[k]) cudaFree(c->d_stage[k]);
         if (c->ev_staged[k]) cudaEventDestroy(c->ev_staged[k]);
@@ -259,6 +262,7 @@ static lc_status create_single(const double box[3], double rc, int64_t n, lc_pre
     lc_ctx *c = new lc_ctx();
     memset(static_cast<Ctx *>(c), 0, sizeof(Ctx));
     make_grid(&c->g, box, rc, dims);
+    c->skin = 0.3;
     c->n = n;
     c->prec = prec;
     c->ni = 16;
@@ -435,6 +439,7 @@ lc_status lc_set_state(lc_ctx *c, const double *pos, const double *vel, const in
     c->have_state = true;
     c->binned = false;
     c->forces_valid = false;
+    c->list_valid = false;
     return LC_OK;
 }
 
@@ -473,6 +478,7 @@ lc_status lc_set_state_staged(lc_ctx *c, int32_t slot, void *stream) {
     c->have_state = true;
     c->binned = false;
     c->forces_valid = false;
+    c->list_valid = false;
     return LC_OK;
 }
 
@@ -507,12 +513,118 @@ static lc_status do_forces(lc_ctx *c, lc_schedule sched, cudaStream_t s, int *la
     return LC_OK;
 }
 
+// ---- Verlet neighbour lists ------------------------------------------------
+static void drop_list_graphs(lc_ctx *c) {
+    for (int k = 0; k < 4; ++k)
+        if (c->list_graph[k]) { cudaGraphExecDestroy(c->list_graph[k]); c->list_graph[k] = nullptr; }
+}
+
+// List grid, buffers and row capacity on first use (a counting build of the
+// current state sizes the rows unless lc_set_skin fixed kmax).
+static lc_status ensure_list(lc_ctx *c, cudaStream_t s) {
+    if (c->d_nbr) return LC_OK;
+    if (!make_list_grid(c)) return LC_ERR_BOX_TOO_SMALL;
+    const size_t N = (size_t)(c->n > 0 ? c->n : 1);
+    if (!c->d_nn) LC_TRY(dalloc(&c->d_nn, N));
+    if (!c->d_q4) LC_TRY(dalloc(&c->d_q4, 2 * N));
+    if (!c->d_list_stats) {
+        LC_TRY(dalloc(&c->d_list_stats, 5));   // 4 counters + 2 control words
+        LC_TRY(cudaMemsetAsync(c->d_list_stats, 0, 5 * sizeof(unsigned long long), s));
+    }
+    int64_t kmax = c->list_kmax_req;
+    if (kmax == 0) {
+        int l = 0;
+        const Grid saved = c->g;
+        c->g = c->gl;
+        cudaError_t e = launch_bin(c, s, &l, 0, 0.0);
+        c->g = saved;
+        LC_TRY(e);
+        c->list_kmax = 0;
+        LC_TRY(launch_list_build(c, s, false));
+        unsigned long long longest = 0;
+        LC_TRY(cudaMemcpyAsync(&longest, c->d_list_stats + 2, sizeof(longest), cudaMemcpyDeviceToHost, s));
+        LC_TRY(cudaStreamSynchronize(s));
+        LC_TRY(cudaMemsetAsync(c->d_list_stats + 2, 0, sizeof(longest), s));
+        kmax = (int64_t)(longest + longest / 4 + 8);
+    }
+    if (kmax * (int64_t)N > (int64_t(1) << 36)) return LC_ERR_TOO_LARGE;
+    c->list_kmax = (int)kmax;
+    LC_TRY(dalloc(&c->d_nbr, (size_t)kmax * N));
+    return LC_OK;
+}
+
+static lc_status list_forces(lc_ctx *c, cudaStream_t s, int *launches) {
+    if (c->prec != LC_PREC_MIXED || c->nbox > 0) return LC_ERR_INVALID_ARG;
+    LC_TRY_ST(ensure_list(c, s));
+    LC_TRY(launch_list_rebuild(c, s, false, launches));
+    LC_TRY(launch_list_forces(c, s, true, launches));
+    c->binned = false;   // the cells are the list grid's
+    c->forces_valid = true;
+    c->list_valid = true;
+    return LC_OK;
+}
+
+static lc_status list_verlet(lc_ctx *c, double dt, int nsteps, cudaStream_t s) {
+    if (c->prec != LC_PREC_MIXED || c->nbox > 0) return LC_ERR_INVALID_ARG;
+    int launches = 0;
+    if (!c->list_valid || !c->forces_valid) LC_TRY_ST(list_forces(c, s, &launches));
+    const int par = c->cur.x == c->state_a ? 0 : 1;   // the graphs keep the buffers in place
+    int done = 0;
+    while (done < nsteps) {
+        const int k = nsteps - done >= 2 ? 2 : 1;
+        const int gi = 2 * (k - 1) + par;
+        if (!c->list_graph[gi] || c->list_graph_dt[gi] != dt) {
+            if (c->list_graph[gi]) { cudaGraphExecDestroy(c->list_graph[gi]); c->list_graph[gi] = nullptr; }
+            int per = 0;
+            LC_TRY(capture_list_steps(c, dt, k, &c->list_graph[gi], &per));
+            c->list_graph_dt[gi] = dt;
+            c->launches_step = per / k;
+        }
+        LC_TRY(cudaGraphLaunch(c->list_graph[gi], s));
+        done += k;
+    }
+    c->binned = false;
+    c->forces_valid = true;
+    c->list_valid = true;
+    return LC_OK;
+}
+
+lc_status lc_set_skin(lc_ctx *c, double skin, int32_t kmax) {
+    if (!c || !(skin >= 0.0) || !isfinite(skin) || kmax < 0) return LC_ERR_INVALID_ARG;
+    drop_list_graphs(c);
+    if (c->d_nbr) { cudaFree(c->d_nbr); c->d_nbr = nullptr; }
+    c->skin = skin;
+    c->list_kmax_req = kmax;
+    c->list_kmax = 0;
+    c->list_valid = false;
+    if (c->d_list_stats) LC_TRY(cudaMemset(c->d_list_stats, 0, 5 * sizeof(unsigned long long)));
+    return LC_OK;
+}
+
+lc_status lc_list_info(lc_ctx *c, int64_t *builds, int64_t *long_rows, int64_t *longest_row, int64_t *rebuild_steps,
+                       int32_t *kmax, void *stream) {
+    if (!c) return LC_ERR_INVALID_ARG;
+    unsigned long long v[4] = {0, 0, 0, 0};
+    if (c->d_list_stats) {
+        cudaStream_t s = (cudaStream_t)stream;
+        LC_TRY(cudaMemcpyAsync(v, c->d_list_stats, sizeof(v), cudaMemcpyDeviceToHost, s));
+        LC_TRY(cudaStreamSynchronize(s));
+    }
+    if (builds) *builds = (int64_t)v[0];
+    if (long_rows) *long_rows = (int64_t)v[1];
+    if (longest_row) *longest_row = (int64_t)v[2];
+    if (rebuild_steps) *rebuild_steps = (int64_t)v[3];
+    if (kmax) *kmax = c->list_kmax;
+    return LC_OK;
+}
+
 lc_status lc_forces(lc_ctx *c, lc_schedule sched, void *stream) {
-    if (!c || sched < LC_SCHED_COLOUR || sched > LC_SCHED_BUFFER) return LC_ERR_INVALID_ARG;
+    if (!c || sched < LC_SCHED_COLOUR || sched > LC_SCHED_LIST) return LC_ERR_INVALID_ARG;
     if (c->nbox > 0 && sched == LC_SCHED_COLOUR) return LC_ERR_INVALID_ARG;
     if (!c->have_state) return LC_ERR_STATE;
     int launches = 0;
-    lc_status st = do_forces(c, sched, (cudaStream_t)stream, &launches);
+    lc_status st = sched == LC_SCHED_LIST ? list_forces(c, (cudaStream_t)stream, &launches)
+                                          : do_forces(c, sched, (cudaStream_t)stream, &launches);
     c->launches_force = launches;
     return st;
 }
@@ -536,10 +648,11 @@ static cudaError_t step_launches(lc_ctx *c, double dt, lc_schedule sched, cudaSt
 }
 
 lc_status lc_verlet_step(lc_ctx *c, double dt, int nsteps, lc_schedule sched, void *stream) {
-    if (!c || nsteps < 0 || !isfinite(dt) || sched < LC_SCHED_COLOUR || sched > LC_SCHED_BUFFER)
+    if (!c || nsteps < 0 || !isfinite(dt) || sched < LC_SCHED_COLOUR || sched > LC_SCHED_LIST)
         return LC_ERR_INVALID_ARG;
     if (c->nbox > 0 && sched == LC_SCHED_COLOUR) return LC_ERR_INVALID_ARG;
     if (!c->have_state) return LC_ERR_STATE;
+    if (sched == LC_SCHED_LIST) return list_verlet(c, dt, nsteps, (cudaStream_t)stream);
     cudaStream_t s = (cudaStream_t)stream;
     int launches = 0;
     if (!c->forces_valid) {

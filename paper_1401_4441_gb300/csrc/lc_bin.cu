@@ -238,33 +238,7 @@ __global__ void k_rank_gather(Grid g1, const BoxDev *__restrict__ boxes, const u
         out.x[dst] = X[0]; out.y[dst] = X[1]; out.z[dst] = X[2];
         out.vx[dst] = V[0]; out.vy[dst] = V[1]; out.vz[dst] = V[2];
         out.id[dst] = my_id;
-        if (write_p4) {
-            // FP32 offset from the cell centre (c + 1/2) h, formed in
-            // double-float arithmetic (TwoProduct / TwoSum) from the hi + lo
-            // split of x; the rounding residual of each offset (|r| <= 2^-23
-            // for |offset| < 4) is kept as a 10-bit signed fraction of 2^-23
-            // in the spare fourth word (offset + residual equals
-            // x - (c + 1/2) h to ~2e-10).
-            float hi[3];
-            unsigned w = 0;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const float cf = (float)cc[d] + 0.5f;
-                const float ph = cf * g.hf[d];
-                const float pl = fmaf(cf, g.hf[d], -ph) + cf * g.hl[d];
-                const float sum = sp[d].hi - ph;                 // TwoSum(hi, -ph)
-                const float bb = sum - sp[d].hi;
-                const float e2 = (sp[d].hi - (sum - bb)) + (-ph - bb);
-                const float rest = (sp[d].lo - pl) + e2;
-                const float tt = sum + rest;
-                const float res = rest - (tt - sum);
-                hi[d] = tt;
-                int q = __float2int_rn(res * kLoScale);
-                q = q > 511 ? 511 : (q < -511 ? -511 : q);
-                w |= (unsigned)(q + 512) << (10 * d);
-            }
-            p4[dst] = make_float4(hi[0], hi[1], hi[2], __uint_as_float(w));
-        }
+        if (write_p4) p4[dst] = cell_offset_p4(g, sp, cc);
     }
 }
 
@@ -325,6 +299,7 @@ cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches, int kicks, double 
     e = cudaGetLastError();
     if (e) return e;
     State t = c->cur; c->cur = c->nxt; c->nxt = t;
+    c->list_valid = false;   // the slot order changed
     return cudaSuccess;
 }
 

@@ -181,6 +181,21 @@ struct Ctx {
     cudaGraphExec_t graph[2 * kNumSched];
     double graph_dt[2 * kNumSched];
     double *state_a;       // cur.x of buffer set A (parity reference)
+    // Verlet neighbour lists (LC_SCHED_LIST): a coarser list grid with
+    // cells of side >= rc + skin, fixed-point offsets from the build cells'
+    // centres and one list row per particle, allocated on first use
+    double skin;
+    int list_kmax_req;     // row capacity requested (0: sized from the first build)
+    int list_kmax;         // row capacity of d_nbr
+    int list_shift;        // offsets are stored in units of 2^-list_shift
+    Grid gl;               // list grid; its cutoff fields are those of g
+    unsigned *d_nbr;       // [kmax][n]: slot << 6 | (o_x + 1) | (o_y + 1) << 2 | (o_z + 1) << 4
+    int *d_nn;             // [n] row lengths (a row longer than kmax is swept from the cells)
+    int4 *d_q4;            // [2n]: offsets now, then at the build; w = build cell
+    unsigned long long *d_list_stats;   // builds, long rows, longest row, rebuild steps; + 2 control words
+    bool list_valid;       // the lists match the current slot order and state
+    cudaGraphExec_t list_graph[4];      // (one / two steps) x (state-buffer parity)
+    double list_graph_dt[4];
 };
 
 // ---- kernels / launchers (stream-ordered, return cudaError_t) -------------
@@ -210,6 +225,12 @@ cudaError_t launch_unsort_vec(Ctx *c, const double *a, const double *b, const do
                               double *dst, cudaStream_t s, int wrap);
 cudaError_t launch_set_state(Ctx *c, const double *pos, const double *vel, cudaStream_t s);
 int force_grid_warps(const Ctx *c);
+// Verlet neighbour lists (lc_list.cu)
+bool make_list_grid(Ctx *c);   // false: fewer than 3 list cells in some dimension
+cudaError_t launch_list_build(Ctx *c, cudaStream_t s, bool write);
+cudaError_t launch_list_rebuild(Ctx *c, cudaStream_t s, bool copy_back, int *launches);
+cudaError_t launch_list_forces(Ctx *c, cudaStream_t s, bool stats, int *launches);
+cudaError_t capture_list_steps(Ctx *c, double dt, int nsteps, cudaGraphExec_t *out, int *launches);
 cudaError_t init_force_kernels();
 
 // scan kernels of the binning (lc_bin.cu), also launched by lc_noalloc.cu
@@ -298,6 +319,39 @@ __device__ __forceinline__ bool cell_coord_fast(const Split &s, float Lf_lo, flo
 
 __host__ __device__ __forceinline__ int colour_class(int c, int nc) {
     return ((nc & 1) && c == nc - 1) ? 2 : (c & 1);
+}
+
+// Offset x - (c + 1/2) h of one coordinate from the centre of its cell c,
+// as an unevaluated FP32 sum hi + lo, formed in double-float arithmetic
+// (TwoProduct / TwoSum) from the hi + lo split of the FP64 coordinate.
+__device__ __forceinline__ void cell_offset_df(const Grid &g, const Split &sp, int c, int d, float &hi, float &lo) {
+    const float cf = (float)c + 0.5f;
+    const float ph = cf * g.hf[d];
+    const float pl = fmaf(cf, g.hf[d], -ph) + cf * g.hl[d];
+    const float sum = sp.hi - ph;                    // TwoSum(hi, -ph)
+    const float bb = sum - sp.hi;
+    const float e2 = (sp.hi - (sum - bb)) + (-ph - bb);
+    const float rest = (sp.lo - pl) + e2;
+    hi = sum + rest;
+    lo = rest - (hi - sum);
+}
+
+// FP32 offset of a particle from the centre (c + 1/2) h of cell cc; the
+// rounding residual of each offset (|r| <= 2^-23 for |offset| < 4) is kept
+// as a 10-bit signed fraction of 2^-23 in the spare fourth word (offset +
+// residual equals x - (c + 1/2) h to ~2e-10).
+__device__ __forceinline__ float4 cell_offset_p4(const Grid &g, const Split (&sp)[3], const int (&cc)[3]) {
+    float hi[3];
+    unsigned w = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float res;
+        cell_offset_df(g, sp[d], cc[d], d, hi[d], res);
+        int q = __float2int_rn(res * kLoScale);
+        q = q > 511 ? 511 : (q < -511 ? -511 : q);
+        w |= (unsigned)(q + 512) << (10 * d);
+    }
+    return make_float4(hi[0], hi[1], hi[2], __uint_as_float(w));
 }
 
 }  // namespace lc

@@ -13,7 +13,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "liblc.so")
 
-SCHED = {"colour": 0, "atomic": 1, "fullshell": 2, "buffer": 3}
+SCHED = {"colour": 0, "atomic": 1, "fullshell": 2, "buffer": 3, "list": 4}
 PREC = {"fp64": 0, "mixed": 1}
 ORDER = {"cell": 0, "loopex": 1}
 DAG_WITHHOLD = 1
@@ -65,6 +65,8 @@ def _load():
         "lc_create_2d": ([dp, ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctx_pp], ctypes.c_int),
         "lc_stage_state": ([vp, vp, vp, ctypes.c_int32, vp], ctypes.c_int),
         "lc_set_state_staged": ([vp, ctypes.c_int32, vp], ctypes.c_int),
+        "lc_set_skin": ([vp, ctypes.c_double, ctypes.c_int32], ctypes.c_int),
+        "lc_list_info": ([vp, lp, lp, lp, lp, ip, vp], ctypes.c_int),
         "lc_destroy": ([vp], None),
         "lc_status_str": ([ctypes.c_int], ctypes.c_char_p),
     }
@@ -263,6 +265,21 @@ class Box:
             raise TypeError("trace must be a CUDA tensor")
         _check(self._lib.lc_dag_forces(self._h, ORDER[order], float(wait_seconds), DAG_WITHHOLD if withhold else 0,
                                        tp, _stream(stream)), "lc_dag_forces")
+
+    def set_skin(self, skin=0.3, kmax=0):
+        """Skin of the Verlet lists (schedule "list"); kmax = 0: row capacity
+        sized from the first build."""
+        _check(self._lib.lc_set_skin(self._h, float(skin), int(kmax)), "lc_set_skin")
+
+    def list_info(self, stream=None):
+        """dict of the list counters: builds, long_rows, longest_row,
+        rebuild_steps, kmax."""
+        v = [ctypes.c_int64() for _ in range(4)]
+        km = ctypes.c_int32()
+        _check(self._lib.lc_list_info(self._h, *(ctypes.byref(x) for x in v), ctypes.byref(km), _stream(stream)),
+               "lc_list_info")
+        return {"builds": v[0].value, "long_rows": v[1].value, "longest_row": v[2].value,
+                "rebuild_steps": v[3].value, "kmax": km.value}
 
     def set_tile(self, ni=0, warps=0):
         _check(self._lib.lc_set_tile(self._h, int(ni), int(warps)), "lc_set_tile")
