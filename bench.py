@@ -33,6 +33,8 @@ sys.path.insert(0, ROOT)
 from paper_1401_4441_gb300 import inputs  # noqa: E402
 
 METRIC = "LJ pair interactions/s (link-cell, Newton-3, velocity-Verlet steps)"
+# --schedule list: Verlet lists with a skin (an extension, not the paper's method)
+METRIC_LIST = "LJ pair interactions/s (Verlet lists with skin, velocity-Verlet steps)"
 UNIT = "pairs/s"
 DT = 0.005
 RC = 2.5
@@ -151,12 +153,14 @@ def half_shell_candidates(counts, nc, dims=3):
 
 def measured_traffic(workload, sched):
     """DRAM bytes (read + write) of one force evaluation from the committed ncu
-    summary profiles/k_force_<workload>.md, or None when the force kernel's
-    source changed since that capture (or there is none)."""
+    summary profiles/k_force_<workload>.md (k_list_force_<workload>.md for the
+    lists), or None when the kernel's source changed since that capture (or
+    there is none)."""
     import hashlib
     import re
-    src = os.path.join(ROOT, "paper_1401_4441_gb300", "csrc", "lc_force.cu")
-    path = os.path.join(ROOT, "profiles", f"k_force_{workload}.md")
+    kern, cu = ("k_list_force", "lc_list.cu") if sched == "list" else ("k_force", "lc_force.cu")
+    src = os.path.join(ROOT, "paper_1401_4441_gb300", "csrc", cu)
+    path = os.path.join(ROOT, "profiles", f"{kern}_{workload}.md")
     try:
         cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
         for line in open(path):
@@ -265,6 +269,8 @@ def run_profile(args, dist):
     g = lc.Box(w["box"], w["rc"], w["pos"].shape[0], args.precision, dims=w.get("dims", 3))
     g.set_state(torch.from_numpy(w["pos"]).cuda(), torch.from_numpy(w["vel"]).cuda())
     sched = "atomic" if args.schedule == "auto" else args.schedule
+    if sched == "list":
+        g.set_skin(args.skin)
     g.forces(sched)
     g.verlet(DT, args.warmup, sched)
     torch.cuda.synchronize()
@@ -354,7 +360,8 @@ def run_batch(args, dist):
     value_fp64 = pairs_fp64 / (t_fp64 * 1e-3)
     if dist.rank == 0:
         ns = [b["pos"].shape[0] for b in boxes]
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+        line = {"metric": METRIC_LIST if is_list else METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
+                "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
                 "data": "synthetic",
@@ -392,19 +399,25 @@ def run_gb300(args, dist):
     dvel = torch.from_numpy(vel).to(dev)
     g.set_state(dpos, dvel)
 
-    # schedule and tile shape: the autotuner's pick, unless fixed on the command line
-    from paper_1401_4441_gb300 import autotune
-    tuned = autotune.tune(g, use_cache=False)
-    sched_ms = {}
-    for row in tuned["table"]:
-        sched_ms[row["schedule"]] = min(sched_ms.get(row["schedule"], 1e30), row["ms"])
-    if args.schedule == "auto":
-        sched = tuned["schedule"]
+    is_list = args.schedule == "list"
+    if is_list:   # Verlet lists: no link-cell schedule or tile to choose
+        g.set_skin(args.skin)
+        sched, sched_ms, tile = "list", {}, None
     else:
-        sched = args.schedule
-        best = min((r for r in tuned["table"] if r["schedule"] == sched), key=lambda r: r["ms"])
-        g.set_tile(best["ni"], best["warps"])
-    tile = {"ni": tuned["ni"], "warps": tuned["warps"]} if args.schedule == "auto" else {"ni": best["ni"], "warps": best["warps"]}
+        # schedule and tile shape: the autotuner's pick, unless fixed on the command line
+        from paper_1401_4441_gb300 import autotune
+        tuned = autotune.tune(g, use_cache=False)
+        sched_ms = {}
+        for row in tuned["table"]:
+            sched_ms[row["schedule"]] = min(sched_ms.get(row["schedule"], 1e30), row["ms"])
+        if args.schedule == "auto":
+            sched = tuned["schedule"]
+        else:
+            sched = args.schedule
+            best = min((r for r in tuned["table"] if r["schedule"] == sched), key=lambda r: r["ms"])
+            g.set_tile(best["ni"], best["warps"])
+        tile = {"ni": tuned["ni"], "warps": tuned["warps"]} if args.schedule == "auto" else \
+            {"ni": best["ni"], "warps": best["warps"]}
 
     g.set_state(dpos, dvel)
     g.forces(sched)
@@ -444,20 +457,29 @@ def run_gb300(args, dist):
     elapsed_ms = sum(a.elapsed_time(b) for a, b in evs)
     _, _, _, npairs1 = g.energy()
     per_force, per_step = g.launch_counts()
+    list_stats = g.list_info() if is_list else None
     elapsed_ms = dist.max(elapsed_ms)
     pairs = 0.5 * (npairs0 + npairs1) * args.steps
     total_pairs = dist.sum(pairs)
     value = total_pairs / (elapsed_ms * 1e-3)
 
-    # dominant kernel: the force sweep of one evaluation (binned state, L2 flushed)
+    # dominant kernel: the force sweep of one evaluation (binned state or
+    # valid lists, L2 flushed)
     if forces_only:
         g.set_state(dpos, dvel)
         g.forces(sched)
-    counts = g.get("cell_count")
-    nc, _, _ = g.grid()
-    cand = half_shell_candidates(counts, nc, w.get("dims", 3))
     _, _, _, npairs_now = g.energy()
-    flops = 8.0 * cand + 21.0 * npairs_now
+    if is_list:
+        # per list entry the distance test (8 flop), per pair twice the
+        # one-sided pair term (21 flop less the 3 of the partner's update)
+        info = g.list_info()
+        cand = info["entries"] / max(1, info["builds"])
+        flops = 8.0 * cand + 2 * 18.0 * npairs_now
+    else:
+        counts = g.get("cell_count")
+        nc, _, _ = g.grid()
+        cand = half_shell_candidates(counts, nc, w.get("dims", 3))
+        flops = 8.0 * cand + 21.0 * npairs_now
     fts = []
     for _ in range(5):
         flush.zero_()
@@ -473,7 +495,8 @@ def run_gb300(args, dist):
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_clock * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": measured_traffic(args.workload, sched),
-                "kernel": f"k_force ({sched}, {args.precision}): one force evaluation",
+                "kernel": "k_list_force (mixed): one force evaluation from the lists" if is_list else
+                          f"k_force ({sched}, {args.precision}): one force evaluation",
                 "flops_per_eval": flops, "candidates": cand, "pairs": npairs_now,
                 "eval_ms": t_force * 1e3,
                 "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"}
@@ -526,7 +549,8 @@ def run_gb300(args, dist):
 
     if dist.rank == 0:
         cpu = cpu_baseline(pos, oracle_box(w), rc) if (dist.world == 1 and not args.no_cpu_baseline) else None
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+        line = {"metric": METRIC_LIST if is_list else METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
+                "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
                 "data": "synthetic", "config": workload_config(args, w),
@@ -534,6 +558,12 @@ def run_gb300(args, dist):
                 "schedule": sched, "schedule_force_ms": sched_ms, "tile": tile,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": per_step * args.steps}
+        if is_list:
+            line["list"] = {"skin": args.skin, "builds": list_stats["builds"],
+                            "rebuild_steps": list_stats["rebuild_steps"], "kmax": list_stats["kmax"],
+                            "entries_per_build": cand,
+                            "note": "not the paper's method; rebuilds are decided on the device and not "
+                                    "counted in gpu_launches"}
         print(json.dumps(line), flush=True)
 
 
@@ -594,7 +624,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--schedule", default="auto", choices=["auto", "colour", "atomic", "fullshell", "buffer"])
+    ap.add_argument("--schedule", default="auto", choices=["auto", "colour", "atomic", "fullshell", "buffer", "list"],
+                    help="list: Verlet lists with a skin (not the paper's method; auxiliary line)")
+    ap.add_argument("--skin", type=float, default=0.4, help="skin of --schedule list")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--workload", default="liquid1m", choices=sorted(inputs.WORKLOADS) + ["batch512"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

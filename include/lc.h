@@ -158,9 +158,10 @@ lc_status lc_bin(lc_ctx *ctx, void *stream);
  * the virial and the number of pairs inside r_c.  LC_ERR_OOM if the buffers
  * of LC_SCHED_BUFFER or the lists of LC_SCHED_LIST cannot be allocated;
  * LC_ERR_INVALID_ARG for LC_SCHED_COLOUR on a batch of boxes, and for
- * LC_SCHED_LIST on a batch or an FP64 context.  LC_SCHED_LIST bins on the
- * list grid and builds the lists first (the first build also sizes them,
- * which synchronises the stream). */
+ * LC_SCHED_LIST on a batch or an FP64 context.  LC_SCHED_LIST evaluates
+ * from the lists, which it first builds (binning on the list grid) when they
+ * are stale -- after lc_set_state, lc_set_skin or any link-cell binning;
+ * the first build also sizes them, which synchronises the stream. */
 lc_status lc_forces(lc_ctx *ctx, lc_schedule sched, void *stream);
 
 /* nsteps velocity-Verlet steps of size dt (m = 1): v += dt/2 F; x += dt v;
@@ -178,15 +179,17 @@ lc_status lc_verlet_step(lc_ctx *ctx, double dt, int nsteps, lc_schedule sched, 
  * A list build bins the particles on a list grid of cells of side >= rc + skin
  * and records for every particle all partners within rc + skin (both
  * directions).  While no particle has moved by skin / 2 since the build,
- * every pair inside rc is on the lists.  lc_forces(LC_SCHED_LIST) builds
- * and evaluates; lc_verlet_step(LC_SCHED_LIST) reuses the lists and rebuilds
+ * every pair inside rc is on the lists.  lc_forces(LC_SCHED_LIST) evaluates
+ * from the lists (built when stale); lc_verlet_step(LC_SCHED_LIST) reuses them
+ * and rebuilds
  * when a particle's displacement since the build exceeds skin / 2, a
  * decision taken on the device inside the step's CUDA graph (a conditional
  * node), so the host never waits.  Positions stay unwrapped between builds
- * (lc_get wraps them).  The binning of the other schedules is stale after
- * list calls (LC_GET_CELL_* return LC_ERR_STATE until the next lc_bin).
+ * (lc_get wraps them).  The link-cell binning is stale after list calls
+ * (LC_GET_CELL_COUNT, LC_GET_CELL_START and LC_GET_PERM return LC_ERR_STATE
+ * until the next lc_bin).
  *
- * lc_set_skin: skin >= 0 (default 0.3); kmax = entries per particle kept in
+ * lc_set_skin: skin >= 0 (default 0.4); kmax = entries per particle kept in
  * the list (0: sized from the first build, 1.25 x the longest row + 8).
  * A row longer than kmax is still exact: its partners are swept from the
  * cells.  Frees the current lists (allocated again on next use: 4 kmax + 36
@@ -197,10 +200,11 @@ lc_status lc_set_skin(lc_ctx *ctx, double skin, int32_t kmax);
 
 /* Counters of the lists since the last lc_set_skin: builds, rows longer
  * than kmax over all builds, the longest row seen, steps whose displacement
- * check asked for a rebuild, and the row capacity kmax.  Any output may be
- * NULL.  Synchronises the stream. */
+ * check asked for a rebuild, list entries written over all builds (each
+ * pair within rc + skin appears in two rows), and the row capacity kmax.
+ * Any output may be NULL.  Synchronises the stream. */
 lc_status lc_list_info(lc_ctx *ctx, int64_t *builds, int64_t *long_rows, int64_t *longest_row,
-                       int64_t *rebuild_steps, int32_t *kmax, void *stream);
+                       int64_t *rebuild_steps, int64_t *entries, int32_t *kmax, void *stream);
 
 /* Energies of the current state, FP64: potential U and virial W of the last
  * force evaluation, kinetic K = 1/2 sum v^2 of the current velocities, and the

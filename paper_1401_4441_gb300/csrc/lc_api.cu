@@ -262,7 +262,7 @@ static lc_status create_single(const double box[3], double rc, int64_t n, lc_pre
     lc_ctx *c = new lc_ctx();
     memset(static_cast<Ctx *>(c), 0, sizeof(Ctx));
     make_grid(&c->g, box, rc, dims);
-    c->skin = 0.3;
+    c->skin = 0.4;
     c->n = n;
     c->prec = prec;
     c->ni = 16;
@@ -528,8 +528,8 @@ static lc_status ensure_list(lc_ctx *c, cudaStream_t s) {
     if (!c->d_nn) LC_TRY(dalloc(&c->d_nn, N));
     if (!c->d_q4) LC_TRY(dalloc(&c->d_q4, 2 * N));
     if (!c->d_list_stats) {
-        LC_TRY(dalloc(&c->d_list_stats, 5));   // 4 counters + 2 control words
-        LC_TRY(cudaMemsetAsync(c->d_list_stats, 0, 5 * sizeof(unsigned long long), s));
+        LC_TRY(dalloc(&c->d_list_stats, 6));   // 5 counters + 2 control words
+        LC_TRY(cudaMemsetAsync(c->d_list_stats, 0, 6 * sizeof(unsigned long long), s));
     }
     int64_t kmax = c->list_kmax_req;
     if (kmax == 0) {
@@ -553,10 +553,15 @@ static lc_status ensure_list(lc_ctx *c, cudaStream_t s) {
     return LC_OK;
 }
 
+// Forces from the lists, built first when they are stale (new state, or a
+// link-cell binning re-sorted the particles); lists kept valid by list
+// steps are used as they are.
 static lc_status list_forces(lc_ctx *c, cudaStream_t s, int *launches) {
     if (c->prec != LC_PREC_MIXED || c->nbox > 0) return LC_ERR_INVALID_ARG;
-    LC_TRY_ST(ensure_list(c, s));
-    LC_TRY(launch_list_rebuild(c, s, false, launches));
+    if (!c->list_valid || !c->d_nbr) {
+        LC_TRY_ST(ensure_list(c, s));
+        LC_TRY(launch_list_rebuild(c, s, false, launches));
+    }
     LC_TRY(launch_list_forces(c, s, true, launches));
     c->binned = false;   // the cells are the list grid's
     c->forces_valid = true;
@@ -597,14 +602,14 @@ lc_status lc_set_skin(lc_ctx *c, double skin, int32_t kmax) {
     c->list_kmax_req = kmax;
     c->list_kmax = 0;
     c->list_valid = false;
-    if (c->d_list_stats) LC_TRY(cudaMemset(c->d_list_stats, 0, 5 * sizeof(unsigned long long)));
+    if (c->d_list_stats) LC_TRY(cudaMemset(c->d_list_stats, 0, 6 * sizeof(unsigned long long)));
     return LC_OK;
 }
 
 lc_status lc_list_info(lc_ctx *c, int64_t *builds, int64_t *long_rows, int64_t *longest_row, int64_t *rebuild_steps,
-                       int32_t *kmax, void *stream) {
+                       int64_t *entries, int32_t *kmax, void *stream) {
     if (!c) return LC_ERR_INVALID_ARG;
-    unsigned long long v[4] = {0, 0, 0, 0};
+    unsigned long long v[5] = {0, 0, 0, 0, 0};
     if (c->d_list_stats) {
         cudaStream_t s = (cudaStream_t)stream;
         LC_TRY(cudaMemcpyAsync(v, c->d_list_stats, sizeof(v), cudaMemcpyDeviceToHost, s));
@@ -614,6 +619,7 @@ lc_status lc_list_info(lc_ctx *c, int64_t *builds, int64_t *long_rows, int64_t *
     if (long_rows) *long_rows = (int64_t)v[1];
     if (longest_row) *longest_row = (int64_t)v[2];
     if (rebuild_steps) *rebuild_steps = (int64_t)v[3];
+    if (entries) *entries = (int64_t)v[4];
     if (kmax) *kmax = c->list_kmax;
     return LC_OK;
 }

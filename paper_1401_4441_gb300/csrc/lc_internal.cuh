@@ -192,7 +192,7 @@ struct Ctx {
     unsigned *d_nbr;       // [kmax][n]: slot << 6 | (o_x + 1) | (o_y + 1) << 2 | (o_z + 1) << 4
     int *d_nn;             // [n] row lengths (a row longer than kmax is swept from the cells)
     int4 *d_q4;            // [2n]: offsets now, then at the build; w = build cell
-    unsigned long long *d_list_stats;   // builds, long rows, longest row, rebuild steps; + 2 control words
+    unsigned long long *d_list_stats;   // builds, long rows, longest row, rebuild steps, entries; + 2 control words
     bool list_valid;       // the lists match the current slot order and state
     cudaGraphExec_t list_graph[4];      // (one / two steps) x (state-buffer parity)
     double list_graph_dt[4];

@@ -32,8 +32,8 @@
 
 namespace lc {
 
-constexpr int kLBWarps = 8;     // warps per block of the build
-constexpr int kLBCap = 512;     // candidate slots listed per batch (per warp)
+constexpr int kLBWarps = 4;     // warps per block of the build
+constexpr int kLBCap = 1024;    // candidates listed per batch (per warp)
 constexpr int kListThreads = 256;
 constexpr int kPF = 4;          // list entries in flight per thread (force kernel)
 
@@ -55,7 +55,7 @@ struct ListArgs {
     double *fx, *fy, *fz;
     double *warp_acc;
     long long *warp_pairs;
-    unsigned long long *stats;  // builds, long rows, longest row, rebuild steps
+    unsigned long long *stats;  // builds, long rows, longest row, rebuild steps, entries
     unsigned *ctl;              // rebuild flag, block ticket
     int *err;
 };
@@ -76,12 +76,23 @@ __device__ __forceinline__ int image_of(int c, int o, int nc) {
 }
 
 // ------------------------------------------------------------- build -----
-struct BuildSmem {
-    float4 ip[32];              // centre particles of the chunk (FP32 offsets)
-    float4 nb_sh[27];           // o * h (FP32) of each neighbour entry
+// One warp per list cell and chunk of up to 32 of its particles, in two
+// phases per batch of candidates (the particles of the 27 surrounding cells,
+// in table order):
+//   test  lane = candidate: FP32 distance to every chunk particle, two per
+//         packed f32x2 operation; the ballot of each (round, particle) goes
+//         to shared memory
+//   emit  lane = chunk particle: walks its bits in candidate order and
+//         appends the entries; the t-th append of every lane writes row t,
+//         so the stores of a warp are contiguous
+struct alignas(16) BuildSmem {
+    unsigned mask[kLBCap / 32][32];    // [round][chunk particle]: candidates within rc + skin
+    float ipx[32], ipy[32], ipz[32];   // chunk particles (FP32 offsets); far past the chunk
+    unsigned jl[kLBCap];               // candidate entries: slot << 6 | cell-shift code
     int nb_start[27], nb_count[27], nb_code[27];
-    int jl[kLBCap];             // candidates: slot | entry << 26
 };
+
+__device__ __forceinline__ float2 lds2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
 
 template <bool WRITE>
 __global__ void __launch_bounds__(kLBWarps * 32) k_list_build(ListArgs a) {
@@ -91,8 +102,8 @@ __global__ void __launch_bounds__(kLBWarps * 32) k_list_build(ListArgs a) {
     const int W = gridDim.x * kLBWarps;
     const Grid &g = a.g;
     const int nf = g.dims == 2 ? 9 : 27;
-    const unsigned below = (1u << lane) - 1u;
     int my_max = 0, my_long = 0;
+    long long my_entries = 0;
     for (int A = blockIdx.x * kLBWarps + wib; A < g.ncell; A += W) {
         const int a0 = a.start[A], na = a.count[A];
         if (na == 0) continue;
@@ -111,73 +122,74 @@ __global__ void __launch_bounds__(kLBWarps * 32) k_list_build(ListArgs a) {
             sm.nb_start[lane] = a.start[B];
             sm.nb_count[lane] = a.count[B];
             sm.nb_code[lane] = (o[0] + 1) | ((o[1] + 1) << 2) | ((o[2] + 1) << 4);
-            sm.nb_sh[lane] = make_float4((float)o[0] * g.hf[0], (float)o[1] * g.hf[1], (float)o[2] * g.hf[2], 0.f);
         }
         __syncwarp();
         for (int i0 = 0; i0 < na; i0 += 32) {
             const int ni = min(32, na - i0);
             const int si = a0 + i0 + lane;
-            if (lane < ni) sm.ip[lane] = a.p4[si];
-            int rows[32];   // row lengths of the chunk's particles (uniform)
-#pragma unroll
-            for (int ii = 0; ii < 32; ++ii) rows[ii] = 0;
+            float4 pi = make_float4(1.0e30f, 1.0e30f, 1.0e30f, 0.f);
+            if (lane < ni) pi = a.p4[si];
+            sm.ipx[lane] = pi.x; sm.ipy[lane] = pi.y; sm.ipz[lane] = pi.z;
+            const int nii = (ni + 1) & ~1;   // chunk particles tested, in pairs
+            int cnt = 0;                     // this lane's row length
             __syncwarp();
             int b = 0, kin = 0;
             while (b < nf) {
                 int nj = 0;   // next batch of candidates, in table order
                 while (b < nf && nj < kLBCap) {
                     const int take = min(sm.nb_count[b] - kin, kLBCap - nj);
-                    const int st = sm.nb_start[b] + kin;
-                    for (int k = lane; k < take; k += 32) sm.jl[nj + k] = (st + k) | (b << 26);
+                    const unsigned st = (unsigned)(sm.nb_start[b] + kin), code = (unsigned)sm.nb_code[b];
+                    for (int k = lane; k < take; k += 32) sm.jl[nj + k] = ((st + k) << 6) | code;
                     nj += take;
                     kin += take;
                     if (kin >= sm.nb_count[b]) { ++b; kin = 0; }
                 }
                 __syncwarp();
-                for (int jc = 0; jc < nj; jc += 32) {
-                    const int e = jc + lane;
+                const int nr = (nj + 31) >> 5;
+                for (int r = 0; r < nr; ++r) {   // test
+                    const int e = r * 32 + lane;
                     const bool valid = e < nj;
                     int sj = -1;
-                    unsigned code = 0;
-                    float px = 1.0e30f, py = 1.0e30f, pz = 1.0e30f;
+                    float2 px = make_float2(1.0e30f, 1.0e30f), py = px, pz = px;
                     if (valid) {
-                        const int wj = sm.jl[e];
-                        sj = wj & ((1 << 26) - 1);
-                        const int bi = wj >> 26;
+                        const unsigned w = sm.jl[e];
+                        sj = (int)(w >> 6);
                         const float4 q = a.p4[sj];
-                        const float4 sh = sm.nb_sh[bi];
-                        px = q.x + sh.x; py = q.y + sh.y; pz = q.z + sh.z;
-                        code = (unsigned)sm.nb_code[bi];
+                        const float x = q.x + (float)((int)(w & 3u) - 1) * g.hf[0];
+                        const float y = q.y + (float)((int)((w >> 2) & 3u) - 1) * g.hf[1];
+                        const float z = q.z + (float)((int)((w >> 4) & 3u) - 1) * g.hf[2];
+                        px = make_float2(-x, -x); py = make_float2(-y, -y); pz = make_float2(-z, -z);
                     }
-                    const unsigned entry = ((unsigned)sj << 6) | code;
-                    // every centre particle against the lane's candidate; the
-                    // row lengths are warp-uniform registers, so an append
-                    // needs only the ballot (no shuffle on the path)
-#pragma unroll
-                    for (int ii = 0; ii < 32; ++ii) {
-                        if (ii < ni) {
-                            const float4 P = sm.ip[ii];
-                            const float dx = P.x - px, dy = P.y - py, dz = P.z - pz;
-                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            const bool hit = valid && r2 < a.rl2 && sj != a0 + i0 + ii;
-                            const unsigned m = __ballot_sync(kFull, hit);
-                            if (WRITE && hit) {
-                                const int pos = rows[ii] + __popc(m & below);
-                                if (pos < a.kmax) a.nbr[(size_t)pos * (size_t)a.n + (size_t)(a0 + i0 + ii)] = entry;
-                            }
-                            rows[ii] += __popc(m);
-                        }
+                    const int self = sj - (a0 + i0);   // chunk index of the candidate itself, if it is one
+                    for (int ii = 0; ii < nii; ii += 2) {
+                        const float2 dx = __fadd2_rn(lds2(&sm.ipx[ii]), px);
+                        const float2 dy = __fadd2_rn(lds2(&sm.ipy[ii]), py);
+                        const float2 dz = __fadd2_rn(lds2(&sm.ipz[ii]), pz);
+                        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+                        const unsigned m0 = __ballot_sync(kFull, r2.x < a.rl2 && self != ii);
+                        const unsigned m1 = __ballot_sync(kFull, r2.y < a.rl2 && self != ii + 1);
+                        if (lane == 0) *reinterpret_cast<uint2 *>(&sm.mask[r][ii]) = make_uint2(m0, m1);
+                    }
+                }
+                __syncwarp();
+                if (lane < ni) {   // emit: this lane's bits, round by round
+                    int r = 0;
+                    unsigned m = sm.mask[0][lane];
+                    for (;;) {
+                        while (m == 0u && ++r < nr) m = sm.mask[r][lane];
+                        if (m == 0u) break;
+                        const int bit = __ffs(m) - 1;
+                        m &= m - 1u;
+                        if (WRITE && cnt < a.kmax) a.nbr[(size_t)cnt * (size_t)a.n + (size_t)si] = sm.jl[r * 32 + bit];
+                        ++cnt;
                     }
                 }
                 __syncwarp();
             }
-            int cnt = 0;   // this lane's row length
-#pragma unroll
-            for (int ii = 0; ii < 32; ++ii) cnt = lane == ii ? rows[ii] : cnt;
             if (lane < ni) {
                 a.nn[si] = cnt;
                 if (WRITE) {
-                    const float4 p = sm.ip[lane];
+                    const float4 p = pi;
                     const unsigned wr = __float_as_uint(p.w);
                     int4 q;
                     q.x = quantize(p.x, lo_residual(wr, 0), a.scale);
@@ -189,6 +201,7 @@ __global__ void __launch_bounds__(kLBWarps * 32) k_list_build(ListArgs a) {
                 }
                 my_max = max(my_max, cnt);
                 my_long += cnt > a.kmax ? 1 : 0;
+                my_entries += cnt;
             }
             __syncwarp();
         }
@@ -197,10 +210,12 @@ __global__ void __launch_bounds__(kLBWarps * 32) k_list_build(ListArgs a) {
     for (int m = 16; m >= 1; m >>= 1) {
         my_max = max(my_max, __shfl_xor_sync(kFull, my_max, m));
         my_long += __shfl_xor_sync(kFull, my_long, m);
+        my_entries += __shfl_xor_sync(kFull, my_entries, m);
     }
     if (lane == 0) {
         atomicMax(a.stats + 2, (unsigned long long)my_max);
         if (WRITE && my_long) atomicAdd(a.stats + 1, (unsigned long long)my_long);
+        if (WRITE && my_entries) atomicAdd(a.stats + 4, (unsigned long long)my_entries);
     }
     if (WRITE && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.stats + 0, 1ull);
 }
@@ -224,49 +239,66 @@ __device__ __forceinline__ bool exact_inside_list(const ListArgs &a, int i, int 
     return r2 < a.g.rc2;
 }
 
-// One list entry of particle i: displacement in exact integer arithmetic
-// (offsets and cell side in units of 2^-k; modular, the result fits), one
-// rounding to FP32, then the pair term, masked rather than branched on (the
-// FP64 decision in the band around rc is the only branch, and it is rare).
-// pih = offset of i + h; live = false: a padding slot, no contribution.
+// Two list entries of particle i, one per half of the packed f32x2
+// operations: displacement in exact integer arithmetic (offsets in units of
+// 2^-k, the entry's cell shift from the block's table; modular, the result
+// fits), one rounding to FP32, then the pair terms, masked rather than
+// branched on (the FP64 decision in the band around rc is the only branch,
+// and it is rare).  live = false: a padding slot, no contribution.
 template <bool STATS>
-__device__ __forceinline__ void list_pair(const ListArgs &a, int i, int celli, const unsigned (&pih)[3], unsigned w,
-                                          const int4 &qj, bool live, float &fx, float &fy, float &fz, float &e6,
-                                          float &e12, int &np) {
-    const float dx = (float)(int)(pih[0] - (unsigned)qj.x - (w & 3u) * (unsigned)a.hq[0]);
-    const float dy = (float)(int)(pih[1] - (unsigned)qj.y - ((w >> 2) & 3u) * (unsigned)a.hq[1]);
-    const float dz = (float)(int)(pih[2] - (unsigned)qj.z - ((w >> 4) & 3u) * (unsigned)a.hq[2]);
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));   // units of 2^-2k
-    bool take = live && r2 < a.rc2s_lo;
-    if (live && r2 < a.rc2s_hi && !take) take = exact_inside_list(a, i, (int)(w >> 6), celli, w);
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r2));
-    y = fmaf(y, fmaf(-r2, y, 1.0f), y);   // Newton step
-    const float inv = take ? y * a.scale2 : 0.0f;   // r^-2, or 0 for no pair
-    const float s6 = inv * inv * inv;
-    const float f = (s6 * inv) * fmaf(48.0f, s6, -24.0f) * a.inv_scale;
-    fx = fmaf(f, dx, fx);
-    fy = fmaf(f, dy, fy);
-    fz = fmaf(f, dz, fz);
+__device__ __forceinline__ void list_pair2(const ListArgs &a, const int4 *shift, int i, const int4 &qi, unsigned w0,
+                                           const int4 &q0, bool live0, unsigned w1, const int4 &q1, bool live1,
+                                           float2 &fx, float2 &fy, float2 &fz, float2 &e6, float2 &e12, int &np) {
+    const int4 s0 = shift[w0 & 63u], s1 = shift[w1 & 63u];
+    const float2 dx = make_float2((float)(int)((unsigned)qi.x - (unsigned)q0.x - (unsigned)s0.x),
+                                  (float)(int)((unsigned)qi.x - (unsigned)q1.x - (unsigned)s1.x));
+    const float2 dy = make_float2((float)(int)((unsigned)qi.y - (unsigned)q0.y - (unsigned)s0.y),
+                                  (float)(int)((unsigned)qi.y - (unsigned)q1.y - (unsigned)s1.y));
+    const float2 dz = make_float2((float)(int)((unsigned)qi.z - (unsigned)q0.z - (unsigned)s0.z),
+                                  (float)(int)((unsigned)qi.z - (unsigned)q1.z - (unsigned)s1.z));
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));   // units of 2^-2k
+    bool t0 = live0 && r2.x < a.rc2s_lo, t1 = live1 && r2.y < a.rc2s_lo;
+    if (live0 && r2.x < a.rc2s_hi && !t0) t0 = exact_inside_list(a, i, (int)(w0 >> 6), qi.w, w0);
+    if (live1 && r2.y < a.rc2s_hi && !t1) t1 = exact_inside_list(a, i, (int)(w1 >> 6), qi.w, w1);
+    float2 y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y.x) : "f"(r2.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y.y) : "f"(r2.y));
+    const float2 e = __ffma2_rn(make_float2(-r2.x, -r2.y), y, make_float2(1.0f, 1.0f));   // Newton step
+    y = __ffma2_rn(y, e, y);
+    float2 inv = __fmul2_rn(y, make_float2(a.scale2, a.scale2));   // r^-2
+    inv.x = t0 ? inv.x : 0.0f;
+    inv.y = t1 ? inv.y : 0.0f;
+    const float2 s6 = __fmul2_rn(__fmul2_rn(inv, inv), inv);
+    const float2 g = __ffma2_rn(s6, make_float2(48.0f, 48.0f), make_float2(-24.0f, -24.0f));
+    const float2 f = __fmul2_rn(__fmul2_rn(s6, inv), __fmul2_rn(g, make_float2(a.inv_scale, a.inv_scale)));
+    fx = __ffma2_rn(f, dx, fx);
+    fy = __ffma2_rn(f, dy, fy);
+    fz = __ffma2_rn(f, dz, fz);
     if (STATS) {
-        e6 += s6;
-        e12 = fmaf(s6, s6, e12);
-        np += take ? 1 : 0;
+        e6 = __fadd2_rn(e6, s6);
+        e12 = __ffma2_rn(s6, s6, e12);
+        np += (t0 ? 1 : 0) + (t1 ? 1 : 0);
     }
 }
 
 template <bool STATS>
 __global__ void __launch_bounds__(kListThreads) k_list_force(ListArgs a) {
+    // cell shift of every entry code (o_d + 1 in two bits per axis), in
+    // units of 2^-k
+    __shared__ int4 shift[64];
+    if (threadIdx.x < 64) {
+        const int c = threadIdx.x;
+        shift[c] = make_int4(((c & 3) - 1) * a.hq[0], (((c >> 2) & 3) - 1) * a.hq[1], (((c >> 4) & 3) - 1) * a.hq[2], 0);
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
-    float e6 = 0.f, e12 = 0.f;
+    float2 e6 = make_float2(0.f, 0.f), e12 = make_float2(0.f, 0.f);
     int np = 0;
     const size_t n = (size_t)a.n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
         const int4 qi = a.q4[i];
         const int cnt = a.nn[i];
-        const unsigned pih[3] = {(unsigned)qi.x + (unsigned)a.hq[0], (unsigned)qi.y + (unsigned)a.hq[1],
-                                 (unsigned)qi.z + (unsigned)a.hq[2]};
-        float fx = 0.f, fy = 0.f, fz = 0.f;
+        float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx;
         if (cnt <= a.kmax) {
             // software pipeline: the next kPF entries load while the
             // current ones' partner offsets load and are used
@@ -283,8 +315,9 @@ __global__ void __launch_bounds__(kListThreads) k_list_force(ListArgs a) {
                 for (int j = 0; j < kPF; ++j)
                     wn[j] = k + kPF + j < cnt ? __ldcs(row + (size_t)(k + kPF + j) * n) : 0u;
 #pragma unroll
-                for (int j = 0; j < kPF; ++j)
-                    list_pair<STATS>(a, i, qi.w, pih, w[j], q[j], k + j < cnt, fx, fy, fz, e6, e12, np);
+                for (int j = 0; j < kPF; j += 2)
+                    list_pair2<STATS>(a, shift, i, qi, w[j], q[j], k + j < cnt, w[j + 1], q[j + 1], k + j + 1 < cnt,
+                                      fx, fy, fz, e6, e12, np);
 #pragma unroll
                 for (int j = 0; j < kPF; ++j) w[j] = wn[j];
             }
@@ -307,20 +340,21 @@ __global__ void __launch_bounds__(kListThreads) k_list_force(ListArgs a) {
                 const int B = c[0] + a.g.nc[0] * (c[1] + a.g.nc[1] * c[2]);
                 const unsigned code = (unsigned)((o[0] + 1) | ((o[1] + 1) << 2) | ((o[2] + 1) << 4));
                 const int b0 = a.start[B], b1 = b0 + a.count[B];
-                for (int j = b0; j < b1; ++j)
-                    if (j != i)
-                        list_pair<STATS>(a, i, qi.w, pih, ((unsigned)j << 6) | code, a.q4[j], true, fx, fy, fz, e6,
-                                         e12, np);
+                for (int j = b0; j < b1; ++j) {
+                    const unsigned wj = ((unsigned)j << 6) | code;
+                    list_pair2<STATS>(a, shift, i, qi, wj, a.q4[j], j != i, wj, qi, false, fx, fy, fz, e6, e12, np);
+                }
             }
         }
-        a.fx[i] = f32_to_f64_bits(fx);
-        a.fy[i] = f32_to_f64_bits(fy);
-        a.fz[i] = f32_to_f64_bits(fz);
+        a.fx[i] = f32_to_f64_bits(fx.x + fx.y);
+        a.fy[i] = f32_to_f64_bits(fy.x + fy.y);
+        a.fz[i] = f32_to_f64_bits(fz.x + fz.y);
     }
     if (STATS) {   // block partials in FP64, fixed order: one slot per block
         __shared__ double r6[kListThreads / 32], r12[kListThreads / 32];
         __shared__ long long rp[kListThreads / 32];
-        double s6 = f32_to_f64_bits(e6), s12 = f32_to_f64_bits(e12);
+        double s6 = f32_to_f64_bits(e6.x) + f32_to_f64_bits(e6.y);
+        double s12 = f32_to_f64_bits(e12.x) + f32_to_f64_bits(e12.y);
         long long p = np;
 #pragma unroll
         for (int m = 16; m >= 1; m >>= 1) {
@@ -468,7 +502,7 @@ static ListArgs list_args(const Ctx *c) {
     a.warp_acc = c->d_warp_acc;
     a.warp_pairs = c->d_warp_pairs;
     a.stats = c->d_list_stats;
-    a.ctl = reinterpret_cast<unsigned *>(c->d_list_stats + 4);
+    a.ctl = reinterpret_cast<unsigned *>(c->d_list_stats + 5);
     a.err = c->d_err;
     return a;
 }
@@ -485,7 +519,7 @@ cudaError_t launch_list_build(Ctx *c, cudaStream_t s, bool write) {
     if (c->n == 0) return cudaSuccess;
     ListArgs a = list_args(c);
     int blocks = (c->gl.ncell + kLBWarps - 1) / kLBWarps;
-    if (blocks > c->num_sms * 4) blocks = c->num_sms * 4;
+    if (blocks > c->num_sms * 6) blocks = c->num_sms * 6;   // six resident per SM (shared memory)
     if (write) k_list_build<true><<<blocks, kLBWarps * 32, 0, s>>>(a);
     else k_list_build<false><<<blocks, kLBWarps * 32, 0, s>>>(a);
     return cudaGetLastError();

@@ -66,7 +66,7 @@ def _load():
         "lc_stage_state": ([vp, vp, vp, ctypes.c_int32, vp], ctypes.c_int),
         "lc_set_state_staged": ([vp, ctypes.c_int32, vp], ctypes.c_int),
         "lc_set_skin": ([vp, ctypes.c_double, ctypes.c_int32], ctypes.c_int),
-        "lc_list_info": ([vp, lp, lp, lp, lp, ip, vp], ctypes.c_int),
+        "lc_list_info": ([vp, lp, lp, lp, lp, lp, ip, vp], ctypes.c_int),
         "lc_destroy": ([vp], None),
         "lc_status_str": ([ctypes.c_int], ctypes.c_char_p),
     }
@@ -266,20 +266,20 @@ class Box:
         _check(self._lib.lc_dag_forces(self._h, ORDER[order], float(wait_seconds), DAG_WITHHOLD if withhold else 0,
                                        tp, _stream(stream)), "lc_dag_forces")
 
-    def set_skin(self, skin=0.3, kmax=0):
+    def set_skin(self, skin=0.4, kmax=0):
         """Skin of the Verlet lists (schedule "list"); kmax = 0: row capacity
         sized from the first build."""
         _check(self._lib.lc_set_skin(self._h, float(skin), int(kmax)), "lc_set_skin")
 
     def list_info(self, stream=None):
         """dict of the list counters: builds, long_rows, longest_row,
-        rebuild_steps, kmax."""
-        v = [ctypes.c_int64() for _ in range(4)]
+        rebuild_steps, entries (over all builds), kmax."""
+        v = [ctypes.c_int64() for _ in range(5)]
         km = ctypes.c_int32()
         _check(self._lib.lc_list_info(self._h, *(ctypes.byref(x) for x in v), ctypes.byref(km), _stream(stream)),
                "lc_list_info")
         return {"builds": v[0].value, "long_rows": v[1].value, "longest_row": v[2].value,
-                "rebuild_steps": v[3].value, "kmax": km.value}
+                "rebuild_steps": v[3].value, "entries": v[4].value, "kmax": km.value}
 
     def set_tile(self, ni=0, warps=0):
         _check(self._lib.lc_set_tile(self._h, int(ni), int(warps)), "lc_set_tile")

@@ -50,6 +50,11 @@ def test_list_forces_4k(lc):
     # FCC + small jitter: 78 partners within rc + skin on average
     assert 60 <= info["longest_row"] <= 120 and info["long_rows"] == 0
     assert info["kmax"] == info["longest_row"] + info["longest_row"] // 4 + 8
+    # every pair within rc + skin in two rows: brute force over the box
+    from scipy.spatial import cKDTree
+    pos, box = b["pos"], b["box"]
+    n_rl = len(cKDTree(np.mod(pos, box), boxsize=box).query_pairs(RC + 0.3))
+    assert abs(info["entries"] - 2 * n_rl) <= 2 * 1e-3 * n_rl   # FP32 test with a 2e-5 margin on (rc + skin)^2
 
 
 def test_list_forces_liquid_like(lc):
@@ -183,6 +188,13 @@ def test_list_verlet_matches_oracle(lc, skin):
         p = g.get("pos")
         vel = g.get("vel")
         info = g.list_info()
+        g.forces("list")              # the lists are still valid: no build
+        f_now = g.get("forces")
+        _, _, _, np_now = g.energy()
+        assert g.list_info()["builds"] == info["builds"]
+    fref, _, _, npairs_now = oracle.lc_forces(p[:, 0], p[:, 1], p[:, 2], b["box"], RC)
+    assert np_now == npairs_now
+    assert rel_err(f_now, fref) <= TOL
     dx = p - x
     dx -= b["box"] * np.rint(dx / b["box"])
     assert np.abs(dx).max() < 1e-5
