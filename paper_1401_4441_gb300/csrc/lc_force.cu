@@ -102,12 +102,6 @@ __device__ __forceinline__ int colour_task_cell(const Grid &g, int colour, int t
     return cA[0] + g.nc[0] * (cA[1] + g.nc[1] * cA[2]);
 }
 
-__device__ __forceinline__ int colour_ntasks(const Grid &g, int colour) {
-    int raw = g.raw_of_colour[colour];
-    int a[3] = {raw % 3, (raw / 3) % 3, raw / 9};
-    return g.class_count[0][a[0]] * g.class_count[1][a[1]] * g.class_count[2][a[2]];
-}
-
 // Neighbour k of the task (k < nnb): offset and periodic image.
 template <int MODE>
 __device__ __forceinline__ void task_offset(int group, int k, bool self, int dims, int o[3]) {
@@ -1280,8 +1274,6 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
     }
     return e;
 }
-
-int force_grid_warps(const Ctx *c) { return c->nwarp_max; }
 
 template <bool MIXED>
 static cudaError_t launch_dag(Ctx *c, const DagDev *dd, long long wait_ns, int32_t *trace, cudaStream_t s) {

@@ -224,7 +224,6 @@ cudaError_t launch_schedule_check(Ctx *c, lc_schedule sched, cudaStream_t s);
 cudaError_t launch_unsort_vec(Ctx *c, const double *a, const double *b, const double *cc,
                               double *dst, cudaStream_t s, int wrap);
 cudaError_t launch_set_state(Ctx *c, const double *pos, const double *vel, cudaStream_t s);
-int force_grid_warps(const Ctx *c);
 // Verlet neighbour lists (lc_list.cu)
 bool make_list_grid(Ctx *c);   // false: fewer than 3 list cells in some dimension
 cudaError_t launch_list_build(Ctx *c, cudaStream_t s, bool write);
