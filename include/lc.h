@@ -214,6 +214,20 @@ lc_status lc_list_info(lc_ctx *ctx, int64_t *builds, int64_t *long_rows, int64_t
 lc_status lc_energy_virial(lc_ctx *ctx, double *u_pot, double *k_kin, double *virial,
                            int64_t *npairs, void *stream);
 
+/* The same energies without waiting: queues on `stream` the kinetic-energy
+ * reduction and the copy of the 48-byte result block into `out` and returns
+ * at once, so the next step can be queued before this one's result is read.
+ * out: 48 bytes, 8-byte aligned host memory owned by the caller, valid until
+ * the stream has passed the copy; page-locked memory keeps the call
+ * asynchronous (pageable memory makes the copy synchronous).  After the
+ * stream has passed the copy (an event or a stream synchronisation),
+ * lc_result_decode(out, ...) gives U, K, W and the pair count, and the
+ * status lc_energy_virial would have returned.  LC_ERR_INVALID_ARG for a
+ * batch of boxes (lc_batch_energies), LC_ERR_STATE if no forces were
+ * evaluated for the current state. */
+lc_status lc_energy_virial_async(lc_ctx *ctx, void *out, void *stream);
+lc_status lc_result_decode(const void *out, double *u_pot, double *k_kin, double *virial, int64_t *npairs);
+
 /* Copy one array out (layouts under lc_get_what).  on_device != 0: dst is
  * device memory.  Host copies synchronise the stream. */
 lc_status lc_get(lc_ctx *ctx, lc_get_what what, void *dst, int on_device, void *stream);

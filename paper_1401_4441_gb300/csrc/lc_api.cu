@@ -746,6 +746,33 @@ lc_status lc_energy_virial(lc_ctx *c, double *u_pot, double *k_kin, double *viri
     return LC_OK;
 }
 
+lc_status lc_energy_virial_async(lc_ctx *c, void *out, void *stream) {
+    if (!c || !out || c->nbox > 0) return LC_ERR_INVALID_ARG;
+    if (!c->have_state || !c->forces_valid) return LC_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    LC_TRY(launch_kinetic(c, s));
+    LC_TRY(cudaMemcpyAsync(out, c->d_result, 48, cudaMemcpyDeviceToHost, s));
+    return LC_OK;
+}
+
+// Layout of the result block: U, W, pairs (as double), K, then the pair
+// count as int64 and the error flags as int32.
+lc_status lc_result_decode(const void *out, double *u_pot, double *k_kin, double *virial, int64_t *npairs) {
+    if (!out) return LC_ERR_INVALID_ARG;
+    const double *r = static_cast<const double *>(out);
+    long long np;
+    int err;
+    memcpy(&np, r + 4, sizeof(np));
+    memcpy(&err, r + 5, sizeof(err));
+    if (err & kErrNonfinite) return LC_ERR_NONFINITE;
+    if (err & kErrTimeout) return LC_ERR_TIMEOUT;
+    if (u_pot) *u_pot = r[0];
+    if (virial) *virial = r[1];
+    if (npairs) *npairs = (int64_t)np;
+    if (k_kin) *k_kin = r[3];
+    return LC_OK;
+}
+
 lc_status lc_get(lc_ctx *c, lc_get_what what, void *dst, int on_device, void *stream) {
     if (!c || !dst) return LC_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;

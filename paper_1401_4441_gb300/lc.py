@@ -65,6 +65,8 @@ def _load():
         "lc_create_2d": ([dp, ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctx_pp], ctypes.c_int),
         "lc_stage_state": ([vp, vp, vp, ctypes.c_int32, vp], ctypes.c_int),
         "lc_set_state_staged": ([vp, ctypes.c_int32, vp], ctypes.c_int),
+        "lc_energy_virial_async": ([vp, vp, vp], ctypes.c_int),
+        "lc_result_decode": ([vp, dp, dp, dp, lp], ctypes.c_int),
         "lc_set_skin": ([vp, ctypes.c_double, ctypes.c_int32], ctypes.c_int),
         "lc_list_info": ([vp, lp, lp, lp, lp, lp, ip, vp], ctypes.c_int),
         "lc_destroy": ([vp], None),
@@ -115,6 +117,17 @@ def _perm(perm):
         return None, 0
     perm = [int(x) for x in perm]
     return (ctypes.c_int32 * len(perm))(*perm), len(perm)
+
+
+def decode(out):
+    """(U, K, W, npairs) from a result block filled by Box.energy_async."""
+    lib = _load()
+    p, _ = _ptr(out)
+    u, k, w = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    npairs = ctypes.c_int64()
+    _check(lib.lc_result_decode(p, ctypes.byref(u), ctypes.byref(k), ctypes.byref(w), ctypes.byref(npairs)),
+           "lc_result_decode")
+    return u.value, k.value, w.value, npairs.value
 
 
 def dag_plan(nc, order="loopex", perm=None):
@@ -208,6 +221,15 @@ class Box:
         _check(self._lib.lc_energy_virial(self._h, ctypes.byref(u), ctypes.byref(k), ctypes.byref(w),
                                           ctypes.byref(npairs), _stream(stream)), "lc_energy_virial")
         return u.value, k.value, w.value, npairs.value
+
+    def energy_async(self, out, stream=None):
+        """Queue the energies into `out` (48 bytes of page-locked host
+        memory: a pinned torch tensor or a numpy array) without waiting;
+        read them with decode(out) once the stream has passed this point."""
+        p, dev = _ptr(out)
+        if dev:
+            raise TypeError("out must be host memory")
+        _check(self._lib.lc_energy_virial_async(self._h, p, _stream(stream)), "lc_energy_virial_async")
 
     def grid(self):
         nc = (ctypes.c_int32 * 3)()

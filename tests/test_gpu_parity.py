@@ -342,3 +342,45 @@ def test_staged_host_input(lc):
             assert np.array_equal(f, ref[k % 2][0])
             assert np.array_equal(v, ref[k % 2][1])
         torch.cuda.synchronize()
+
+
+def test_energy_async_pipelined(lc):
+    """Result blocks read back without waiting: decoded one step later they
+    equal lc_energy_virial's values, with staged host input on a copy stream
+    (the pipelined end-to-end loop of the benchmark)."""
+    import torch
+    boxes = [inputs.fcc_box(4000, 0.8442, 0.72, seed=s, jitter=0.05) for s in (1, 2)]
+    h = [(torch.from_numpy(b["pos"]).pin_memory(), torch.from_numpy(b["vel"]).pin_memory()) for b in boxes]
+    ref = []
+    with lc.Box(boxes[0]["box"], RC, 4000, "mixed") as g:
+        for p, v in h:
+            g.set_state(p, v)
+            g.forces("buffer")
+            ref.append(g.energy())
+        res = [torch.zeros(6, dtype=torch.float64).pin_memory() for _ in range(2)]
+        done = [torch.cuda.Event(), torch.cuda.Event()]
+        cs = torch.cuda.Stream()
+        st = torch.cuda.current_stream()
+        got = []
+        g.stage_state(*h[0], slot=0, copy_stream=cs.cuda_stream)
+        for k in range(6):
+            g.set_state_staged(k % 2)
+            if k + 1 < 6:
+                g.stage_state(*h[(k + 1) % 2], slot=(k + 1) % 2, copy_stream=cs.cuda_stream)
+            g.forces("buffer")
+            g.energy_async(res[k % 2])
+            done[k % 2].record(st)
+            if k >= 1:
+                done[(k - 1) % 2].synchronize()
+                got.append(lc.decode(res[(k - 1) % 2]))
+        done[1].synchronize()
+        got.append(lc.decode(res[1]))
+        for k, e in enumerate(got):
+            assert e == ref[k % 2]
+        g.set_state(*h[0])
+        with pytest.raises(lc.LCError) as ei:
+            g.energy_async(res[0])          # no forces for this state yet
+        assert ei.value.code == 7
+    with lc.Batch([boxes[0]["box"]] * 2, RC, [10, 10]) as g:
+        with pytest.raises(lc.LCError):
+            g.energy_async(res[0])
