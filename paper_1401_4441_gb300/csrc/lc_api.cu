@@ -203,7 +203,7 @@ static cudaError_t alloc_common(Ctx *c) {
         (e = dalloc(&c->d_blocksums, (size_t)ntiles + 1)) || (e = dalloc(&c->d_colour, NC)) ||
         (e = dalloc(&c->d_p4, N)) || (e = dalloc(&c->fx, 3 * N)) || (e = dalloc(&c->kx, 3 * N)) ||
         (e = dalloc(&c->d_warp_acc, 4 * (size_t)c->nwarp_max)) || (e = dalloc(&c->d_warp_pairs, (size_t)c->nwarp_max)) ||
-        (e = dalloc(&c->d_kin_part, (size_t)c->num_sms * 2)) || (e = dalloc(&c->d_result, 8)) ||
+        (e = dalloc(&c->d_kin_part, (size_t)kinetic_blocks(c))) || (e = dalloc(&c->d_result, 8)) ||
         (e = cudaHostAlloc(&c->h_out, 64, cudaHostAllocDefault)))
         return e;
     c->d_npairs = reinterpret_cast<long long *>(c->d_result + 4);
@@ -658,6 +658,7 @@ lc_status lc_verlet_step(lc_ctx *c, double dt, int nsteps, lc_schedule sched, vo
         return LC_ERR_INVALID_ARG;
     if (c->nbox > 0 && sched == LC_SCHED_COLOUR) return LC_ERR_INVALID_ARG;
     if (!c->have_state) return LC_ERR_STATE;
+    if (nsteps > 0) c->kin_valid = false;   // the steps change the velocities
     if (sched == LC_SCHED_LIST) return list_verlet(c, dt, nsteps, (cudaStream_t)stream);
     cudaStream_t s = (cudaStream_t)stream;
     int launches = 0;

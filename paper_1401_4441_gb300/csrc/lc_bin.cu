@@ -304,25 +304,31 @@ cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches, int kicks, double 
 }
 
 // ---------------------------------------------------------- state I/O ---
-__global__ void k_deinterleave(int n, const double *__restrict__ in, double *__restrict__ a,
-                               double *__restrict__ b, double *__restrict__ cc) {
+// New state from [n][3] arrays in one pass: positions, velocities (zero
+// when vel is null), identity IDs, and the block partials of v^2.  2D
+// contexts: the particles sit at z = zval inside the single cell layer (a
+// value away from the layer's faces) with vz = 0; the z the caller gave is
+// ignored.
+__global__ void __launch_bounds__(kKinThreads) k_set_state(int n, const double *__restrict__ pos,
+                                                           const double *__restrict__ vel, int plane, double zval,
+                                                           State st, double *__restrict__ kin_part) {
+    __shared__ double red[kKinThreads];
+    double acc = 0.0;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        a[s] = in[3 * s + 0]; b[s] = in[3 * s + 1]; cc[s] = in[3 * s + 2];
+        const double x = pos[3 * (size_t)s], y = pos[3 * (size_t)s + 1];
+        const double z = plane ? zval : pos[3 * (size_t)s + 2];
+        double vx = 0.0, vy = 0.0, vz = 0.0;
+        if (vel) {
+            vx = vel[3 * (size_t)s]; vy = vel[3 * (size_t)s + 1];
+            vz = plane ? 0.0 : vel[3 * (size_t)s + 2];
+        }
+        st.x[s] = x; st.y[s] = y; st.z[s] = z;
+        st.vx[s] = vx; st.vy[s] = vy; st.vz[s] = vz;
+        st.id[s] = s;
+        acc = __dadd_rn(acc, kin_term(vx, vy, vz));
     }
-}
-
-__global__ void k_iota(int n, int *id) {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) id[s] = s;
-}
-
-// 2D contexts: the particles sit at z = zval inside the single cell layer
-// (a value away from the layer's faces) with vz = 0; the z the caller gave
-// is ignored.
-__global__ void k_plane(int n, double zval, double *__restrict__ z, double *__restrict__ vz) {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        z[s] = zval;
-        vz[s] = 0.0;
-    }
+    const double t = block_sum_kin(acc, red);
+    if (threadIdx.x == 0) kin_part[blockIdx.x] = t;
 }
 
 // dst[id[s]] = (a[s], b[s], c[s]); wrap != 0 wraps positions into [0, L);
@@ -344,19 +350,13 @@ __global__ void k_unsort_vec(int n, Grid g1, const BoxDev *__restrict__ boxes, c
 
 cudaError_t launch_set_state(Ctx *c, const double *pos, const double *vel, cudaStream_t s) {
     const int n = (int)c->n;
+    c->kin_valid = false;
     if (n == 0) return cudaSuccess;
-    const int grid_n = c->num_sms * 8;
-    k_deinterleave<<<grid_n, 256, 0, s>>>(n, pos, c->cur.x, c->cur.y, c->cur.z);
-    if (vel) {
-        k_deinterleave<<<grid_n, 256, 0, s>>>(n, vel, c->cur.vx, c->cur.vy, c->cur.vz);
-    } else {
-        cudaMemsetAsync(c->cur.vx, 0, sizeof(double) * (size_t)n, s);
-        cudaMemsetAsync(c->cur.vy, 0, sizeof(double) * (size_t)n, s);
-        cudaMemsetAsync(c->cur.vz, 0, sizeof(double) * (size_t)n, s);
-    }
-    if (c->g.dims == 2) k_plane<<<grid_n, 256, 0, s>>>(n, 0.25 * c->g.L[2], c->cur.z, c->cur.vz);
-    k_iota<<<grid_n, 256, 0, s>>>(n, c->cur.id);
-    return cudaGetLastError();
+    k_set_state<<<kinetic_blocks(c), kKinThreads, 0, s>>>(n, pos, vel, c->g.dims == 2, 0.25 * c->g.L[2], c->cur,
+                                                          c->d_kin_part);
+    cudaError_t e = cudaGetLastError();
+    if (!e) c->kin_valid = true;
+    return e;
 }
 
 cudaError_t launch_unsort_vec(Ctx *c, const double *a, const double *b, const double *cc, double *dst,

@@ -139,7 +139,8 @@ struct Ctx {
     float2 *kx, *ky, *kz;  // Kahan (sum, compensation) accumulators, colour + mixed
     double *d_warp_acc;    // per-warp partials: [nwarp_max][4] (s6, s12, K, spare)
     long long *d_warp_pairs;
-    double *d_kin_part;    // per-block partial sums of v^2
+    double *d_kin_part;    // per-block partial sums of v^2 (kinetic_blocks of them)
+    bool kin_valid;        // d_kin_part holds the partials of the current velocities
     // one 64-byte device block, read back in one copy: U, W, pairs (as
     // double), K, then the pair count and the error flags
     double *d_result;      // [4] U, W, npairs (as double), K  (block + 0)
@@ -239,6 +240,23 @@ __global__ void k_scan_partials(int ntiles, int *__restrict__ partial);
 __global__ void k_scan_add(int ncell, int n, int *__restrict__ start, const int *__restrict__ partial);
 
 // ---- small device helpers ----------------------------------------------------
+// v^2 of one particle, each operation rounded once (no contraction), and the
+// block sum of 256 thread partials in a fixed tree: every kernel that forms
+// kinetic-energy partials gets the same bits for the same state.
+constexpr int kKinThreads = 256;
+__device__ __forceinline__ double kin_term(double vx, double vy, double vz) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz));
+}
+__device__ __forceinline__ double block_sum_kin(double acc, double *red) {
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int m = kKinThreads / 2; m > 0; m >>= 1) {
+        if (threadIdx.x < m) red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + m]);
+        __syncthreads();
+    }
+    return red[0];
+}
+
 // Periodic wrap into [0, L), each operation rounded once (no contraction):
 // x - L floor(x / L), then one correction for the rounding edge cases.
 // For x in (0, L) that formula returns x itself (x / L rounds below

@@ -22,21 +22,15 @@ __global__ void k_kick(int n, double half, State st, const double *__restrict__ 
     }
 }
 
-// Block partial sums of v^2 (grid-stride, fixed assignment: deterministic).
-__global__ void __launch_bounds__(256) k_kinetic(int n, State st, double *__restrict__ part) {
-    __shared__ double red[256];
+// Block partial sums of v^2 (grid-stride, fixed assignment: deterministic;
+// the same arithmetic as the partials the state set-up forms).
+__global__ void __launch_bounds__(kKinThreads) k_kinetic(int n, State st, double *__restrict__ part) {
+    __shared__ double red[kKinThreads];
     double acc = 0.0;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        double vx = st.vx[s], vy = st.vy[s], vz = st.vz[s];
-        acc += vx * vx + vy * vy + vz * vz;
-    }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int m = 128; m > 0; m >>= 1) {
-        if (threadIdx.x < m) red[threadIdx.x] += red[threadIdx.x + m];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        acc = __dadd_rn(acc, kin_term(st.vx[s], st.vy[s], st.vz[s]));
+    const double t = block_sum_kin(acc, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 // Sum of the per-warp partials in a fixed tree order.
@@ -143,14 +137,18 @@ cudaError_t launch_kick(Ctx *c, double dt, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-int kinetic_blocks(const Ctx *c) { return c->num_sms * 2; }
+int kinetic_blocks(const Ctx *c) { return c->num_sms * 8; }
 
+// K into the result block; the pass over the velocities is skipped while
+// the partials still describe them (the state set-up forms them).
 cudaError_t launch_kinetic(Ctx *c, cudaStream_t s) {
     const int nb = kinetic_blocks(c);
     double *part = c->d_kin_part;
-    k_kinetic<<<nb, 256, 0, s>>>((int)c->n, c->cur, part);
+    if (!c->kin_valid) k_kinetic<<<nb, kKinThreads, 0, s>>>((int)c->n, c->cur, part);
     k_final_kin<<<1, kRedThreads, 0, s>>>(nb, part, c->d_result);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (!e) c->kin_valid = true;
+    return e;
 }
 
 cudaError_t launch_energy_reduce(Ctx *c, cudaStream_t s, int full) {
