@@ -272,3 +272,24 @@ def test_list_energy_drift_1m(lc):
         drift[sched] = abs((u1 + k1) - (u0 + k0)) / abs(u0 + k0)
     assert info["long_rows"] == 0 and info["builds"] >= 2
     assert drift["list"] <= 3 * drift["atomic"] + 1e-6, drift
+
+
+def test_list_16m_sampled(lc):
+    """The 16.7M-particle box from fresh lists: per-particle oracle sums on a
+    sample, and the pair count of the link-cell sweep on the same state."""
+    b = inputs.workload("fcc16m")
+    pos, box = b["pos"], b["box"]
+    with lc.Box(box, RC, pos.shape[0], "mixed") as g:
+        g.set_state(pos)
+        g.forces("list")
+        f = g.get("forces")
+        _, _, _, np_list = g.energy()
+        info = g.list_info()
+        g.forces("atomic")
+        _, _, _, np_lc = g.energy()
+    ids = np.linspace(0, pos.shape[0] - 1, 3000).astype(np.int64)
+    fref, _ = oracle.forces_sample(pos[:, 0], pos[:, 1], pos[:, 2], box, RC, ids)
+    scale = max(1e-3, math.sqrt(float((fref ** 2).sum(1).mean())))
+    assert np.abs(f[ids] - fref).max() <= 1e-5 * scale + 1e-9
+    assert np_list == np_lc
+    assert info["long_rows"] == 0 and info["builds"] == 1
