@@ -192,10 +192,10 @@ lc_status lc_verlet_step(lc_ctx *ctx, double dt, int nsteps, lc_schedule sched, 
  * lc_set_skin: skin >= 0 (default 0.4); kmax = entries per particle kept in
  * the list (0: sized from the first build, 1.25 x the longest row + 8).
  * A row longer than kmax is still exact: its partners are swept from the
- * cells.  Frees the current lists (allocated again on next use: 4 kmax + 36
- * bytes per particle).  LC_ERR_INVALID_ARG for a negative or non-finite skin
- * or kmax < 0; LC_ERR_BOX_TOO_SMALL if some box edge holds fewer than 3 cells
- * of side rc + skin (checked on first use). */
+ * cells.  Waits for the device, then frees the current lists (allocated
+ * again on next use: 4 kmax + 36 bytes per particle).  LC_ERR_INVALID_ARG for
+ * a negative or non-finite skin or kmax < 0; LC_ERR_BOX_TOO_SMALL if some box
+ * edge holds fewer than 3 cells of side rc + skin (checked on first use). */
 lc_status lc_set_skin(lc_ctx *ctx, double skin, int32_t kmax);
 
 /* Counters of the lists since the last lc_set_skin: builds, rows longer

@@ -596,6 +596,7 @@ static lc_status list_verlet(lc_ctx *c, double dt, int nsteps, cudaStream_t s) {
 
 lc_status lc_set_skin(lc_ctx *c, double skin, int32_t kmax) {
     if (!c || !(skin >= 0.0) || !isfinite(skin) || kmax < 0) return LC_ERR_INVALID_ARG;
+    LC_TRY(cudaDeviceSynchronize());   // no list step in flight past this point
     drop_list_graphs(c);
     if (c->d_nbr) { cudaFree(c->d_nbr); c->d_nbr = nullptr; }
     c->skin = skin;
