@@ -75,6 +75,23 @@ def test_list_long_rows_swept_from_cells(lc, kmax):
     assert np.abs(f - f_full).max() <= 1e-5 * np.abs(f_full).max()
 
 
+def test_list_overlap_stress(lc):
+    """Overlapping particles (min distance 0.46 sigma, forces up to 1e6): the
+    exact pair set, and the error bound the link-cell schedules meet on this
+    input (FP32 pair math keeps about 1e-6 of each particle's own force)."""
+    b = inputs.fcc_box(20000, 0.8442, 1.0, seed=3, jitter=0.25)
+    pos, box = b["pos"], b["box"]
+    fref, U, W, npairs = oracle.lc_forces(pos[:, 0], pos[:, 1], pos[:, 2], box, RC)
+    with lc.Box(box, RC, pos.shape[0], "mixed") as g:
+        g.set_state(pos)
+        g.forces("list")
+        f = g.get("forces")
+        u, k, w, np_ = g.energy()
+    assert np_ == npairs
+    assert rel_err(f, fref) <= 1e-4
+    assert u == pytest.approx(U, rel=1e-4)
+
+
 def test_list_odd_grids_and_skins(lc):
     for box, skin in ((np.array([9.1, 8.5, 12.7]), 0.3), (np.array([10.2, 15.3, 8.6]), 0.1),
                       (np.array([7.6, 7.6, 7.6]), 0.0)):
