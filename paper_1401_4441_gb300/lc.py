@@ -322,6 +322,7 @@ class Batch(Box):
         rcs = np.ascontiguousarray(np.broadcast_to(np.asarray(rcs, np.float64), (boxes.shape[0],)))
         ns = np.ascontiguousarray(np.asarray(ns, np.int64))
         self.nbox = boxes.shape[0]
+        self.rcs = rcs
         self.ns = ns
         self.offsets = np.concatenate([[0], np.cumsum(ns)])
         self.n = int(ns.sum())
