@@ -717,14 +717,17 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
             S[2 * m + h] = ii < na ? a0 + ii : 0x7fffffff;
             sm.corr[lane][0] = sm.corr[lane][1] = sm.corr[lane][2] = 0.f;
         }
+        // the box is only used by the prune (lists longer than one chunk)
+        if (total > kWarp) {
 #pragma unroll
-        for (int m = 16; m >= 1; m >>= 1) {
-            bmin.x = fminf(bmin.x, __shfl_xor_sync(kFull, bmin.x, m));
-            bmin.y = fminf(bmin.y, __shfl_xor_sync(kFull, bmin.y, m));
-            bmin.z = fminf(bmin.z, __shfl_xor_sync(kFull, bmin.z, m));
-            bmax.x = fmaxf(bmax.x, __shfl_xor_sync(kFull, bmax.x, m));
-            bmax.y = fmaxf(bmax.y, __shfl_xor_sync(kFull, bmax.y, m));
-            bmax.z = fmaxf(bmax.z, __shfl_xor_sync(kFull, bmax.z, m));
+            for (int m = 16; m >= 1; m >>= 1) {
+                bmin.x = fminf(bmin.x, __shfl_xor_sync(kFull, bmin.x, m));
+                bmin.y = fminf(bmin.y, __shfl_xor_sync(kFull, bmin.y, m));
+                bmin.z = fminf(bmin.z, __shfl_xor_sync(kFull, bmin.z, m));
+                bmax.x = fmaxf(bmax.x, __shfl_xor_sync(kFull, bmax.x, m));
+                bmax.y = fmaxf(bmax.y, __shfl_xor_sync(kFull, bmax.y, m));
+                bmax.z = fmaxf(bmax.z, __shfl_xor_sync(kFull, bmax.z, m));
+            }
         }
         float2 ax2[NI / 2], ay2[NI / 2], az2[NI / 2];
 #pragma unroll
@@ -739,7 +742,10 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
         while (b < tc.nnb) {
             int nj = total;
             const int *list = sm.jk;
-            if (total <= kJCap) {                            // listed once above: prune it
+            if (total <= kWarp) {                            // one chunk whatever the prune keeps
+                b = tc.nnb;
+                list = sm.jl;
+            } else if (total <= kJCap) {                     // listed once above: prune it
                 b = tc.nnb;
                 nj = prune_list<MODE>(a, sm, total, bmin, bmax, g.rc2f_hi * 1.0001f, i0 == 0, lane);
             } else {                                         // long lists: in batches, unpruned
