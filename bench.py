@@ -360,8 +360,7 @@ def run_batch(args, dist):
     value_fp64 = pairs_fp64 / (t_fp64 * 1e-3)
     if dist.rank == 0:
         ns = [b["pos"].shape[0] for b in boxes]
-        line = {"metric": METRIC_LIST if is_list else METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
-                "steps": args.steps,
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
                 "data": "synthetic",
