@@ -310,3 +310,27 @@ def test_list_16m_sampled(lc):
     assert np.abs(f[ids] - fref).max() <= 1e-5 * scale + 1e-9
     assert np_list == np_lc
     assert info["long_rows"] == 0 and info["builds"] == 1
+
+
+def test_list_verlet_skin_change_and_long_rows(lc):
+    """Skin changed between calls (the lists and step graphs are rebuilt),
+    and steps whose rows mostly exceed the capacity (swept from the cells
+    inside the captured step): the oracle's trajectory."""
+    b = inputs.fcc_box(4000, 0.8442, 0.72, jitter=0.05)
+    x, v, f, e = oracle.verlet(b["pos"], b["vel"], b["box"], RC, 0.005, 12)
+    with lc.Box(b["box"], RC, 4000, "mixed") as g:
+        g.set_state(b["pos"], b["vel"])
+        g.set_skin(0.3)
+        g.verlet(0.005, 4, "list")
+        g.set_skin(0.1, 40)                 # rows of ~55: most are swept from the cells
+        g.verlet(0.005, 5, "list")
+        info = g.list_info()
+        g.set_skin(0.5)
+        g.verlet(0.005, 3, "list")
+        p = g.get("pos")
+        u, k, w, np_ = g.energy()
+    assert info["kmax"] == 40 and info["long_rows"] > 0 and info["builds"] >= 1
+    dx = p - x
+    dx -= b["box"] * np.rint(dx / b["box"])
+    assert np.abs(dx).max() < 1e-5
+    assert u == pytest.approx(e[-1, 0], rel=1e-5)
