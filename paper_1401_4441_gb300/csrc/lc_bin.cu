@@ -255,8 +255,26 @@ cudaError_t launch_colour(Ctx *c, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// One resident wave of 256-thread blocks of `kernel` (its register count
+// decides how many fit on an SM): the grid-stride loops then run without a
+// partial second wave.
+template <typename K>
+static int one_wave(const Ctx *c, K kernel, int *cache) {
+    if (!*cache) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0) != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 4;
+        }
+        *cache = per_sm;
+    }
+    return c->num_sms * *cache;
+}
+
 template <bool BATCHED, int KICKS>
-static void cellid_launch(Ctx *c, int grid_n, const Drift &dr, cudaStream_t s) {
+static void cellid_launch(Ctx *c, int, const Drift &dr, cudaStream_t s) {
+    static int per_sm = 0;
+    const int grid_n = one_wave(c, k_cellid<BATCHED, KICKS>, &per_sm);
     k_cellid<BATCHED, KICKS><<<grid_n, 256, 0, s>>>(c->g, BATCHED ? c->d_boxes : nullptr,
                                                     BATCHED ? c->d_slot_box : nullptr, (int)c->n, c->cur.x, c->cur.y,
                                                     c->cur.z, dr, c->d_cell, c->d_rank, c->d_count, c->d_err);
@@ -286,14 +304,15 @@ cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches, int kicks, double 
     *launches += 3;
     if (n > 0) {
         k_scatter<<<grid_n, 256, 0, s>>>(n, c->d_cell, c->d_rank, c->d_start, c->cur.id, c->d_src, c->d_key);
+        static int per_sm_b = 0, per_sm_s = 0;
         if (c->nbox > 0)
-            k_rank_gather<true><<<grid_n, 256, 0, s>>>(c->g, c->d_boxes, c->d_slot_box, n, c->prec == LC_PREC_MIXED,
-                                                       c->d_start, c->d_count, c->d_cell, c->d_src, c->d_key, c->cur,
-                                                       c->nxt, c->d_p4);
+            k_rank_gather<true><<<one_wave(c, k_rank_gather<true>, &per_sm_b), 256, 0, s>>>(
+                c->g, c->d_boxes, c->d_slot_box, n, c->prec == LC_PREC_MIXED, c->d_start, c->d_count, c->d_cell,
+                c->d_src, c->d_key, c->cur, c->nxt, c->d_p4);
         else
-            k_rank_gather<false><<<grid_n, 256, 0, s>>>(c->g, nullptr, nullptr, n, c->prec == LC_PREC_MIXED, c->d_start,
-                                                        c->d_count, c->d_cell, c->d_src, c->d_key, c->cur, c->nxt,
-                                                        c->d_p4);
+            k_rank_gather<false><<<one_wave(c, k_rank_gather<false>, &per_sm_s), 256, 0, s>>>(
+                c->g, nullptr, nullptr, n, c->prec == LC_PREC_MIXED, c->d_start, c->d_count, c->d_cell, c->d_src,
+                c->d_key, c->cur, c->nxt, c->d_p4);
         *launches += 2;
     }
     e = cudaGetLastError();
