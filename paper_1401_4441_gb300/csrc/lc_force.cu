@@ -66,6 +66,7 @@ struct ForceArgs {
     int group, colour;          // colour phase
     int ntasks;
     int stats;                  // accumulate energy, virial and pair count
+    int pairx;                  // 2D atomic: a task is two x-adjacent cells (see single_task)
     float sh[27][3];            // o * h rounded to FP32, offset index (ox+1) + 3 (oy+1) + 9 (oz+1)
     float sl[27][3];            // o * h - sh, rounded to FP32
     // batch of boxes (BATCHED kernels): per-box grids, box of every global
@@ -82,6 +83,8 @@ struct TaskCells {
     int cA[3];        // its coordinates in its box
     int nnb;          // neighbour cells listed (self first when present)
     bool self;        // intra-cell interaction included
+    int nself;        // leading entries whose pairs are taken once by slot order (0, 1, or 2)
+    int pairx;        // 1: the task is cells A and A + x (2D atomic), see single_task
     int group;        // colour: the phase's offset group; DAG: the offset index
     int dims;         // 3, or 2 (stencil in the x-y plane)
     const Grid *g;    // the box's grid
@@ -103,8 +106,20 @@ __device__ __forceinline__ int colour_task_cell(const Grid &g, int colour, int t
 }
 
 // Neighbour k of the task (k < nnb): offset and periodic image.
+// Entries of a two-cell task (cells A and A + x of the 2D atomic schedule),
+// as offsets from A: the two cells themselves (both ordered by slot), the
+// cell after them, and the four cells of the next row from A - x to A + 2x.
+// The pairs each cell needs are among them; the others (A with the two
+// outer cells, A + x with A - x + y) lie at least a cell side, >= r_c, apart
+// and never pass the cutoff, so every pair inside r_c is taken once.
+__constant__ int c_pair_off[7][2] = {{0, 0}, {1, 0}, {2, 0}, {-1, 1}, {0, 1}, {1, 1}, {2, 1}};
+
 template <int MODE>
-__device__ __forceinline__ void task_offset(int group, int k, bool self, int dims, int o[3]) {
+__device__ __forceinline__ void task_offset(int group, int k, bool self, int dims, int o[3], int pairx = 0) {
+    if (MODE == kAtomic && pairx) {
+        o[0] = c_pair_off[k][0]; o[1] = c_pair_off[k][1]; o[2] = 0;
+        return;
+    }
     if (self) {
         if (k == 0) { o[0] = o[1] = o[2] = 0; return; }
         --k;
@@ -125,23 +140,38 @@ __device__ __forceinline__ void task_offset(int group, int k, bool self, int dim
 // Single-box task t: the cell (colour schedule: the t-th cell of the phase's
 // colour) and its neighbour count; used by the force and check kernels.
 template <int MODE>
-__device__ __forceinline__ void single_task(const Grid &g, int group, int colour, int t, TaskCells &tc) {
+__device__ __forceinline__ void single_task(const Grid &g, int group, int colour, int t, TaskCells &tc,
+                                            int pairx = 0) {
     tc.group = group;
     tc.dims = g.dims;
+    tc.pairx = 0;
     const Stencil &S = stencil(g.dims);
     if (MODE == kColour) {
         tc.A = colour_task_cell(g, colour, t, tc.cA);
         tc.self = (group == 0);
         tc.nnb = (S.group_first[group + 1] - S.group_first[group]) + (tc.self ? 1 : 0);
+        tc.nself = tc.self ? 1 : 0;
+    } else if (MODE == kAtomic && pairx) {
+        // 2D atomic: task t = cells (2 tx, ty) and (2 tx + 1, ty); an odd
+        // row's last cell is a task of its own (the one-cell half-shell)
+        const int nhx = (g.nc[0] + 1) >> 1;
+        const int ty = t / nhx, tx = t - ty * nhx;
+        tc.cA[0] = 2 * tx; tc.cA[1] = ty; tc.cA[2] = 0;
+        tc.A = tc.cA[0] + g.nc[0] * ty;
+        tc.self = true;
+        tc.pairx = (tc.cA[0] + 1 < g.nc[0]) ? 1 : 0;
+        tc.nself = tc.pairx ? 2 : 1;
+        tc.nnb = tc.pairx ? 7 : S.nh + 1;
     } else {
         tc.A = t;
         cell_xyz(g, t, tc.cA);
         tc.self = true;
+        tc.nself = 1;
         tc.nnb = (MODE == kFullShell) ? S.nf : S.nh + 1;
     }
 }
 
-template <int MODE, bool BATCHED>
+template <int MODE, bool BATCHED, bool PX = false>
 __device__ __forceinline__ TaskCells make_task(const ForceArgs &a, int t) {
     TaskCells tc;
     if constexpr (BATCHED) {
@@ -154,10 +184,12 @@ __device__ __forceinline__ TaskCells make_task(const ForceArgs &a, int t) {
         tc.group = 0;
         tc.dims = 3;
         tc.self = true;
+        tc.nself = 1;
+        tc.pairx = 0;
         tc.nnb = (MODE == kFullShell) ? 27 : 14;
     } else {
         tc.g = &a.g; tc.sh = a.sh; tc.sl = a.sl; tc.cell_off = 0; tc.box = 0;
-        single_task<MODE>(a.g, a.group, a.colour, t, tc);
+        single_task<MODE>(a.g, a.group, a.colour, t, tc, PX ? 1 : 0);
     }
     return tc;
 }
@@ -426,17 +458,19 @@ __device__ __forceinline__ void setup_neighbours(const ForceArgs &a, WarpSmem<ty
 struct NbPre {
     int start, count;   // of neighbour entry `lane`
     int img, oi;        // its periodic image code and offset index
-    int a0, na;         // the centre cell's first slot and count
+    int dbl;            // two-cell task: the entry lies two cells along x (shift 2 h_x)
+    int a0, na;         // the centre's first slot and count (both cells of a two-cell task)
+    int nA;             // particles of cell A (the rest belong to A + x)
 };
 
-template <int MODE>
+template <int MODE, bool PX = false>
 __device__ __forceinline__ NbPre load_neighbours(const ForceArgs &a, const TaskCells &tc, int lane) {
     NbPre p;
-    p.start = 0; p.count = 0; p.img = 0; p.oi = 13;
+    p.start = 0; p.count = 0; p.img = 0; p.oi = 13; p.dbl = 0;
     if (lane < tc.nnb) {
         const Grid &g = *tc.g;
         int o[3];
-        task_offset<MODE>(tc.group, lane, tc.self, tc.dims, o);
+        task_offset<MODE>(tc.group, lane, tc.self, tc.dims, o, PX ? tc.pairx : 0);
         int c[3];
         int img = 0;
         for (int d = 0; d < 3; ++d) {
@@ -446,22 +480,27 @@ __device__ __forceinline__ NbPre load_neighbours(const ForceArgs &a, const TaskC
             else if (c[d] < 0) { c[d] += g.nc[d]; sgn = -1; }
             img |= (sgn + 1) << (2 * d);
         }
-        p.oi = (o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1);
+        p.dbl = PX && o[0] == 2;   // o * h = 2 * (h rounded to FP32): the table's entry doubled, exactly
+        p.oi = (o[0] - p.dbl + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1);
         p.img = img;
         const int B = tc.cell_off + c[0] + g.nc[0] * (c[1] + g.nc[1] * c[2]);
         p.start = a.start[B];
         p.count = a.count[B];
     }
     p.a0 = a.start[tc.A];
-    p.na = a.count[tc.A];
+    p.nA = a.count[tc.A];
+    p.na = p.nA + ((PX && tc.pairx) ? a.count[tc.A + 1] : 0);
     return p;
 }
 
-template <typename S>
+template <typename S, bool PX = false>
 __device__ __forceinline__ void commit_neighbours(S &sm, const TaskCells &tc, const NbPre &p, int lane) {
     if (lane < tc.nnb) {
-        sm.nb_sh[lane] = make_float4(tc.sh[p.oi][0], tc.sh[p.oi][1], tc.sh[p.oi][2], 0.f);
-        sm.nb_sl[lane] = make_float4(tc.sl[p.oi][0], tc.sl[p.oi][1], tc.sl[p.oi][2], 0.f);
+        float4 sh4 = make_float4(tc.sh[p.oi][0], tc.sh[p.oi][1], tc.sh[p.oi][2], 0.f);
+        float4 sl4 = make_float4(tc.sl[p.oi][0], tc.sl[p.oi][1], tc.sl[p.oi][2], 0.f);
+        if (PX && p.dbl) { sh4.x *= 2.0f; sl4.x *= 2.0f; }
+        sm.nb_sh[lane] = sh4;
+        sm.nb_sl[lane] = sl4;
         sm.nb_img[lane] = p.img;
         sm.nb_start[lane] = p.start;
         sm.nb_count[lane] = p.count;
@@ -681,7 +720,7 @@ __device__ __forceinline__ void box_stats(const ForceArgs &a, int box, double s6
     }
 }
 
-template <int NI, int MODE, bool STATS, bool BATCHED>
+template <int NI, int MODE, bool STATS, bool BATCHED, bool PX = false>
 __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const TaskCells &tc, const NbPre &pre,
                                int lane, LaneEnergy &le) {
     constexpr bool N3 = (MODE != kFullShell);
@@ -697,8 +736,22 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
         if (lane < NI) {   // stage the i chunk (far-away sentinels past the end)
             const int ii = i0 + lane;
             float4 p = make_float4(1.0e15f, 1.0e15f, 1.0e15f, 0.f);
+            unsigned q = 0x20080200u;   // all three residuals zero
             if (ii < na) {
                 p = a.p4[a0 + ii];
+                q = __float_as_uint(p.w);
+            }
+            float rx = lo_residual(q, 0);
+            if (ii < na) {
+                if (PX && tc.pairx && ii >= pre.nA) {
+                    // cell A + x of a two-cell task: into A's frame by its
+                    // shift h_x, added as the neighbours' shifts are
+                    // (Fast2Sum, the error joining the residual)
+                    const float sh = tc.sh[14][0], sl = tc.sl[14][0];   // offset (1, 0, 0)
+                    const float sum = sh + p.x;
+                    rx = ((p.x - (sum - sh)) + rx) + sl;
+                    p.x = sum;
+                }
                 bmin = make_float3(p.x, p.y, p.z);
                 bmax = bmin;
             }
@@ -707,12 +760,11 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
             float *C = reinterpret_cast<float *>(sm.ipc);
             int *S = reinterpret_cast<int *>(sm.islot2);
             const int m = lane >> 1, h = lane & 1;
-            const unsigned q = ii < na ? __float_as_uint(p.w) : 0x20080200u;   // all three residuals zero
             A[4 * m + h] = p.x;
             A[4 * m + 2 + h] = p.y;
             B[4 * m + h] = p.z;
             B[4 * m + 2 + h] = lo_residual(q, 2);
-            C[4 * m + h] = lo_residual(q, 0);
+            C[4 * m + h] = rx;
             C[4 * m + 2 + h] = lo_residual(q, 1);
             S[2 * m + h] = ii < na ? a0 + ii : 0x7fffffff;
             sm.corr[lane][0] = sm.corr[lane][1] = sm.corr[lane][2] = 0.f;
@@ -760,7 +812,7 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
                 const bool valid = cur.w >= 0;
                 const int sj = valid ? (cur.w & ((1 << 26) - 1)) : 0x7fffffff;
                 const int nb = valid ? (cur.w >> 26) : 0;
-                const bool is_self = valid && tc.self && nb == 0;
+                const bool is_self = PX ? (valid && nb < tc.nself) : (valid && tc.self && nb == 0);
                 const int jlim = (N3 && is_self) ? sj : 0x7fffffff;   // Newton-3 intra: slot_i < slot_j
                 const int jexcl = (!N3 && is_self) ? sj : -1;         // full shell: skip i == j
                 // the j position in the centre cell's frame as hi + lo: the
@@ -925,7 +977,7 @@ __device__ void run_task_fp64(const ForceArgs &a, WarpSmem<double> &sm, const Ta
     }
 }
 
-template <bool MIXED, int NI, int MODE, bool STATS, bool BATCHED>
+template <bool MIXED, int NI, int MODE, bool STATS, bool BATCHED, bool PX = false>
 __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
     using T = typename std::conditional<MIXED, float, double>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -941,10 +993,10 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
     le.pairs = 0;
     if constexpr (MIXED) {
         for (int t = w; t < a.ntasks; t += W) {
-            const TaskCells tc = make_task<MODE, BATCHED>(a, t);
-            const NbPre pre = load_neighbours<MODE>(a, tc, lane);
-            commit_neighbours(sm, tc, pre, lane);
-            run_task_mixed<NI, MODE, STATS, BATCHED>(a, sm, tc, pre, lane, le);
+            const TaskCells tc = make_task<MODE, BATCHED, PX>(a, t);
+            const NbPre pre = load_neighbours<MODE, PX>(a, tc, lane);
+            commit_neighbours<WarpSmem<float>, PX>(sm, tc, pre, lane);
+            run_task_mixed<NI, MODE, STATS, BATCHED, PX>(a, sm, tc, pre, lane, le);
         }
     } else {
         for (int t = w; t < a.ntasks; t += W) {
@@ -1008,6 +1060,8 @@ __device__ __forceinline__ TaskCells dag_task(const ForceArgs &a, int A, int k) 
     tc.A = A;
     cell_xyz(a.g, A, tc.cA);
     tc.self = (k == 0);
+    tc.nself = tc.self ? 1 : 0;
+    tc.pairx = 0;
     tc.group = k > 0 ? k - 1 : 0;
     tc.dims = a.g.dims;
     tc.nnb = 1;
@@ -1155,13 +1209,13 @@ static size_t smem_bytes(int warps) {
 }
 
 // One resident wave: SMs x the blocks that fit on an SM (cached per shape).
-template <bool MIXED, int NI, int MODE, bool STATS, bool BATCHED>
+template <bool MIXED, int NI, int MODE, bool STATS, bool BATCHED, bool PX = false>
 static int force_blocks(Ctx *c) {
     static int cache[17] = {0};
     const int warps = c->warps;
     if (!cache[warps]) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force<MIXED, NI, MODE, STATS, BATCHED>, warps * 32,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force<MIXED, NI, MODE, STATS, BATCHED, PX>, warps * 32,
                                                       smem_bytes<MIXED, NI>(warps));
         if (per_sm < 1) per_sm = 1;
         cache[warps] = per_sm;
@@ -1171,13 +1225,13 @@ static int force_blocks(Ctx *c) {
     return blocks < maxb ? blocks : maxb;
 }
 
-template <bool MIXED, int NI, int MODE, bool STATS, bool BATCHED>
+template <bool MIXED, int NI, int MODE, bool STATS, bool BATCHED, bool PX = false>
 static cudaError_t launch_one(Ctx *c, ForceArgs &a, cudaStream_t s) {
     const int warps = c->warps;
     const size_t sm = smem_bytes<MIXED, NI>(warps);
-    const int blocks = force_blocks<MIXED, NI, MODE, STATS, BATCHED>(c);
+    const int blocks = force_blocks<MIXED, NI, MODE, STATS, BATCHED, PX>(c);
     if (blocks * warps > c->nwarp_used) c->nwarp_used = blocks * warps;
-    k_force<MIXED, NI, MODE, STATS, BATCHED><<<blocks, warps * 32, sm, s>>>(a);
+    k_force<MIXED, NI, MODE, STATS, BATCHED, PX><<<blocks, warps * 32, sm, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1189,6 +1243,12 @@ static cudaError_t launch_mode(Ctx *c, ForceArgs &a, cudaStream_t s, bool stats)
         if (c->nbox > 0) {
             if (!MIXED || stats) return launch_one<MIXED, NI, MODE, true, true>(c, a, s);
             return launch_one<MIXED, NI, MODE, (MIXED ? false : true), true>(c, a, s);
+        }
+    }
+    if constexpr (MIXED && MODE == kAtomic) {
+        if (a.pairx) {   // two-cell tasks (2D)
+            if (stats) return launch_one<true, NI, kAtomic, true, false, true>(c, a, s);
+            return launch_one<true, NI, kAtomic, false, false, true>(c, a, s);
         }
     }
     if (!MIXED || stats) return launch_one<MIXED, NI, MODE, true, false>(c, a, s);
@@ -1219,6 +1279,7 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
     a.kx = c->kx; a.ky = c->ky; a.kz = c->kz;
     a.warp_acc = c->d_warp_acc; a.warp_pairs = c->d_warp_pairs;
     a.group = 0; a.colour = 0;
+    a.pairx = 0;
     a.stats = stats ? 1 : 0;
     a.boxes = c->d_boxes;
     a.cell_box = c->d_cell_box;
@@ -1260,6 +1321,11 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
         e = cudaMemsetAsync(c->fx, 0, 3 * nbytes, s);
         if (e) return e;
         a.ntasks = c->g.ncell;   // a batch: the total cell count of all boxes
+        if (MIXED && c->nbox == 0 && c->g.dims == 2) {
+            // sparse 2D cells: two x-adjacent cells per task (half the tasks)
+            a.pairx = 1;
+            a.ntasks = ((c->g.nc[0] + 1) / 2) * c->g.nc[1];
+        }
         e = launch_mode<MIXED, NI, kAtomic>(c, a, s, stats);
         ++*launches;
     } else if (sched == LC_SCHED_BUFFER) {
@@ -1410,6 +1476,8 @@ static cudaError_t attrs_for() {
     const int bytes = (int)smem_bytes<MIXED, NI>(8);
     if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kColour, STATS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
     if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kAtomic, STATS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    if constexpr (MIXED)
+        if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kAtomic, STATS, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
     if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kFullShell, STATS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
     if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kBuffer, STATS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
     if constexpr (NI == 16) {
