@@ -84,3 +84,37 @@ def test_size_limits_are_checked_on_the_host(so):
     assert so.lc_create_2d(small2, 2.5, 10, 1, ctypes.byref(h)) == 2
     assert so.lc_create_2d(None, 2.5, 10, 1, ctypes.byref(h)) == 1
     assert h.value is None
+
+
+def test_header_is_plain_c_and_links(so, tmp_path):
+    """A C99 program that calls the boundary compiles against include/lc.h
+    with warnings as errors and links against liblc.so (no C++ in the ABI)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_lc.c"
+    src.write_text("""
+#include <stdint.h>
+#include <stddef.h>
+#include "lc.h"
+int main(void) {
+    const double box[3] = {12.0, 12.0, 12.0};
+    lc_ctx *ctx = NULL;
+    double pos[3] = {1.0, 1.0, 1.0}, u, k, w;
+    int64_t np;
+    if (lc_create(box, 2.5, 1, LC_PREC_MIXED, &ctx) != LC_OK) return 1;
+    lc_set_state(ctx, pos, NULL, NULL, 0, NULL);
+    lc_forces(ctx, LC_SCHED_ATOMIC, NULL);
+    lc_verlet_step(ctx, 0.005, 2, LC_SCHED_LIST, NULL);
+    lc_energy_virial(ctx, &u, &k, &w, &np, NULL);
+    lc_destroy(ctx);
+    return 0;
+}
+""")
+    lib = so._name
+    out = tmp_path / "use_lc"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        lib, "-o", str(out)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
