@@ -1,7 +1,8 @@
 """The largest particle count a context accepts (n = 2^26 - 1, 67.1M
-particles, about 12 GB on the device): binning invariants, forces against
-per-particle oracle sums on a sample, Newton's third law; one particle more is
-refused."""
+particles, about 12 GB on the device; 45 GB with the Verlet lists): binning
+invariants, forces of the link-cell sweep and of the lists against
+per-particle oracle sums on a sample, Newton's third law, the same pair count
+on both paths; one particle more is refused."""
 import math
 
 import numpy as np
@@ -40,3 +41,12 @@ def test_max_particle_count(lc):
     assert np.abs(f[ids] - fref).max() <= 1e-5 * scale + 1e-9
     assert np.abs(f.sum(0)).max() < 1e-6 * n       # Newton's third law
     assert npairs > 0 and math.isfinite(u) and u < 0
+    # the Verlet lists at the same size: entries slot << 6 use all 32 bits
+    with lc.Box(box, RC, n, "mixed") as g:
+        g.set_state(pos)
+        g.forces("list")
+        fl = g.get("forces")
+        _, _, _, npairs_list = g.energy()
+        info = g.list_info()
+    assert npairs_list == npairs and info["long_rows"] == 0
+    assert np.abs(fl[ids] - fref).max() <= 1e-5 * scale + 1e-9
