@@ -1081,29 +1081,37 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force_dag(ForceArgs a, D
     le.s12 = make_float2(0.f, 0.f);
     le.d6 = le.d12 = 0.0;
     le.pairs = 0;
+    int next = -1;   // a successor this warp made ready and runs itself (continuation)
     for (;;) {
-        int pos = 0;
-        if (lane == 0) pos = atomicAdd(d.ctrl + 0, 1);
-        pos = __shfl_sync(kFull, pos, 0);
-        if (pos >= d.ntasks) break;
-        int tid = -1;
-        if (lane == 0) {
-            const unsigned long long t0 = global_ns();
-            bool gave_up = true;
-            for (unsigned it = 0; it < kDagMaxSpins; ++it) {
-                tid = ld_acquire(d.queue + pos);
-                if (tid >= 0) { gave_up = false; break; }
-                if ((it & 15) == 15) {
-                    if (ld_acquire(d.err) & kErrTimeout) break;              // another warp gave up
-                    if ((long long)(global_ns() - t0) > d.wait_ns) break;
+        int tid = next;
+        next = -1;
+        if (tid < 0) {
+            int pos = 0;
+            if (lane == 0) pos = atomicAdd(d.ctrl + 0, 1);
+            pos = __shfl_sync(kFull, pos, 0);
+            if (pos >= d.ntasks) break;
+            if (lane == 0) {
+                // wait for a task to be published at this slot, or for every
+                // task to be done (tasks run as continuations are never
+                // published, so the last slots stay empty)
+                const unsigned long long t0 = global_ns();
+                bool gave_up = true;
+                for (unsigned it = 0; it < kDagMaxSpins; ++it) {
+                    tid = ld_acquire(d.queue + pos);
+                    if (tid >= 0) { gave_up = false; break; }
+                    if (ld_acquire(d.ctrl + 3) >= d.ntasks) { gave_up = false; break; }   // all done
+                    if ((it & 15) == 15) {
+                        if (ld_acquire(d.err) & kErrTimeout) break;              // another warp gave up
+                        if ((long long)(global_ns() - t0) > d.wait_ns) break;
+                    }
+                    __nanosleep(200);
                 }
-                __nanosleep(200);
+                if (gave_up) { atomicOr(d.err, kErrTimeout); tid = -1; }
             }
-            if (gave_up) { atomicOr(d.err, kErrTimeout); tid = -1; }
+            tid = __shfl_sync(kFull, tid, 0);
+            __syncwarp();               // order the lanes' reads after lane 0's acquire
+            if (tid < 0) break;
         }
-        tid = __shfl_sync(kFull, tid, 0);
-        __syncwarp();                   // order the lanes' reads after lane 0's acquire
-        if (tid < 0) break;
         if (d.trace && lane == 0) d.trace[2 * tid] = atomicAdd(d.ctrl + 2, 1);
         const int code = d.task[tid];
         const TaskCells tc = dag_task(a, code >> 4, code & 15);
@@ -1120,10 +1128,26 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force_dag(ForceArgs a, D
         const int e1 = d.succ_start[tid + 1];
         for (int e = d.succ_start[tid] + lane; e < e1; e += kWarp) {
             const int sc = d.succ[e];
-            if (atomicSub(d.cnt + sc, 1) == 1) {
+            const bool ready = atomicSub(d.cnt + sc, 1) == 1;
+            // the first ready successor (lowest lane, first round) becomes
+            // this warp's next task; the others are published
+            const unsigned m = __ballot_sync(__activemask(), ready);
+            const bool keep = ready && next < 0 && lane == __ffs(m) - 1;
+            if (ready && !keep) {
                 const int p = atomicAdd(d.ctrl + 1, 1);
                 st_release(d.queue + p, sc);
             }
+            const int kept = __shfl_sync(__activemask(), keep ? sc : -1, m ? __ffs(m) - 1 : 0);
+            if (next < 0 && m) next = kept;
+        }
+        next = __shfl_sync(kFull, next, 0);
+        if (lane == 0) atomicAdd(d.ctrl + 3, 1);   // tasks done
+        if (next >= 0) {
+            // the other predecessors fenced their writes before their
+            // decrements, which the last decrement observed: fence here
+            // before reading them (the queued path's acquire load)
+            __threadfence();
+            __syncwarp();
         }
     }
     double s6 = MIXED ? (f32_to_f64_bits(le.s6.x) - f32_to_f64_bits(le.s6.y)) : le.d6;
