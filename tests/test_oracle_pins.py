@@ -5,7 +5,7 @@ sign in the pair force (closed form, finite differences), a wrong image or
 wrap (boundary pair, translation invariance, O(N^2) == link-cell), a missed or
 doubled neighbour cell (FCC shell sums, pair counts), an asymmetric update
 (Newton's third law), a wrong integrator step (energy conservation,
-time reversibility), a wrong sort (binning invariants), an unsafe colouring
+time reversibility, a two-body trajectory against an independent ODE solver), a wrong sort (binning invariants), an unsafe colouring
 (phase write sets).
 """
 import itertools
@@ -202,6 +202,37 @@ def test_verlet_energy_conservation_and_reversibility():
     dx -= b["box"] * np.rint(dx / b["box"])
     assert np.abs(dx).max() < 1e-9
     assert np.abs(-v2 - b["vel"]).max() < 1e-9
+
+
+def test_verlet_two_body_trajectory_converges_at_second_order():
+    """Two particles far from every image (box 10, r_c 2.5): the oracle's
+    velocity Verlet trajectory approaches the solution of Newton's equations
+    for the closed-form pair force, integrated by scipy's DOP853 (8th order,
+    rtol 1e-13), with the error falling four-fold per halved step.  A kick of
+    dt instead of dt/2, a stale force in the closing kick or a sign slip gives
+    order one or a diverging error."""
+    from scipy.integrate import solve_ivp
+
+    L = np.array([10.0, 10.0, 10.0])
+    p = np.array([[4.4, 5.0, 5.0], [5.7, 5.1, 5.0]])
+    v = np.array([[0.3, 0.1, 0.0], [-0.3, -0.1, 0.05]])
+
+    def rhs(t, y):
+        d = y[0:3] - y[3:6]
+        r = np.linalg.norm(d)
+        f0 = -lj_du(r) * d / r
+        return np.concatenate([y[6:], f0, -f0])
+
+    T = 0.6
+    ref = solve_ivp(rhs, (0.0, T), np.concatenate([p.ravel(), v.ravel()]), method="DOP853",
+                    rtol=1e-13, atol=1e-14).y[:, -1]
+    errs = []
+    for n in (150, 300, 600):
+        x, vv, _, _ = oracle.verlet(p, v, L, RC, T / n, n)
+        errs.append(max(np.abs(x.ravel() - ref[:6]).max(), np.abs(vv.ravel() - ref[6:]).max()))
+    assert errs[0] < 2e-4
+    for a, b in zip(errs, errs[1:]):
+        assert 3.8 < a / b < 4.2
 
 
 def test_binning_invariants():
