@@ -199,7 +199,7 @@ static cudaError_t alloc_common(Ctx *c) {
     c->nwarp_max = c->num_sms * 64;
     if ((e = upload_stencil(st, st2)) || (e = alloc_state(&c->cur, n)) || (e = alloc_state(&c->nxt, n)) ||
         (e = dalloc(&c->d_cell, N)) || (e = dalloc(&c->d_rank, N)) || (e = dalloc(&c->d_count, NC)) ||
-        (e = dalloc(&c->d_start, NC + 1)) || (e = dalloc(&c->d_src, N)) || (e = dalloc(&c->d_key, N)) ||
+        (e = dalloc(&c->d_start, 2 * (NC + 1))) || (e = dalloc(&c->d_src, N)) || (e = dalloc(&c->d_key, N)) ||
         (e = dalloc(&c->d_blocksums, (size_t)ntiles + 1)) || (e = dalloc(&c->d_colour, NC)) ||
         (e = dalloc(&c->d_p4, N)) || (e = dalloc(&c->fx, 3 * N)) || (e = dalloc(&c->kx, 3 * N)) ||
         (e = dalloc(&c->d_warp_acc, 4 * (size_t)c->nwarp_max)) || (e = dalloc(&c->d_warp_pairs, (size_t)c->nwarp_max)) ||
@@ -214,6 +214,7 @@ static cudaError_t alloc_common(Ctx *c) {
     c->ky = c->kx + N; c->kz = c->kx + 2 * N;
     cudaStream_t s = 0;
     if ((e = cudaMemsetAsync(c->d_result, 0, 8 * sizeof(double), s)) ||   // energies, pair count, flags
+        (e = cudaMemsetAsync(c->d_blocksums, 0, ((size_t)ntiles + 1) * sizeof(int), s)) ||   // scan ticket
         (e = cudaMemsetAsync(c->fx, 0, 3 * N * sizeof(double), s)))
         return e;
     return cudaSuccess;

@@ -3,8 +3,10 @@
 //
 //   k_cellid      wrap, cell index, count per cell (warp-aggregated atomics;
 //                 the atomic's return value gives a provisional rank)
-//   k_scan_*      exclusive prefix sum of the counts -> cell start
-//   k_scatter     provisional slot start[cell] + rank: source index and ID
+//   k_scan_tiles_ticket  exclusive prefix sum of the counts per tile; the
+//                 last block scans the tile totals
+//   k_scatter_starts  provisional slot start[cell] + rank: source index and
+//                 ID; the final cell starts
 //   k_rank_gather one thread per slot: final rank = number of the cell's
 //                 particles with a smaller ID (so the result does not depend
 //                 on the order in which the atomics were served); gather the
@@ -96,11 +98,12 @@ __global__ void k_cellid(Grid g1, const BoxDev *__restrict__ boxes, const unsign
     }
 }
 
-// Block-level exclusive scan of kScanTile counts; block totals to partial[].
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(int ncell, const int *__restrict__ count,
-                                                            int *__restrict__ start, int *__restrict__ partial) {
+// Block-level exclusive scan of the kScanTile counts of tile `tile` into
+// out[]; returns the tile's total (valid in every thread).
+__device__ __forceinline__ int scan_tile(int tile, int ncell, const int *__restrict__ count, int *__restrict__ out) {
     __shared__ int warp_tot[kScanThreads / 32];
-    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    __shared__ int tile_tot;
+    const int base = tile * kScanTile + threadIdx.x * kScanItems;
     int v[kScanItems];
     int sum = 0;
 #pragma unroll
@@ -127,20 +130,21 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(int ncell, const in
             if (lane >= m) ti += u;
         }
         warp_tot[lane] = ti - t;   // exclusive
-        if (lane == 31) partial[blockIdx.x] = ti;
+        if (lane == 31) tile_tot = ti;
     }
     __syncthreads();
     int run = warp_tot[wid] + inc - sum;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        if (base + k < ncell) start[base + k] = run;
+        if (base + k < ncell) out[base + k] = run;
         run += v[k];
     }
+    return tile_tot;
 }
 
-// Exclusive scan of the tile totals (one block; loops if there are more
-// tiles than threads).
-__global__ void __launch_bounds__(kScanThreads) k_scan_partials(int ntiles, int *__restrict__ partial) {
+// In-place exclusive scan of partial[0, ntiles) by one block (loops if there
+// are more tiles than threads).
+__device__ __forceinline__ void scan_partials(int ntiles, int *partial) {
     __shared__ int warp_tot[kScanThreads / 32];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_partials(int ntiles, int 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int b0 = 0; b0 < ntiles; b0 += kScanThreads) {
         int i = b0 + threadIdx.x;
-        int v = i < ntiles ? partial[i] : 0;
+        int v = i < ntiles ? __ldcg(&partial[i]) : 0;
         int inc = v;
 #pragma unroll
         for (int m = 1; m < 32; m <<= 1) {
@@ -176,6 +180,40 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_partials(int ntiles, int 
     }
 }
 
+// Tile scans with the tile totals to partial[] (three-pass scan, with
+// k_scan_partials and k_scan_add).
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(int ncell, const int *__restrict__ count,
+                                                            int *__restrict__ start, int *__restrict__ partial) {
+    const int tot = scan_tile(blockIdx.x, ncell, count, start);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_partials(int ntiles, int *__restrict__ partial) {
+    scan_partials(ntiles, partial);
+}
+
+// Tile scans into local[] and the tile totals to partial[]; the block that
+// finishes last (a ticket counter, no waiting) scans the totals in place, so
+// partial[k] becomes the start of tile k, and resets the ticket for the next
+// launch.  Cell c then starts at local[c] + partial[c / kScanTile], which
+// k_scatter writes out.
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles_ticket(int ncell, const int *__restrict__ count,
+                                                                   int *__restrict__ local, int *partial,
+                                                                   unsigned *ticket) {
+    __shared__ bool last;
+    const int tot = scan_tile(blockIdx.x, ncell, count, local);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = tot;
+        __threadfence();   // the total is visible before the ticket is taken
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();       // every other block's total is visible
+    scan_partials(gridDim.x, partial);
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
 __global__ void k_scan_add(int ncell, int n, int *__restrict__ start, const int *__restrict__ partial) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x)
         start[c] += partial[c / kScanTile];
@@ -190,6 +228,25 @@ __global__ void k_scatter(int n, const int *__restrict__ cell, const int *__rest
         src[t] = s;
         key[t] = id[s];
     }
+}
+
+// k_scatter after the two-pass scan: the cell start is the tile-local start
+// plus the tile's start; the same threads then write every cell's final
+// start (and start[ncell] = n).
+__global__ void k_scatter_starts(int n, int ncell, const int *__restrict__ cell, const int *__restrict__ rank,
+                                 const int *__restrict__ local, const int *__restrict__ partial,
+                                 const int *__restrict__ id, int *__restrict__ src, int *__restrict__ key,
+                                 int *__restrict__ start) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += stride) {
+        const int c = cell[s];
+        const int t = local[c] + partial[c / kScanTile] + rank[s];
+        src[t] = s;
+        key[t] = id[s];
+    }
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += stride)
+        start[c] = local[c] + partial[c / kScanTile];
+    if (blockIdx.x == 0 && threadIdx.x == 0) start[ncell] = n;
 }
 
 // One thread per slot t of the new order.  Rank = number of the cell's
@@ -298,12 +355,15 @@ cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches, int kicks, double 
         else b ? cellid_launch<true, 2>(c, grid_n, dr, s) : cellid_launch<false, 2>(c, grid_n, dr, s);
         ++*launches;
     }
-    k_scan_tiles<<<ntiles, kScanThreads, 0, s>>>(ncell, c->d_count, c->d_start, c->d_blocksums);
-    k_scan_partials<<<1, kScanThreads, 0, s>>>(ntiles, c->d_blocksums);
-    k_scan_add<<<c->num_sms * 4, 256, 0, s>>>(ncell, n, c->d_start, c->d_blocksums);
-    *launches += 3;
+    // two-pass scan: tile scans (the last tile block scans the tile totals),
+    // then the starts completed inside k_scatter_starts
+    int *local = c->d_start + (ncell + 1);
+    unsigned *ticket = reinterpret_cast<unsigned *>(c->d_blocksums + ntiles);
+    k_scan_tiles_ticket<<<ntiles, kScanThreads, 0, s>>>(ncell, c->d_count, local, c->d_blocksums, ticket);
+    k_scatter_starts<<<grid_n, 256, 0, s>>>(n, ncell, c->d_cell, c->d_rank, local, c->d_blocksums, c->cur.id,
+                                            c->d_src, c->d_key, c->d_start);
+    *launches += 2;
     if (n > 0) {
-        k_scatter<<<grid_n, 256, 0, s>>>(n, c->d_cell, c->d_rank, c->d_start, c->cur.id, c->d_src, c->d_key);
         static int per_sm_b = 0, per_sm_s = 0;
         if (c->nbox > 0)
             k_rank_gather<true><<<one_wave(c, k_rank_gather<true>, &per_sm_b), 256, 0, s>>>(
@@ -313,7 +373,7 @@ cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches, int kicks, double 
             k_rank_gather<false><<<one_wave(c, k_rank_gather<false>, &per_sm_s), 256, 0, s>>>(
                 c->g, nullptr, nullptr, n, c->prec == LC_PREC_MIXED, c->d_start, c->d_count, c->d_cell, c->d_src,
                 c->d_key, c->cur, c->nxt, c->d_p4);
-        *launches += 2;
+        *launches += 1;
     }
     e = cudaGetLastError();
     if (e) return e;
