@@ -355,7 +355,7 @@ lc_status lc_batch_info(const lc_ctx *ctx, int32_t *nbox, int64_t *total_particl
  *               ascending ID inside a cell (the same arrays as lc_get's
  *               CELL_COUNT / CELL_START / PERM after lc_bin)
  * Work is queued on `stream`; the call does not synchronise.  Its scratch is
- * one fixed array of device memory inside the library (about 21 MB, held by
+ * one fixed array of device memory inside the library (about 25 MB, held by
  * every GPU that loads the library until the process exits), so
  * n <= 1,048,576 and ncell <= 1,048,576 (LC_ERR_TOO_LARGE otherwise).  The
  * array's device address is looked up on the first call on each device,

@@ -23,10 +23,6 @@
 
 namespace lc {
 
-constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 4;
-constexpr int kScanTile = kScanThreads * kScanItems;
-
 // BATCHED: slot s belongs to box slot_box[s] (boxes keep their slot ranges),
 // whose grid gives the local cell; the global cell adds the box's offset.
 // KICKS: velocity-Verlet updates fused in front of the cell index (the
@@ -180,23 +176,11 @@ __device__ __forceinline__ void scan_partials(int ntiles, int *partial) {
     }
 }
 
-// Tile scans with the tile totals to partial[] (three-pass scan, with
-// k_scan_partials and k_scan_add).
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(int ncell, const int *__restrict__ count,
-                                                            int *__restrict__ start, int *__restrict__ partial) {
-    const int tot = scan_tile(blockIdx.x, ncell, count, start);
-    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_scan_partials(int ntiles, int *__restrict__ partial) {
-    scan_partials(ntiles, partial);
-}
-
 // Tile scans into local[] and the tile totals to partial[]; the block that
 // finishes last (a ticket counter, no waiting) scans the totals in place, so
 // partial[k] becomes the start of tile k, and resets the ticket for the next
 // launch.  Cell c then starts at local[c] + partial[c / kScanTile], which
-// k_scatter writes out.
+// k_scatter_starts writes out.
 __global__ void __launch_bounds__(kScanThreads) k_scan_tiles_ticket(int ncell, const int *__restrict__ count,
                                                                    int *__restrict__ local, int *partial,
                                                                    unsigned *ticket) {
@@ -214,25 +198,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles_ticket(int ncell, c
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
-__global__ void k_scan_add(int ncell, int n, int *__restrict__ start, const int *__restrict__ partial) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x)
-        start[c] += partial[c / kScanTile];
-    if (blockIdx.x == 0 && threadIdx.x == 0) start[ncell] = n;
-}
-
-__global__ void k_scatter(int n, const int *__restrict__ cell, const int *__restrict__ rank,
-                          const int *__restrict__ start, const int *__restrict__ id, int *__restrict__ src,
-                          int *__restrict__ key) {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        const int t = start[cell[s]] + rank[s];
-        src[t] = s;
-        key[t] = id[s];
-    }
-}
-
-// k_scatter after the two-pass scan: the cell start is the tile-local start
-// plus the tile's start; the same threads then write every cell's final
-// start (and start[ncell] = n).
+// Provisional slot of every particle (cell start + the rank its count
+// atomic returned): its source index and ID (identity when id is null).
+// The cell start is the tile-local start plus the tile's start; the same
+// threads then write every cell's final start (and start[ncell] = n).
 __global__ void k_scatter_starts(int n, int ncell, const int *__restrict__ cell, const int *__restrict__ rank,
                                  const int *__restrict__ local, const int *__restrict__ partial,
                                  const int *__restrict__ id, int *__restrict__ src, int *__restrict__ key,
@@ -242,7 +211,7 @@ __global__ void k_scatter_starts(int n, int ncell, const int *__restrict__ cell,
         const int c = cell[s];
         const int t = local[c] + partial[c / kScanTile] + rank[s];
         src[t] = s;
-        key[t] = id[s];
+        key[t] = id ? id[s] : s;
     }
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += stride)
         start[c] = local[c] + partial[c / kScanTile];

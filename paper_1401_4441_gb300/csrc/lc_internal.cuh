@@ -233,11 +233,19 @@ cudaError_t launch_list_forces(Ctx *c, cudaStream_t s, bool stats, int *launches
 cudaError_t capture_list_steps(Ctx *c, double dt, int nsteps, cudaGraphExec_t *out, int *launches);
 cudaError_t init_force_kernels();
 
-// scan kernels of the binning (lc_bin.cu), also launched by lc_noalloc.cu
-__global__ void k_scan_tiles(int ncell, const int *__restrict__ count, int *__restrict__ start,
-                             int *__restrict__ partial);
-__global__ void k_scan_partials(int ntiles, int *__restrict__ partial);
-__global__ void k_scan_add(int ncell, int n, int *__restrict__ start, const int *__restrict__ partial);
+// cell-start scan of the binning (lc_bin.cu), also launched by lc_noalloc.cu:
+// tiles of kScanTile counts, one block of kScanThreads each; partial[] holds
+// one int per tile, ticket one zero-initialised counter (reset by the
+// kernel); start[] needs ncell + 1 ints; id == nullptr: identity IDs
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+__global__ void k_scan_tiles_ticket(int ncell, const int *__restrict__ count, int *__restrict__ local, int *partial,
+                                    unsigned *ticket);
+__global__ void k_scatter_starts(int n, int ncell, const int *__restrict__ cell, const int *__restrict__ rank,
+                                 const int *__restrict__ local, const int *__restrict__ partial,
+                                 const int *__restrict__ id, int *__restrict__ src, int *__restrict__ key,
+                                 int *__restrict__ start);
 
 // ---- small device helpers ----------------------------------------------------
 // v^2 of one particle, each operation rounded once (no contraction), and the

@@ -12,7 +12,7 @@
 // library holds until the process exits.
 //
 // Limits: at most kNoAllocMaxParticles particles and kNoAllocMaxCells cells
-// per call (about 21 MB of device memory in total).  All calls share the one
+// per call (about 25 MB of device memory in total).  All calls share the one
 // array and it keeps the contents of the last call: calls that overlap on the
 // GPU (different streams without ordering, or several host threads) race.
 #include <cuda_runtime.h>
@@ -27,7 +27,7 @@ namespace lc {
 
 constexpr int64_t kNoAllocMaxParticles = int64_t(1) << 20;
 constexpr int64_t kNoAllocMaxCells = int64_t(1) << 20;
-constexpr int kNoAllocTiles = (int)((kNoAllocMaxCells + 4095) / 4096) + 1;
+constexpr int kNoAllocTiles = (int)((kNoAllocMaxCells + kScanTile - 1) / kScanTile) + 1;
 constexpr int kMaxDevices = 64;
 
 struct NoAllocScratch {
@@ -36,7 +36,9 @@ struct NoAllocScratch {
     int src[kNoAllocMaxParticles];
     int key[kNoAllocMaxParticles];
     int start[kNoAllocMaxCells + 1];
+    int local[kNoAllocMaxCells + 1];
     int partial[kNoAllocTiles];
+    unsigned ticket;   // zero at load; the scan resets it after each use
 };
 
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
@@ -77,15 +79,6 @@ __global__ void k_na_cellid(Grid g, int n, const double *__restrict__ pos, int *
             cell[s] = c;
             rank[s] = base + __popc(peers & ((1u << lane) - 1u));
         }
-    }
-}
-
-__global__ void k_na_scatter(int n, const int *__restrict__ cell, const int *__restrict__ rank,
-                             const int *__restrict__ start, int *__restrict__ src, int *__restrict__ key) {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        const int t = start[cell[s]] + rank[s];
-        src[t] = s;
-        key[t] = s;
     }
 }
 
@@ -146,7 +139,7 @@ extern "C" lc_status lc_bin_noalloc(const double *pos, int64_t n, const double b
     make_grid(&g, box, rc);
     const int ncell = g.ncell;
     const int nn = (int)n;
-    const int ntiles = (ncell + 4095) / 4096;
+    const int ntiles = (ncell + kScanTile - 1) / kScanTile;
     cudaStream_t s = (cudaStream_t)stream;
     int nsm = 0, dev = 0;
     cudaGetDevice(&dev);
@@ -157,11 +150,10 @@ extern "C" lc_status lc_bin_noalloc(const double *pos, int64_t n, const double b
         return LC_ERR_CUDA;
     }
     if (nn > 0) k_na_cellid<<<grid_n, 256, 0, s>>>(g, nn, pos, sc->cell, sc->rank, cell_count);
-    k_scan_tiles<<<ntiles, 1024, 0, s>>>(ncell, cell_count, sc->start, sc->partial);
-    k_scan_partials<<<1, 1024, 0, s>>>(ntiles, sc->partial);
-    k_scan_add<<<grid_n, 256, 0, s>>>(ncell, nn, sc->start, sc->partial);
+    k_scan_tiles_ticket<<<ntiles, kScanThreads, 0, s>>>(ncell, cell_count, sc->local, sc->partial, &sc->ticket);
+    k_scatter_starts<<<grid_n, 256, 0, s>>>(nn, ncell, sc->cell, sc->rank, sc->local, sc->partial, nullptr, sc->src,
+                                            sc->key, sc->start);
     if (nn > 0) {
-        k_na_scatter<<<grid_n, 256, 0, s>>>(nn, sc->cell, sc->rank, sc->start, sc->src, sc->key);
         k_na_rank<<<grid_n, 256, 0, s>>>(nn, sc->start, cell_count, sc->cell, sc->src, sc->key, perm);
     }
     e = cudaGetLastError();
