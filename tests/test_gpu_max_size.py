@@ -27,11 +27,13 @@ def test_max_particle_count(lc):
         g.set_state(pos)
         g.bin()
         counts = g.get("cell_count")
+        starts = g.get("cell_start")
         perm = g.get("perm")
         g.forces("atomic")
         f = g.get("forces")
         u, k, w, npairs = g.energy()
     assert int(counts.sum()) == n
+    assert starts[0] == 0 and np.array_equal(np.diff(starts), counts[:-1])   # exclusive scan, 1243 tiles
     seen = np.zeros(n, np.bool_)
     seen[perm] = True
     assert seen.all()                              # a permutation of the IDs

@@ -70,6 +70,16 @@ def test_binning_dense_cells(lc):
     check_bin(lc, pos, box)
 
 
+def test_binning_bit_exact_many_scan_tiles(lc):
+    """A dilute gas over 165^3 = 4.49M cells: 1097 scan tiles of 4096 cells,
+    more than the 1024 threads of the block that scans the tile totals (its
+    carry loop runs twice); most cells are empty."""
+    n = 200000
+    box = np.array([412.5, 412.5, 412.5])
+    pos = inputs.uniform(8, 0, 3 * n).reshape(n, 3) * box
+    check_bin(lc, pos, box)
+
+
 def test_binning_bit_exact_1m(lc):
     b = inputs.workload("liquid1m")
     check_bin(lc, b["pos"], b["box"])
