@@ -580,8 +580,10 @@ def run_gb300(args, dist):
 def run_dag(args, dist):
     """The force sweep as the paper's task program on the device (Sec. III,
     Sec. V, Sec. VI Strategy 2): the DAG of each task-creation order executed
-    by the dependency-counted device queue, next to the atomic schedule.
-    Prints one JSON line (an auxiliary measurement, not the headline)."""
+    by the dependency-counted device queue, next to the atomic schedule; for
+    a 2D workload also the cell creation order under the three stencil
+    orders of Fig. 5.  Prints one JSON line (an auxiliary measurement, not
+    the headline)."""
     import torch
     from paper_1401_4441_gb300 import build
     torch.cuda.set_device(dist.local)
@@ -620,12 +622,42 @@ def run_dag(args, dist):
                                 "speedup_bound": t / cp, "us_per_critical_task": 1e3 * ms / cp}
     for r in rows.values():
         r["pairs_per_s"] = npairs / (r["ms"] * 1e-3)
+    fig5 = None
+    if b.get("dims", 3) == 2:
+        # Fig. 5 on the device: the cell creation order under the paper's three
+        # stencil orders (in this library's stencil orientation), on a smaller
+        # 2D box (256 x 256 particles, 131 x 113 cells, 74k tasks) so that the
+        # serial order stays near one second per evaluation
+        s5 = inputs.tri_box(256, 256, 0.7, 0.5, seed=inputs.DEFAULT_SEED + 5, jitter=0.05)
+        g5 = lc.Box(s5["box"], rc, s5["pos"].shape[0], args.precision, dims=2)
+        try:
+            g5.set_state(torch.from_numpy(s5["pos"]).to(dev))
+            g5.forces("atomic")
+            _, _, _, np5 = g5.energy()
+            nc5, _, _ = g5.grid()
+            fig5 = {"cells": [int(nc5[0]), int(nc5[1])], "pairs": int(np5), "orders": {}}
+            for name, perm in (("naive", (0, 2, 3, 1, 4)), ("bad", (0, 2, 3, 4, 1)), ("opt", (1, 0, 4, 3, 2))):
+                g5.dag_stencil_order(perm)
+                t, e, cp = g5.dag_build("cell")
+                ms = timed(lambda: g5.dag_forces("cell"), reps=2)
+                _, _, _, np_ = g5.energy()
+                assert np_ == np5
+                fig5["orders"][name] = {"stencil_perm": list(perm), "ms": ms, "tasks": t, "critical_path": cp,
+                                        "speedup_bound": t / cp, "us_per_critical_task": 1e3 * ms / cp}
+            bad_ms = fig5["orders"]["bad"]["ms"]
+            for r in fig5["orders"].values():
+                r["measured_speedup_vs_bad"] = bad_ms / r["ms"]
+        finally:
+            g5.close()
     if dist.rank == 0:
-        print(json.dumps({"metric": "force evaluation time by task-DAG creation order", "unit": "ms",
-                          "higher_is_better": False, "n_gpus": dist.world, "precision": args.precision,
-                          "config": {"workload": b["name"], "particles": int(pos.shape[0]),
-                                     "l2": "flushed (512 MiB memset) before each timed call"},
-                          "pairs": int(npairs), "results": rows}), flush=True)
+        line = {"metric": "force evaluation time by task-DAG creation order", "unit": "ms",
+                "higher_is_better": False, "n_gpus": dist.world, "precision": args.precision,
+                "config": {"workload": b["name"], "particles": int(pos.shape[0]),
+                           "l2": "flushed (512 MiB memset) before each timed call"},
+                "pairs": int(npairs), "results": rows}
+        if fig5 is not None:
+            line["fig5_stencil_orders"] = fig5
+        print(json.dumps(line), flush=True)
 
 
 def main():

@@ -1398,6 +1398,12 @@ static cudaError_t launch_dag(Ctx *c, const DagDev *dd, long long wait_ns, int32
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int blocks = c->num_sms * per_sm;
     if (blocks > c->nwarp_max / warps) blocks = c->nwarp_max / warps;
+    // a DAG with little parallelism (tasks / critical path of a few, as in
+    // the cell-major creation orders) gets eight warps per unit of it, at
+    // least four blocks: fewer warps polling the queue shortens every hand-off
+    const double width = (double)dd->ntasks / (double)(dd->critical_path > 0 ? dd->critical_path : 1);
+    const double want = ceil(8.0 * width / warps);
+    if (want < (double)blocks) blocks = want < 4.0 ? (blocks < 4 ? blocks : 4) : (int)want;
     c->nwarp_used = blocks * warps;
     // every warp may wait for another one: all of them must be resident
     void *args[] = {&a, &d};
