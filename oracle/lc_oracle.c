@@ -273,7 +273,10 @@ int orc_lc_forces(int64_t n, const double *x, const double *y, const double *z,
     double *fs_ = (double *)calloc(3 * (size_t)(n > 0 ? n : 1), sizeof(double));
     int32_t ncol;
     int rcb = orc_bin(n, x, y, z, L, rc, cell_of, count, start, perm, colour, &ncol);
-    if (rcb) return rcb;
+    if (rcb) {
+        free(cell_of); free(count); free(start); free(perm); free(colour); free(xs); free(fs_);
+        return rcb;
+    }
     for (int64_t s = 0; s < n; ++s) {
         int32_t id = perm[s];
         xs[3 * s + 0] = orc_wrap(x[id], L[0]);
@@ -411,7 +414,10 @@ int orc_forces_sample(int64_t n, const double *x, const double *y, const double 
     int8_t *colour = (int8_t *)malloc((size_t)ncell);
     int32_t ncol;
     int rcb = orc_bin(n, x, y, z, L, rc, cell_of, count, start, perm, colour, &ncol);
-    if (rcb) return rcb;
+    if (rcb) {
+        free(cell_of); free(count); free(start); free(perm); free(colour);
+        return rcb;
+    }
     double rc2 = rc * rc;
     for (int64_t s = 0; s < nsample; ++s) {
         int64_t i = ids[s];
