@@ -157,6 +157,39 @@ def test_translation_invariance():
     assert U1 == pytest.approx(U2, rel=1e-11)
 
 
+def test_wrap_against_exact_modulo():
+    """orc_wrap returns a value in [0, L) within a couple of units in the last
+    place (of max(|x|, L)) of the exact real x mod L (rational arithmetic),
+    and x itself for x already in [0, L)."""
+    from fractions import Fraction
+    for L in (10.0, 7.6, 107.49419, 2.5 * 165):
+        xs = [0.0, -0.0, 1e-300, -1e-300, L, math.nextafter(L, 0.0), -L, 3.0 * L + 0.5, -2.5 * L, 0.5 * L,
+              1e6 + 0.123, -1e6 - 0.123, L * 1e-17, -L * 1e-17]
+        for x in xs:
+            y = oracle.wrap(x, L)
+            assert 0.0 <= y < L
+            if 0.0 <= x < L:
+                assert y == x
+                continue
+            ex = Fraction(x) - Fraction(L) * math.floor(Fraction(x) / Fraction(L))
+            tol = 2.0 * math.ulp(max(abs(x), L))
+            err = abs(Fraction(y) - ex)
+            err = min(err, abs(Fraction(L) - err))   # the same point of the circle
+            assert float(err) <= tol
+
+
+def test_grid_is_the_floor_of_l_over_rc():
+    """Cells per axis = floor(L / r_c) (exact for these values), refused when
+    an axis has fewer than 3 cells."""
+    from fractions import Fraction
+    for L, rc in (([10.0, 7.6, 12.7], 2.5), ([107.49419, 107.49419, 107.49419], 2.5), ([7.5, 7.5, 30.0], 2.5),
+                  ([7.4999, 9.0, 9.0], 2.5), ([485.29, 121.32, 121.32], 3.0)):
+        nc, bad = oracle.grid(np.array(L), rc)
+        ref = [math.floor(Fraction(v) / Fraction(rc)) for v in L]
+        assert list(nc) == ref
+        assert bad == (min(ref) < 3)
+
+
 def test_forces_sample_equals_the_definition():
     """The sampled per-particle sums (the 27 cells around the particle's own
     cell) against a numpy brute force of the definition: every j != i under
