@@ -1,7 +1,8 @@
 """The oracle's pins catch plausible slips.  Each mutant below is the
 oracle's C source with one deliberate mistake (a dropped factor, a wrong
 sign, a missed neighbour cell, a wrong periodic image, a wrong integrator
-step, a wrong virial), built with gcc on the CPU into a scratch directory;
+step, a wrong virial, an unstable or mislabelled binning, an unsafe colour),
+built with gcc on the CPU into a scratch directory;
 with the mutant loaded in place of the oracle library, at least one pin of
 test_oracle_pins.py must fail.  The unmutated oracle passes every pin (that
 file's own run)."""
@@ -32,6 +33,13 @@ MUTANTS = {
     "full_kick": ("double half = 0.5 * dt;", "double half = dt;"),
     # the virial without its r^2
     "virial": ("*w = *f * r2;", "*w = *f;"),
+    # IDs placed in descending order inside a cell (not stable by ID)
+    "unstable_bin": ("for (int64_t i = 0; i < n; ++i) {\n        int32_t c = cell_of[i];",
+                     "for (int64_t i = n - 1; i >= 0; --i) {\n        int32_t c = cell_of[i];"),
+    # cell index with x and y exchanged
+    "cell_index": ("int32_t c = cx + nc[0] * (cy + nc[1] * cz);", "int32_t c = cy + nc[1] * (cx + nc[0] * cz);"),
+    # the last cell of an odd periodic dimension coloured by parity alone
+    "odd_colour": ("if ((nc & 1) && c == nc - 1) return 2;", ""),
 }
 
 # cheap pins first; each is (name, callable)
@@ -44,6 +52,9 @@ PINS = [
     ("fcc_shells", pins.test_fcc_lattice_shell_sums),
     ("newton_nsq_lc", pins.test_newton_third_law_and_nsq_equals_lc),
     ("virial_identity", pins.test_virial_equals_sum_r_dot_f),
+    ("binning_by_hand", pins.test_binning_tiny_by_hand),
+    ("binning_invariants", pins.test_binning_invariants),
+    ("colour_odd_grid", lambda: pins.test_colour_phases_disjoint_and_complete((5, 4, 3))),
 ]
 
 
