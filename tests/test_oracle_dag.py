@@ -109,3 +109,44 @@ def test_loop_exchange_with_colouring_is_not_limited():
     assert s_large > 5 * s_small / 1.01 and s_large > 100
     cp3 = dag.critical_path(dag.build_dag(dag.loopex_tasks(D3, [(0, 0, 0)] + dag.half_shell_3d())))
     assert cp3 < 40
+
+
+def test_address_rule_by_hand():
+    """The dependency rule on parameter addresses, on a four-call program
+    worked out by hand: an input after an output depends on it (t1 on t0 via
+    a, t3 on t1 via b); an output depends on the earlier output of the same
+    address and on the inputs read since (t2 on t0 and t1 via a)."""
+    tasks = [((), ("a",)),            # t0: output a
+             (("a",), ("b",)),        # t1: input a, output b
+             ((), ("a",)),            # t2: output a
+             (("b",), ())]            # t3: input b
+    assert dag.build_dag(tasks) == [[], [0], [0, 1], [1]]
+
+
+def _reach(parents):
+    """reach[t] = the set of tasks with a path to t."""
+    reach = []
+    for ps in parents:
+        r = set(ps)
+        for p in ps:
+            r |= reach[p]
+        reach.append(r)
+    return reach
+
+
+@pytest.mark.parametrize("dims", [(6, 6), (5, 4), (4, 4, 4), (3, 5, 4)])
+def test_tasks_sharing_a_cell_are_ordered(dims):
+    """Sec. IV: both cells of a cell-cell task are inout, so any two tasks
+    that touch a common cell must be ordered by a path of the DAG (else they
+    race), in the cell-major and in the loop-exchanged creation order."""
+    stencil = dag.STENCIL_2D if len(dims) == 2 else [(0, 0, 0)] + dag.half_shell_3d()
+    for tasks in (dag.basic_order_tasks(dims, stencil), dag.loopex_tasks(dims, stencil)):
+        reach = _reach(dag.build_dag(tasks))
+        by_cell = {}
+        for t, (reads, writes) in enumerate(tasks):
+            for c in set(reads) | set(writes):
+                by_cell.setdefault(c, []).append(t)
+        for c, ts in by_cell.items():
+            for i, a in enumerate(ts):
+                for b in ts[i + 1:]:
+                    assert a in reach[b], (c, a, b)
