@@ -1,7 +1,8 @@
 """The oracle's pins catch plausible slips.  Each mutant below is the
 oracle's C source with one deliberate mistake (a dropped factor, a wrong
 sign, a missed neighbour cell, a wrong periodic image, a wrong integrator
-step, a wrong virial, an unstable or mislabelled binning, an unsafe colour),
+step, a wrong virial or energy, an unstable or mislabelled binning, an unsafe
+colour or phase grouping),
 built with gcc on the CPU into a scratch directory;
 with the mutant loaded in place of the oracle library, at least one pin of
 test_oracle_pins.py must fail.  The unmutated oracle passes every pin (that
@@ -40,6 +41,10 @@ MUTANTS = {
     "cell_index": ("int32_t c = cx + nc[0] * (cy + nc[1] * cz);", "int32_t c = cy + nc[1] * (cx + nc[0] * cz);"),
     # the last cell of an odd periodic dimension coloured by parity alone
     "odd_colour": ("if ((nc & 1) && c == nc - 1) return 2;", ""),
+    # the pair energy with the attractive term's sign flipped
+    "energy_sign": ("*u = 4.0 * s6 * (s6 - 1.0);", "*u = 4.0 * s6 * (s6 + 1.0);"),
+    # every half-shell offset put into group 0 (offsets of one parity pattern share a phase)
+    "one_group": ("while (used[g][pat]) ++g;", ""),
 }
 
 # cheap pins first; each is (name, callable)
@@ -55,6 +60,7 @@ PINS = [
     ("binning_by_hand", pins.test_binning_tiny_by_hand),
     ("binning_invariants", pins.test_binning_invariants),
     ("colour_odd_grid", lambda: pins.test_colour_phases_disjoint_and_complete((5, 4, 3))),
+    ("colour_even_grid", lambda: pins.test_colour_phases_disjoint_and_complete((4, 4, 4))),
 ]
 
 
