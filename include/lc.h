@@ -291,7 +291,9 @@ lc_status lc_dag_plan(const int32_t nc[3], lc_order order, const int32_t *perm, 
 lc_status lc_dag_stencil_order(lc_ctx *ctx, const int32_t *perm, int32_t nperm);
 
 /* One force evaluation by executing the DAG of `order` on the device: a
- * persistent kernel (cooperative launch, every warp resident) whose warps
+ * persistent kernel (cooperative launch, every warp resident; a DAG of little
+ * parallelism, tasks / critical path of a few, gets eight warps per unit of
+ * it and at least four blocks instead of the whole GPU) whose warps
  * claim queue slots, wait for a ready task, run it with plain writes to both
  * cells and release its successors (dependency counting).  Forces, energy,
  * virial and pair count as lc_forces.  wait_seconds (> 0) bounds every wait
