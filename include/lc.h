@@ -360,12 +360,17 @@ lc_status lc_batch_info(const lc_ctx *ctx, int32_t *nbox, int64_t *total_particl
  * one fixed array of device memory inside the library (about 25 MB, held by
  * every GPU that loads the library until the process exits), so
  * n <= 1,048,576 and ncell <= 1,048,576 (LC_ERR_TOO_LARGE otherwise).  The
- * array's device address is looked up on the first call on each device,
- * with that device current: make that first call before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race,
- * so order them on one stream.  Non-finite positions are binned into cell
- * 0 (no flag is reported).  Errors: LC_ERR_INVALID_ARG,
- * LC_ERR_BOX_TOO_SMALL, LC_ERR_TOO_LARGE, LC_ERR_CUDA. */
+ * array's device address is looked up on the first call on each device
+ * and again on the first call in every new CUDA context of that device
+ * (after cudaDeviceReset, for example), with that device current: make
+ * those first calls before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU race, so order them on one stream.
+ * Non-finite positions are binned into cell 0 (no flag is reported).  If a
+ * CUDA error is already pending on entry (from the caller's earlier work)
+ * the call returns LC_ERR_CUDA, queues nothing and leaves that error
+ * pending; only errors raised by this call's own launches are cleared.
+ * Errors: LC_ERR_INVALID_ARG, LC_ERR_BOX_TOO_SMALL, LC_ERR_TOO_LARGE,
+ * LC_ERR_CUDA. */
 lc_status lc_bin_noalloc(const double *pos, int64_t n, const double box[3], double rc, int32_t *cell_count,
                          int32_t *cell_start, int32_t *perm, void *stream);
 

@@ -96,21 +96,56 @@ __global__ void k_na_rank(int n, const int *__restrict__ start, const int *__res
     }
 }
 
-// Device address of the scratch array, looked up once per device (with
-// that device current) and cached.
+// Device address of the scratch array, looked up with the device current
+// and cached per device together with the ID of the CUDA context it was
+// looked up in: after cudaDeviceReset (or with another context current) the
+// context ID differs and the address is looked up again, so a kernel never
+// gets an address from a context that no longer exists.  The context ID
+// comes from the driver's cuCtxGetCurrent / cuCtxGetId, reached through the
+// runtime's driver entry points (no link against the driver library).
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+static cudaError_t current_context_id(unsigned long long *id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) return e;
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cudaErrorNotSupported;
+        get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+        get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) return cudaErrorContextIsDestroyed;
+    return get_id(ctx, id) == 0 ? cudaSuccess : cudaErrorContextIsDestroyed;
+}
+
 static cudaError_t scratch_address(NoAllocScratch **out) {
     static std::mutex mu;
     static NoAllocScratch *addr[kMaxDevices] = {nullptr};
+    static unsigned long long ctx_of[kMaxDevices] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    unsigned long long ctx = 0;
+    if (addr[dev]) {
+        e = current_context_id(&ctx);
         if (e != cudaSuccess) return e;
+    }
+    if (!addr[dev] || ctx != ctx_of[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);   // also creates the context if needed
+        if (e != cudaSuccess) return e;
+        if ((e = current_context_id(&ctx)) != cudaSuccess) return e;
         addr[dev] = static_cast<NoAllocScratch *>(p);
+        ctx_of[dev] = ctx;
     }
     *out = addr[dev];
     return cudaSuccess;
@@ -132,6 +167,9 @@ extern "C" lc_status lc_bin_noalloc(const double *pos, int64_t n, const double b
     if (floor(box[0] / rc) * floor(box[1] / rc) * floor(box[2] / rc) > (double)kNoAllocMaxCells)
         return LC_ERR_TOO_LARGE;
 
+    // an error left pending by the caller's earlier work is not ours to
+    // clear: report it and leave it pending
+    if (cudaPeekAtLastError() != cudaSuccess) return LC_ERR_CUDA;
     NoAllocScratch *sc = nullptr;
     cudaError_t e = scratch_address(&sc);
     if (e != cudaSuccess) { cudaGetLastError(); return LC_ERR_CUDA; }

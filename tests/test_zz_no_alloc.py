@@ -74,3 +74,23 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(lc):
     assert fn(p, 10, big, RC, p, p, p, None) == 9
     small = (ctypes.c_double * 3)(7.0, 100.0, 100.0)
     assert fn(p, 10, small, RC, p, p, p, None) == 2
+
+
+def test_noalloc_empty_and_no_device_allocation(lc):
+    """n = 0 gives all-zero counts and starts; after a first call, further
+    calls leave the device's free memory unchanged (nothing is allocated)."""
+    torch = pytest.importorskip("torch")
+    a = inputs.fcc_box(4000, 0.8442, 0.72, jitter=0.05)
+    run_noalloc(lc, torch, a["pos"], a["box"])          # first call: symbol look-up, kernels loaded
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        code, count, start, perm = run_noalloc(lc, torch, a["pos"], a["box"])
+        assert code == 0
+    code, count, start, _ = run_noalloc(lc, torch, np.zeros((0, 3)), a["box"])
+    assert code == 0
+    assert not count.any() and not start.any()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    # the test's own output tensors come from torch's cache, not new driver memory
+    assert free1 == free0
