@@ -38,8 +38,12 @@ METRIC_LIST = "LJ pair interactions/s (Verlet lists with skin, velocity-Verlet s
 UNIT = "pairs/s"
 DT = 0.005
 RC = 2.5
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+# algorithmic bytes of one binning (lc_bin): read the FP64 state (x, v) and
+# the ID (52 B), write it in cell order (52 B) and the FP32 cell-local
+# coordinates (16 B) per particle; per cell its count and start
+BIN_BYTES_PER_PARTICLE = 120
+BIN_BYTES_PER_CELL = 8
 
 
 def dist_env():
@@ -87,7 +91,7 @@ class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, device_index):
         self.dev = device_index
@@ -97,7 +101,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
                  "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -117,23 +121,26 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
-        sm, smax, reasons = [], [], set()
+        sm, smax, load, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.lines:
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                clk, cmax, util = float(parts[1]), float(parts[2]), float(parts[9])
             except ValueError:
                 continue
-            for name, val in zip(names, parts[5:9]):
-                if val.lower() == "active":
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
+            sm.append(clk)
+            smax.append(cmax)
+            if util >= 50.0:   # a sample taken while the GPU was busy
+                load.append(clk)
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(name)
+        return {"sm_mhz": statistics.median(load) if load else (statistics.median(sm) if sm else None),
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "samples_under_load": len(load)}
 
 
 def half_shell_candidates(counts, nc, dims=3):
@@ -191,21 +198,75 @@ def oracle_box(w):
 
 def cpu_baseline(pos, box, rc, budget_s=12.0):
     """The FP64 oracle (as it stands) on this host: repeated link-cell force
-    evaluations of the same box for about budget_s seconds, one core."""
+    evaluations of the same box for about budget_s seconds, one core.
+    Returns the baseline and the oracle's (forces, U, W, pairs) of the box,
+    against which the precision report compares the GPU path."""
     import oracle
     x, y, z = (np.ascontiguousarray(pos[:, d]) for d in range(3))
     t0 = time.perf_counter()
-    evals, pairs = 0, 0
+    evals, pairs, ref = 0, 0, None
     while True:
-        _, _, _, npairs = oracle.lc_forces(x, y, z, box, rc)
+        f, U, W, npairs = oracle.lc_forces(x, y, z, box, rc)
+        if ref is None:
+            ref = (f, U, W, npairs)
         evals += 1
         pairs += npairs
         if time.perf_counter() - t0 > budget_s or evals >= 8:
             break
     dt = time.perf_counter() - t0
-    return {"value": pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    line = {"value": pairs / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{evals} FP64 link-cell force evaluations of the full {pos.shape[0]}-particle box "
                       f"({dt:.1f} s, single thread)"}
+    line["strategy1"] = strategy1_baseline(pos, box, rc)
+    return line, ref
+
+
+def strategy1_baseline(pos, box, rc, budget_s=8.0):
+    """The paper's Strategy 1 (Sec. VI, Fig. 6: loop exchange + 2-strided
+    colouring, plain writes) in OpenMP on all host cores, FP64: repeated
+    force evaluations of the same box for about budget_s seconds."""
+    try:
+        import baseline
+        cores = baseline.threads()
+        baseline.forces(pos[:1000], box, rc)          # build and first touch
+        t0 = time.perf_counter()
+        evals, pairs = 0, 0
+        while True:
+            _, _, _, npairs = baseline.forces(pos, box, rc)
+            evals += 1
+            pairs += npairs
+            if time.perf_counter() - t0 > budget_s or evals >= 20:
+                break
+        dt = time.perf_counter() - t0
+    except Exception as exc:   # no compiler or OpenMP on this host
+        return {"unavailable": f"{type(exc).__name__}: {exc}"}
+    return {"value": pairs / dt, "unit": UNIT, "cores": cores, "kind": "paper Strategy 1, OpenMP",
+            "sample": f"{evals} FP64 force evaluations of the full {pos.shape[0]}-particle box ({dt:.1f} s)",
+            "paper_context": "the paper reports near-perfect scaling of this strategy up to 32 threads on a "
+                             "32-core Cray XE6 node (OmpSs, synthetic fixed-duration tasks, Sec. VII); it "
+                             "prints no LJ throughput"}
+
+
+def precision_report(f, u, w, ref):
+    """Errors of one GPU force evaluation against the oracle's FP64
+    evaluation of the same positions: max and RMS over particles of
+    |dF_i| / RMS |F|, relative errors of U and W."""
+    fref, U, W, _ = ref
+    rms = math.sqrt(float((fref ** 2).sum(1).mean()))
+    err = np.sqrt(((f - fref) ** 2).sum(1))
+    return {"force_max_rel": float(err.max()) / rms, "force_rms_rel": math.sqrt(float((err ** 2).mean())) / rms,
+            "energy_rel": abs(u - U) / abs(U), "virial_rel": abs(w - W) / abs(W),
+            "against": "the oracle's FP64 link-cell evaluation of the same (initial) positions"}
+
+
+def oracle_drift(nsteps, rc):
+    """Relative energy drift |E(n) - E(0)| / |E(0)| of the oracle's FP64
+    velocity-Verlet run of the 4,000-particle FCC box (rho 0.8442, T 0.72)."""
+    import oracle
+    b = inputs.fcc_box(4000, 0.8442, 0.72)
+    _, _, _, e = oracle.verlet(b["pos"], b["vel"], b["box"], rc, DT, nsteps)
+    E = e[:, 0] + e[:, 1]
+    return abs(E[-1] - E[0]) / abs(E[0])
 
 
 def run_reference(args, dist):
@@ -287,18 +348,24 @@ def run_profile(args, dist):
 def run_batch(args, dist):
     """Batched configuration: 512 independent boxes (N log-uniform in
     [500, 50000], density U[0.5, 0.9], T U[0.7, 1.2], FCC + jitter 0.05)
-    stepped together (one launch per stage for all boxes, two-step CUDA graph),
-    mixed precision; compared with the plain FP64 path that steps each box
-    alone (its own context, per-box launches)."""
+    stepped together, mixed precision; the colour schedule runs as one
+    persistent launch fed by the device work queue over (colour, box, cells)
+    (lc_batch_step), the other schedules one launch per stage; two-step CUDA
+    graphs.  Compared with the plain FP64 path that steps each box alone (its
+    own context, per-box launches).  Under torchrun the boxes are partitioned
+    over the ranks (longest-first greedy on N) and the per-box energies are
+    gathered on rank 0: the total work is fixed (strong scaling)."""
     import torch
-    from paper_1401_4441_gb300 import build
+    from paper_1401_4441_gb300 import build, shard
     torch.cuda.set_device(dist.local)
     dev = torch.device("cuda", dist.local)
     if dist.rank == 0:
         build.build()
     dist.barrier()
     from paper_1401_4441_gb300 import lc
-    boxes = inputs.batch_boxes(seed=inputs.DEFAULT_SEED + 1000 * dist.rank)
+    all_boxes = inputs.batch_boxes(seed=inputs.DEFAULT_SEED)
+    mine = shard.partition_boxes([b["pos"].shape[0] for b in all_boxes], dist.world)[dist.rank]
+    boxes = [all_boxes[i] for i in mine]
     pos = np.concatenate([b["pos"] for b in boxes])
     vel = np.concatenate([b["vel"] for b in boxes])
     stream = torch.cuda.current_stream(dev)
@@ -306,21 +373,29 @@ def run_batch(args, dist):
     g = lc.Batch([b["box"] for b in boxes], RC, [b["pos"].shape[0] for b in boxes], args.precision)
     dpos, dvel = torch.from_numpy(pos).to(dev), torch.from_numpy(vel).to(dev)
     sched_ms = {}
-    for sch in ("atomic", "fullshell", "buffer"):
+    for sch in ("colour", "atomic", "fullshell", "buffer"):
         g.set_state(dpos, dvel)
         g.forces(sch)
         ts = []
         for _ in range(3):
+            flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream); g.forces(sch); e1.record(stream)
             torch.cuda.synchronize(dev)
             ts.append(e0.elapsed_time(e1))
         sched_ms[sch] = min(ts)
-    sched = min(sched_ms, key=sched_ms.get) if args.schedule in ("auto", "colour") else args.schedule
+    sched = min(sched_ms, key=sched_ms.get) if args.schedule == "auto" else args.schedule
+
+    def steps(k):
+        if sched == "colour":
+            g.step(DT, k)            # lc_batch_step: the device work queue
+        else:
+            g.verlet(DT, k, sched)
+
     g.set_state(dpos, dvel)
     g.forces(sched)
     _, _, _, np0 = g.energies()
-    g.verlet(DT, max(2, args.warmup), sched)
+    steps(max(2, args.warmup))
     torch.cuda.synchronize(dev)
     calls = [2] * (args.steps // 2) + ([1] if args.steps % 2 else [])
     clocks = ClockSampler(dist.local)
@@ -331,16 +406,19 @@ def run_batch(args, dist):
     for k in calls:
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream); g.verlet(DT, k, sched); e1.record(stream)
+        e0.record(stream); steps(k); e1.record(stream)
         evs.append((e0, e1))
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     ms = dist.max(sum(a.elapsed_time(b) for a, b in evs))
-    _, _, _, np1 = g.energies()
+    u1, k1, w1, np1 = g.energies()
     pairs = 0.5 * (np0.sum() + np1.sum()) * args.steps
     value = dist.sum(pairs) / (ms * 1e-3)
     per_force, per_step = g.launch_counts()
     g.close()
+    # per-box results of every rank on rank 0
+    rows = np.stack([u1, k1, w1, np1.astype(np.float64)], axis=1)
+    gathered = shard.gather_box_results(dist.pg, len(all_boxes), mine, rows)
 
     # plain FP64 per-box path: every box alone, FP64, its own launches
     fp64_steps = 2
@@ -357,21 +435,26 @@ def run_batch(args, dist):
         t_fp64 += e0.elapsed_time(e1)
         pairs_fp64 += gb.energy()[3] * fp64_steps
         gb.close()
-    value_fp64 = pairs_fp64 / (t_fp64 * 1e-3)
+    t_fp64 = dist.max(t_fp64)
+    value_fp64 = dist.sum(pairs_fp64) / (t_fp64 * 1e-3)
     if dist.rank == 0:
-        ns = [b["pos"].shape[0] for b in boxes]
+        ns = [b["pos"].shape[0] for b in all_boxes]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
+                "scaling": "strong", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
                 "data": "synthetic",
                 "config": {"workload": f"batch512: 512 periodic cubic LJ boxes, N log-uniform in [500, 50000] "
                                        f"(total {sum(ns)}), density U[0.5, 0.9], T U[0.7, 1.2], rc={RC}, "
-                                       f"FCC + jitter 0.05, dt={DT}", "boxes": len(ns), "particles": int(sum(ns)),
+                                       f"FCC + jitter 0.05, dt={DT}; boxes partitioned over the ranks",
+                           "boxes": len(ns), "particles": int(sum(ns)), "boxes_rank0": len(mine),
                            "precision": args.precision, "l2": "flushed between timed iterations"},
                 "schedule": sched, "schedule_force_ms": sched_ms, "clocks": clk,
                 "fp64_per_box": {"value": value_fp64, "unit": UNIT, "ms_per_step": t_fp64 / fp64_steps,
                                  "how": "each box alone in an FP64 context, atomic schedule, per-box launches"},
-                "vs_fp64_per_box": value / value_fp64, "gpu_launches": per_step * args.steps}
+                "vs_fp64_per_box": value / value_fp64, "gpu_launches": per_step * args.steps,
+                "energies_gathered": {"boxes": int(gathered.shape[0]),
+                                      "U_total": float(gathered[:, 0].sum()),
+                                      "pairs_total": int(gathered[:, 3].sum())}}
         print(json.dumps(line), flush=True)
 
 
@@ -418,15 +501,28 @@ def run_gb300(args, dist):
         tile = {"ni": tuned["ni"], "warps": tuned["warps"]} if args.schedule == "auto" else \
             {"ni": best["ni"], "warps": best["warps"]}
 
+    # the first evaluation, at the initial positions: the precision report's sample
     g.set_state(dpos, dvel)
     g.forces(sched)
-    _, _, _, npairs0 = g.energy()
+    f_first = g.get("forces")
+    u0, k0, w0, npairs0 = g.energy()
+    E0 = u0 + k0
     for _ in range((args.warmup + 1) // 2):
         if forces_only:
             g.forces(sched)
         else:
             g.verlet(DT, 2, sched)
     torch.cuda.synchronize(dev)
+
+    def run_steps(k):
+        if forces_only:
+            # the slab's random start has near-overlaps: a step is binning +
+            # one force evaluation (no dynamics)
+            for _ in range(k):
+                g.set_state(dpos, dvel)
+                g.forces(sched)
+        else:
+            g.verlet(DT, k, sched)
 
     # timed region: K steps in graph replays of two steps, L2 flushed between
     calls = [2] * (args.steps // 2) + ([1] if args.steps % 2 else [])
@@ -440,27 +536,42 @@ def run_gb300(args, dist):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        if forces_only:
-            # the slab's random start has near-overlaps: a step is binning +
-            # one force evaluation (no dynamics)
-            for _ in range(k):
-                g.set_state(dpos, dvel)
-                g.forces(sched)
-        else:
-            g.verlet(DT, k, sched)
+        run_steps(k)
         e1.record(stream)
         evs.append((e0, e1))
     torch.cuda.synchronize(dev)
     dist.barrier()
-    clk = clocks.stop()
     elapsed_ms = sum(a.elapsed_time(b) for a, b in evs)
     _, _, _, npairs1 = g.energy()
+    # the same steps continued for about one second (sampled clocks under
+    # sustained load; the line's value is the K-step region above)
+    sus_steps, t_sus = 0, 0.0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t_start = time.perf_counter()
+    while time.perf_counter() - t_start < 1.2:
+        run_steps(2 * 50)
+        sus_steps += 100
+        torch.cuda.synchronize(dev)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_sus = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    u1, k1, _, npairs_sus = g.energy()
     per_force, per_step = g.launch_counts()
     list_stats = g.list_info() if is_list else None
     elapsed_ms = dist.max(elapsed_ms)
     pairs = 0.5 * (npairs0 + npairs1) * args.steps
     total_pairs = dist.sum(pairs)
     value = total_pairs / (elapsed_ms * 1e-3)
+    sustained = {"steps": sus_steps, "ms_per_step": t_sus / sus_steps,
+                 "value": 0.5 * (npairs1 + npairs_sus) / (t_sus / sus_steps * 1e-3), "unit": UNIT,
+                 "note": "the timed steps continued back to back for about one second (no L2 flush), "
+                         "during which the clocks were sampled"}
+    drift_gpu = None if forces_only else {
+        "steps": args.warmup + args.steps + sus_steps,
+        "rel": abs((u1 + k1) - E0) / abs(E0)}
 
     # dominant kernel: the force sweep of one evaluation (binned state or
     # valid lists, L2 flushed)
@@ -490,75 +601,112 @@ def run_gb300(args, dist):
         fts.append(e0.elapsed_time(e1))
     t_force = statistics.median(fts) * 1e-3
     achieved = flops / t_force / 1e12
-    sm_clock = 2070.0
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_clock * 1e6 / 1e12
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    sm_clock = clk.get("sm_mhz") if clk.get("samples_under_load") else None
+    clock_src = "median SM clock of the samples under load"
+    if not sm_clock:
+        sm_clock = clk.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
+        clock_src = "maximum SM clock (no sample under load)"
+    peak = sms * FP32_LANES_PER_SM * 2 * sm_clock * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": measured_traffic(args.workload, sched),
                 "kernel": "k_list_force (mixed): one force evaluation from the lists" if is_list else
                           f"k_force ({sched}, {args.precision}): one force evaluation",
                 "flops_per_eval": flops, "candidates": cand, "pairs": npairs_now,
                 "eval_ms": t_force * 1e3,
-                "peak_note": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"}
+                "peak_note": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_clock:.0f} MHz "
+                             f"({clock_src}); MEASURED_PEAKS.json has no FP32 figure"}
 
-    # end to end through the public API with host buffers (pinned)
+    # binning (counting sort by cell, state permuted into cell order, FP32
+    # cell-local coordinates): HBM-bound
+    bts = []
+    for _ in range(5):
+        g.set_state(dpos, dvel)
+        torch.cuda.synchronize(dev)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.bin()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        bts.append(e0.elapsed_time(e1))
+    t_bin = statistics.median(bts) * 1e-3
+    ncell = int(np.prod(g.grid()[0]))
+    bin_bytes = BIN_BYTES_PER_PARTICLE * n + BIN_BYTES_PER_CELL * ncell
+    hbm = measured_peaks().get("hbm_gbs")
+    roofline_bin = {"bound": "hbm", "achieved": bin_bytes / t_bin / 1e9, "unit": "GB/s",
+                    "peak": hbm or 6800.0, "frac": bin_bytes / t_bin / 1e9 / (hbm or 6800.0),
+                    "frac_nominal_8tbs": bin_bytes / t_bin / 8e12,
+                    "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json)" if hbm else "fallback 6.8 TB/s",
+                    "bytes_per_launch": bin_bytes, "ms": t_bin * 1e3,
+                    "kernels": "k_cellid + k_scan_tiles_ticket + k_scatter_starts + k_rank_gather (lc_bin)",
+                    "bytes_note": f"{BIN_BYTES_PER_PARTICLE} B per particle (read x, v, id: 52 B; write them in "
+                                  f"cell order: 52 B; write the FP32 cell-local coordinates: 16 B) + "
+                                  f"{BIN_BYTES_PER_CELL} B per cell (count, start)"}
+
+    # end to end through the C ABI from page-locked host memory, in the unit
+    # of `value` (velocity-Verlet steps): every job of K steps starts from
+    # the host state (copied in), reads each step's energies and pair count
+    # back (48 bytes, without waiting) and ends with the state read back.
     hpos = torch.from_numpy(pos).pin_memory()
     hvel = torch.from_numpy(vel).pin_memory()
-    e2e_iters = 8
-    g.set_state(hpos, hvel)
-    g.forces(sched)
-    g.energy()
-    torch.cuda.synchronize(dev)
-    # serial: each step copies its inputs, then computes
+    out_pos = torch.empty_like(hpos).pin_memory()
+    out_vel = torch.empty_like(hvel).pin_memory()
+    res = [torch.zeros(6, dtype=torch.float64).pin_memory() for _ in range(args.steps + 1)]
+    dpos_e, dvel_e = torch.empty_like(dpos), torch.empty_like(dvel)
+
+    def e2e_job():
+        dpos_e.copy_(hpos, non_blocking=True)
+        dvel_e.copy_(hvel, non_blocking=True)
+        g.set_state(dpos_e, dvel_e)
+        pairs_job = 0
+        if forces_only:
+            for k in range(args.steps):
+                g.set_state(dpos_e, dvel_e)
+                g.forces(sched)
+                g.energy_async(res[k])
+        else:
+            g.forces(sched)
+            for k in range(args.steps):
+                g.verlet(DT, 1, sched)
+                g.energy_async(res[k])
+        g.get("pos", out=dpos_e)
+        g.get("vel", out=dvel_e)
+        out_pos.copy_(dpos_e, non_blocking=True)
+        out_vel.copy_(dvel_e, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        for k in range(args.steps):
+            pairs_job += lc.decode(res[k])[3]
+        return pairs_job
+
+    e2e_job()
+    jobs = 3
     t0 = time.perf_counter()
-    serial_pairs = 0
-    for _ in range(e2e_iters):
-        g.set_state(hpos, hvel)          # H2D positions + velocities
-        g.forces(sched)                   # bin + force sweep
-        _, _, _, npp = g.energy()        # D2H energies + pair count
-        serial_pairs += npp
-    serial_s = dist.max(time.perf_counter() - t0)
-    # pipelined: step k+1's inputs are copied on a copy stream while step k
-    # computes (two staging slots), and step k's result block is read back
-    # without waiting (two pinned result blocks); the host reads step k-1's
-    # result after queueing step k.  Every step's copies are inside the region.
-    copy_stream = torch.cuda.Stream(dev)
-    res = [torch.zeros(6, dtype=torch.float64).pin_memory() for _ in range(2)]
-    done = [torch.cuda.Event(), torch.cuda.Event()]
-    g.stage_state(hpos, hvel, 0, copy_stream.cuda_stream)
-    g.set_state_staged(0)
-    g.forces(sched)
-    g.energy()
-    torch.cuda.synchronize(dev)
-    pipe_iters = 20
-    t0 = time.perf_counter()
-    e2e_pairs = 0
-    g.stage_state(hpos, hvel, 0, copy_stream.cuda_stream)
-    for k in range(pipe_iters):
-        g.set_state_staged(k % 2)                       # waits (on the device) for this step's copy
-        if k + 1 < pipe_iters:
-            g.stage_state(hpos, hvel, (k + 1) % 2, copy_stream.cuda_stream)   # next step's copy
-        g.forces(sched)
-        g.energy_async(res[k % 2])                      # device-to-host copy of the result block
-        done[k % 2].record(stream)
-        if k >= 1:
-            done[(k - 1) % 2].synchronize()
-            e2e_pairs += lc.decode(res[(k - 1) % 2])[3]
-    done[(pipe_iters - 1) % 2].synchronize()
-    e2e_pairs += lc.decode(res[(pipe_iters - 1) % 2])[3]
+    e2e_pairs = sum(e2e_job() for _ in range(jobs))
     e2e_s = dist.max(time.perf_counter() - t0)
+    state_bytes = int(hpos.numel() * 8 + hvel.numel() * 8)
     e2e = {"value": dist.sum(e2e_pairs) / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(hpos.numel() * 8 + hvel.numel() * 8),
-           "d2h_bytes_per_step": 48,
-           "step": "lc_stage_state(host, next step's inputs, copy stream) + lc_set_state_staged + lc_forces "
-                   "+ lc_energy_virial_async (48-byte result block to pinned host memory, decoded one step "
-                   "later); each step's host-to-device copy overlaps the previous step's compute",
-           "serial_value": dist.sum(serial_pairs) / serial_s,
-           "serial_step": "lc_set_state(host) + lc_forces + lc_energy_virial, no overlap",
-           "serial_d2h_bytes_per_step": 48}
+           "h2d_bytes_per_step": state_bytes / args.steps,
+           "d2h_bytes_per_step": 48 + state_bytes / args.steps,
+           "step": ("a job of K steps through the C ABI: host state (page-locked) copied in, lc_set_state, "
+                    "lc_forces, K x (lc_verlet_step of one step + lc_energy_virial_async of its 48-byte "
+                    "result), lc_get of positions and velocities copied out; bytes per step are the job's "
+                    "divided by K") if not forces_only else
+                   "K x (lc_set_state + lc_forces + lc_energy_virial_async), host state copied in and out"}
     g.close()
 
     if dist.rank == 0:
-        cpu = cpu_baseline(pos, oracle_box(w), rc) if (dist.world == 1 and not args.no_cpu_baseline) else None
+        cpu, errors = None, None
+        if dist.world == 1 and not args.no_cpu_baseline:
+            cpu, ref = cpu_baseline(pos, oracle_box(w), rc)
+            u_first = u0
+            errors = precision_report(f_first, u_first, w0, ref)
+            if drift_gpu is not None:
+                errors["drift"] = {"gpu_rel": drift_gpu["rel"], "gpu_steps": drift_gpu["steps"],
+                                   "oracle_4k_fp64_rel": oracle_drift(drift_gpu["steps"], rc),
+                                   "note": "relative energy drift of this run vs the oracle's FP64 run of the "
+                                           "4,000-particle FCC box over the same number of steps"}
         line = {"metric": METRIC_LIST if is_list else METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
                 "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -566,7 +714,8 @@ def run_gb300(args, dist):
                 "data": "synthetic", "config": workload_config(args, w),
                 "steps_per_s": args.steps / (elapsed_ms * 1e-3) * dist.world,
                 "schedule": sched, "schedule_force_ms": sched_ms, "tile": tile,
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "roofline": roofline, "roofline_bin": roofline_bin, "cpu_baseline": cpu, "errors": errors,
+                "e2e": e2e, "sustained": sustained, "clocks": clk,
                 "gpu_launches": per_step * args.steps}
         if is_list:
             line["list"] = {"skin": args.skin, "builds": list_stats["builds"],

@@ -14,8 +14,12 @@
  *     interaction (intra- or inter-cell) is the unit of work.
  *   - Sec. IV-V: two cell-cell interactions that share a cell write the same
  *     force accumulators; this write sharing is the race the paper analyses.
- *   - Sec. VI, Strategy 1, Fig. 6: loop exchange plus 2-strided colouring
- *     makes the writes of one phase disjoint (LC_SCHED_COLOUR).
+ *   - Sec. VI, Strategy 1, Fig. 6: 2-strided colouring makes the writes of
+ *     same-coloured tasks disjoint (LC_SCHED_COLOUR, applied to blocks of
+ *     cells whose tasks one warp runs in order); Strategy 2: tasks run as
+ *     their dependences allow (the colour schedule's blocks wait only for
+ *     their earlier-coloured neighbours; lc_dag_forces runs the cell-pair
+ *     task DAG of a creation order).
  *   - Sec. VIII: commutative updates only need mutual exclusion, not an
  *     order (LC_SCHED_ATOMIC resolves the sharing with atomic adds).
  *   - Sec. VI, Strategy 3: every task writes private buffers, one per
@@ -59,13 +63,17 @@ typedef enum {
     LC_ERR_NONFINITE = 5,     /* a position or velocity was NaN or infinite    */
     LC_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up            */
     LC_ERR_STATE = 7,         /* call order violated (e.g. no state set)       */
-    LC_ERR_RACE = 8,          /* a colour phase wrote one cell twice           */
+    LC_ERR_RACE = 8,          /* one colour's blocks write a cell twice        */
     LC_ERR_TOO_LARGE = 9      /* size beyond a stated maximum                  */
 } lc_status;
 
 /* How the write sharing between cell pairs is resolved (Sec. IV-VI). */
 typedef enum {
-    LC_SCHED_COLOUR = 0,    /* phases (offset group, colour), disjoint writes   */
+    LC_SCHED_COLOUR = 0,    /* blocks of cells coloured 2-strided, run in colour
+                               order on a device queue: blocks of one colour
+                               write disjoint cells, a block waits for its
+                               earlier-coloured neighbours; plain writes, no
+                               atomics, forces bit-reproducible              */
     LC_SCHED_ATOMIC = 1,    /* one pass, both cells updated by atomic adds      */
     LC_SCHED_FULLSHELL = 2, /* all 27 cells, own cell written only, no Newton-3 */
     LC_SCHED_BUFFER = 3,    /* one pass into private per-(cell, offset) buffers,
@@ -157,8 +165,8 @@ lc_status lc_bin(lc_ctx *ctx, void *stream);
  * changed since the last binning).  Also produces the potential energy,
  * the virial and the number of pairs inside r_c.  LC_ERR_OOM if the buffers
  * of LC_SCHED_BUFFER or the lists of LC_SCHED_LIST cannot be allocated;
- * LC_ERR_INVALID_ARG for LC_SCHED_COLOUR on a batch of boxes, and for
- * LC_SCHED_LIST on a batch or an FP64 context.  LC_SCHED_LIST evaluates
+ * LC_ERR_INVALID_ARG for LC_SCHED_LIST on a batch or an FP64 context;
+ * LC_ERR_TIMEOUT if a wait of the colour schedule's queue ran out.  LC_SCHED_LIST evaluates
  * from the lists, which it first builds (binning on the list grid) when they
  * are stale -- after lc_set_state, lc_set_skin or any link-cell binning;
  * the first build also sizes them, which synchronises the stream. */
@@ -232,15 +240,17 @@ lc_status lc_result_decode(const void *out, double *u_pot, double *k_kin, double
  * device memory.  Host copies synchronise the stream. */
 lc_status lc_get(lc_ctx *ctx, lc_get_what what, void *dst, int on_device, void *stream);
 
-/* Grid of the context: cells per dimension, number of colours, number of
- * colour phases (4 offset groups x colours).  Any output may be NULL. */
+/* Grid of the context: cells per dimension, number of cell colours (the
+ * 2-strided classes of LC_GET_COLOUR), number of block colours of
+ * LC_SCHED_COLOUR.  Any output may be NULL. */
 lc_status lc_grid(const lc_ctx *ctx, int32_t nc[3], int32_t *ncolours, int32_t *nphases);
 
 /* Race and coverage check of a schedule's work decomposition on the device
  * (Sec. IV-VI: the write sharing between cell pairs).  Runs the schedule's
  * own task enumeration without the force arithmetic.  For LC_SCHED_COLOUR
- * every task stamps the cells it writes with its phase and counts cells
- * stamped twice within one phase (*conflicts).  For every schedule each
+ * every block stamps the cells its tasks may write with its colour and the
+ * cells stamped twice within one colour are counted (*conflicts: two blocks
+ * of one colour whose writes could meet).  For every schedule each
  * cell pair of the half-shell (the full shell for LC_SCHED_FULLSHELL) must be
  * visited exactly once; *coverage_errors counts the pairs that are not.
  * Its buffers (27 counters per cell) are allocated on the first call
@@ -320,8 +330,13 @@ lc_status lc_launch_counts(const lc_ctx *ctx, int32_t *per_force, int32_t *per_s
 /* ---- batches of independent boxes --------------------------------------
  * A batch context holds nbox independent periodic boxes (each with its own
  * edges, cutoff and particle count) and runs every stage over all boxes in
- * one launch: binning, the force sweep (atomic or full-shell schedule; the
- * colour schedule is single-box only: LC_ERR_INVALID_ARG), integration.
+ * one launch: binning, the force sweep, integration.  With LC_SCHED_COLOUR
+ * the force sweep is one persistent launch fed by a device work queue whose
+ * items are (colour, box, up to 8 cells of that colour), ordered by colour
+ * and then box, so that the boxes interleave: a cell task waits only for the
+ * earlier-coloured tasks of its own box that could write a common cell
+ * (bounded waits, LC_ERR_TIMEOUT), and the per-box energies are summed in a
+ * fixed order.
  * Particles are numbered box after box: box b owns IDs
  * [n_0 + ... + n_{b-1}, ... + n_b).  lc_set_state, lc_forces,
  * lc_verlet_step, lc_get (all but LC_GET_COLOUR) and lc_destroy take a batch
@@ -336,10 +351,29 @@ lc_status lc_batch_create(int32_t nbox, const double *box, const double *rc, con
 /* Per-box energies of the current state into host arrays of nbox entries
  * (any may be NULL): potential U and virial W of the last force evaluation,
  * kinetic K, pairs inside r_c.  Synchronises the stream.  The per-box U and W
- * are summed with FP64 atomics (order not fixed: the last bits may differ
- * between runs). */
+ * are summed with FP64 atomics for the atomic, full-shell and buffer
+ * schedules (order not fixed: the last bits may differ between runs) and in
+ * a fixed order for the colour schedule. */
 lc_status lc_batch_energies(lc_ctx *ctx, double *u_pot, double *k_kin, double *virial, int64_t *npairs,
                             void *stream);
+
+/* nsteps velocity-Verlet steps of every box of a batch (as lc_verlet_step)
+ * with the colour schedule on the device work queue: Sec. VI, Strategy 1
+ * (colouring) for the disjoint writes of concurrent tasks, Strategy 2 (tasks
+ * run as their dependences allow) for the order, over all boxes at once.
+ * Pairs of two steps are captured in a CUDA graph and replayed.
+ * LC_ERR_INVALID_ARG for a single-box context; LC_ERR_TIMEOUT if a wait of
+ * the queue ran out (see lc_set_queue_wait). */
+lc_status lc_batch_step(lc_ctx *ctx, double dt, int32_t nsteps, void *stream);
+
+/* Limit of one wait of the colour schedule's device queue (seconds, default
+ * 2) and flags: LC_QUEUE_WITHHOLD makes no task publish its completion, so
+ * every wait for an earlier-coloured task runs out and the evaluation ends
+ * with LC_ERR_TIMEOUT (a test of the bounded waits; the context stays
+ * usable).  Waits for the device and drops the captured step graphs.
+ * LC_ERR_INVALID_ARG for seconds outside (0, 1e6] or unknown flags. */
+#define LC_QUEUE_WITHHOLD 1
+lc_status lc_set_queue_wait(lc_ctx *ctx, double seconds, int32_t flags);
 
 /* Number of boxes (0 for a single-box context), total particles, total cells. */
 lc_status lc_batch_info(const lc_ctx *ctx, int32_t *nbox, int64_t *total_particles, int64_t *total_cells);

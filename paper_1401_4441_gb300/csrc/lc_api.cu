@@ -55,6 +55,24 @@ void make_stencil(Stencil *s, int dims) {
                 ++f;
             }
     s->nf = f;
+    // differences of two entries of the centre + forward stencil: the
+    // offsets between cells whose tasks can write a common cell
+    int ent[14][3] = {{0, 0, 0}};
+    for (int k = 0; k < s->nh; ++k)
+        for (int d = 0; d < 3; ++d) ent[k + 1][d] = s->hs[k][d];
+    s->ndep = 0;
+    for (int a = 0; a <= s->nh; ++a)
+        for (int b = 0; b <= s->nh; ++b) {
+            const int o[3] = {ent[a][0] - ent[b][0], ent[a][1] - ent[b][1], ent[a][2] - ent[b][2]};
+            if (!o[0] && !o[1] && !o[2]) continue;
+            bool seen = false;
+            for (int k = 0; k < s->ndep && !seen; ++k)
+                seen = s->dep[k][0] == o[0] && s->dep[k][1] == o[1] && s->dep[k][2] == o[2];
+            if (!seen) {
+                for (int d = 0; d < 3; ++d) s->dep[s->ndep][d] = o[d];
+                ++s->ndep;
+            }
+        }
 }
 
 void make_grid(Grid *g, const double box[3], double rc, int dims) {
@@ -91,6 +109,27 @@ void make_grid(Grid *g, const double box[3], double rc, int dims) {
         if (present) { g->raw_of_colour[r] = raw; ++r; }
     }
     g->ncolours = r;
+    // colour schedule: class strides, classes and the colour queue order
+    for (int d = 0; d < 3; ++d) {
+        const bool two_sided = dims == 3 ? d < 2 : d == 0;
+        g->cs_p[d] = (dims == 2 && d == 2) ? 1 : (two_sided ? 3 : 2);
+        g->cs_ncls[d] = g->cs_p[d] + (g->nc[d] - g->cs_p[d] * (g->nc[d] / g->cs_p[d]));
+    }
+    r = 0;
+    g->cs_first[0] = 0;
+    for (int raw = 0; raw < 125; ++raw) {
+        const int a[3] = {raw % 5, (raw / 5) % 5, raw / 25};
+        g->cs_colour_of_raw[raw] = -1;
+        g->cs_raw_of_colour[raw] = -1;
+        if (a[0] >= g->cs_ncls[0] || a[1] >= g->cs_ncls[1] || a[2] >= g->cs_ncls[2]) continue;
+        g->cs_colour_of_raw[raw] = r;
+        g->cs_raw_of_colour[r] = raw;
+        g->cs_first[r + 1] = g->cs_first[r] + cs_count(a[0], g->nc[0], g->cs_p[0]) *
+                                                  cs_count(a[1], g->nc[1], g->cs_p[1]) *
+                                                  cs_count(a[2], g->nc[2], g->cs_p[2]);
+        ++r;
+    }
+    g->cs_ncolours = r;
     // exact division by multiplication: with M = ceil(2^64 / d) and c < 2^32,
     // c M / 2^64 = c / d + c e / (d 2^64) with e = M d - 2^64 < d, an excess
     // below 1 / d, so the floor is floor(c / d)
@@ -158,7 +197,7 @@ static void free_ctx(Ctx *c) {
                     c->d_warp_acc, c->d_warp_pairs, c->d_kin_part, c->d_result,
                     c->d_stamp, c->d_visit, c->d_counters, c->d_boxes, c->d_cell_box, c->d_slot_box,
                     c->d_box_acc, c->d_box_pairs, c->d_box_out, c->d_fbuf, c->d_nbr, c->d_nn, c->d_q4,
-                    c->d_list_stats};
+                    c->d_list_stats, c->d_cs_done, c->d_cs_ctrl, c->d_cell_acc, c->d_cell_pairs, c->d_cs_items};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k < 2 * kNumSched; ++k)
@@ -204,6 +243,8 @@ static cudaError_t alloc_common(Ctx *c) {
         (e = dalloc(&c->d_p4, N)) || (e = dalloc(&c->fx, 3 * N)) || (e = dalloc(&c->kx, 3 * N)) ||
         (e = dalloc(&c->d_warp_acc, 4 * (size_t)c->nwarp_max)) || (e = dalloc(&c->d_warp_pairs, (size_t)c->nwarp_max)) ||
         (e = dalloc(&c->d_kin_part, (size_t)kinetic_blocks(c))) || (e = dalloc(&c->d_result, 8)) ||
+        (e = dalloc(&c->d_cs_done, NC)) || (e = dalloc(&c->d_cs_ctrl, 2)) ||
+        (e = dalloc(&c->d_cell_acc, 4 * NC)) || (e = dalloc(&c->d_cell_pairs, NC)) ||
         (e = cudaHostAlloc(&c->h_out, 64, cudaHostAllocDefault)))
         return e;
     c->d_npairs = reinterpret_cast<long long *>(c->d_result + 4);
@@ -264,6 +305,7 @@ static lc_status create_single(const double box[3], double rc, int64_t n, lc_pre
     memset(static_cast<Ctx *>(c), 0, sizeof(Ctx));
     make_grid(&c->g, box, rc, dims);
     c->skin = 0.4;
+    c->cs_wait_s = 2.0;
     c->n = n;
     c->prec = prec;
     c->ni = 16;
@@ -328,6 +370,7 @@ lc_status lc_batch_create(int32_t nbox, const double *box, const double *rc, con
     }
     c->g = c->h_boxes[0].g;   // scalar fields of box 0; totals below
     c->g.ncell = coff;
+    c->cs_wait_s = 2.0;
     c->n = ntot;
     c->prec = prec;
     c->ni = 16;
@@ -351,7 +394,30 @@ lc_status lc_batch_create(int32_t nbox, const double *box, const double *rc, con
         for (int k = 0; k < bd.g.ncell; ++k) cb[bd.cell_off + k] = (unsigned short)b;
         for (int k = 0; k < bd.n; ++k) sb[bd.part_off + k] = (unsigned short)b;
     }
-    e = cudaMemcpy(c->d_boxes, c->h_boxes, sizeof(BoxDev) * (size_t)nbox, cudaMemcpyHostToDevice);
+    // colour-queue items: for each colour rank, every box that has it, its
+    // cells of that colour in chunks of up to 8
+    int maxcol = 0;
+    int64_t nitems = 0;
+    for (int b = 0; b < nbox; ++b) {
+        const Grid &gb = c->h_boxes[b].g;
+        if (gb.cs_ncolours > maxcol) maxcol = gb.cs_ncolours;
+        for (int k = 0; k < gb.cs_ncolours; ++k) nitems += (gb.cs_first[k + 1] - gb.cs_first[k] + 7) / 8;
+    }
+    int4 *items = (int4 *)malloc(sizeof(int4) * (size_t)(nitems > 0 ? nitems : 1));
+    if (!items) { free(cb); free(sb); free_ctx(c); return LC_ERR_OOM; }
+    int64_t q = 0;
+    for (int k = 0; k < maxcol; ++k)
+        for (int b = 0; b < nbox; ++b) {
+            const Grid &gb = c->h_boxes[b].g;
+            if (k >= gb.cs_ncolours) continue;
+            const int cells = gb.cs_first[k + 1] - gb.cs_first[k];
+            for (int t0 = 0; t0 < cells; t0 += 8) items[q++] = make_int4(b, k, t0, cells - t0 < 8 ? cells - t0 : 8);
+        }
+    c->cs_nitems = (int)nitems;
+    e = dalloc(&c->d_cs_items, (size_t)(nitems > 0 ? nitems : 1));
+    if (!e && nitems > 0) e = cudaMemcpy(c->d_cs_items, items, sizeof(int4) * (size_t)nitems, cudaMemcpyHostToDevice);
+    free(items);
+    if (!e) e = cudaMemcpy(c->d_boxes, c->h_boxes, sizeof(BoxDev) * (size_t)nbox, cudaMemcpyHostToDevice);
     if (!e) e = cudaMemcpy(c->d_cell_box, cb, sizeof(unsigned short) * (size_t)coff, cudaMemcpyHostToDevice);
     if (!e && ntot > 0) e = cudaMemcpy(c->d_slot_box, sb, sizeof(unsigned short) * (size_t)ntot, cudaMemcpyHostToDevice);
     if (!e) e = cudaMemset(c->d_box_out, 0, sizeof(double) * 4 * (size_t)nbox);
@@ -628,7 +694,6 @@ lc_status lc_list_info(lc_ctx *c, int64_t *builds, int64_t *long_rows, int64_t *
 
 lc_status lc_forces(lc_ctx *c, lc_schedule sched, void *stream) {
     if (!c || sched < LC_SCHED_COLOUR || sched > LC_SCHED_LIST) return LC_ERR_INVALID_ARG;
-    if (c->nbox > 0 && sched == LC_SCHED_COLOUR) return LC_ERR_INVALID_ARG;
     if (!c->have_state) return LC_ERR_STATE;
     int launches = 0;
     lc_status st = sched == LC_SCHED_LIST ? list_forces(c, (cudaStream_t)stream, &launches)
@@ -658,7 +723,6 @@ static cudaError_t step_launches(lc_ctx *c, double dt, lc_schedule sched, cudaSt
 lc_status lc_verlet_step(lc_ctx *c, double dt, int nsteps, lc_schedule sched, void *stream) {
     if (!c || nsteps < 0 || !isfinite(dt) || sched < LC_SCHED_COLOUR || sched > LC_SCHED_LIST)
         return LC_ERR_INVALID_ARG;
-    if (c->nbox > 0 && sched == LC_SCHED_COLOUR) return LC_ERR_INVALID_ARG;
     if (!c->have_state) return LC_ERR_STATE;
     if (nsteps > 0) c->kin_valid = false;   // the steps change the velocities
     if (sched == LC_SCHED_LIST) return list_verlet(c, dt, nsteps, (cudaStream_t)stream);
@@ -706,6 +770,22 @@ lc_status lc_verlet_step(lc_ctx *c, double dt, int nsteps, lc_schedule sched, vo
     }
     c->binned = true;
     c->forces_valid = true;
+    return LC_OK;
+}
+
+lc_status lc_batch_step(lc_ctx *c, double dt, int32_t nsteps, void *stream) {
+    if (!c || c->nbox <= 0) return LC_ERR_INVALID_ARG;
+    return lc_verlet_step(c, dt, nsteps, LC_SCHED_COLOUR, stream);
+}
+
+lc_status lc_set_queue_wait(lc_ctx *c, double seconds, int32_t flags) {
+    if (!c || !(seconds > 0.0) || !isfinite(seconds) || seconds > 1.0e6 || (flags & ~LC_QUEUE_WITHHOLD))
+        return LC_ERR_INVALID_ARG;
+    LC_TRY(cudaDeviceSynchronize());   // no captured step in flight: the graphs hold the old values
+    for (int k = 0; k < 2 * kNumSched; ++k)
+        if (c->graph[k]) { cudaGraphExecDestroy(c->graph[k]); c->graph[k] = nullptr; }
+    c->cs_wait_s = seconds;
+    c->cs_withhold = (flags & LC_QUEUE_WITHHOLD) ? 1 : 0;
     return LC_OK;
 }
 
@@ -812,13 +892,7 @@ lc_status lc_grid(const lc_ctx *c, int32_t nc[3], int32_t *ncolours, int32_t *np
     if (!c) return LC_ERR_INVALID_ARG;
     if (nc) for (int d = 0; d < 3; ++d) nc[d] = c->g.nc[d];
     if (ncolours) *ncolours = c->g.ncolours;
-    if (nphases) {
-        Stencil st;
-        make_stencil(&st, c->g.dims);
-        int groups = 0;
-        for (int g = 0; g < 4; ++g) groups += (g == 0 || st.group_first[g + 1] > st.group_first[g]) ? 1 : 0;
-        *nphases = groups * c->g.ncolours;
-    }
+    if (nphases) *nphases = c->g.cs_ncolours;   // colours of LC_SCHED_COLOUR
     return LC_OK;
 }
 

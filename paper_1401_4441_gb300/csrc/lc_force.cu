@@ -36,6 +36,7 @@
 #include <type_traits>
 
 #include "lc_internal.cuh"
+#include "lc_pair.cuh"
 
 namespace lc {
 
@@ -44,7 +45,8 @@ __constant__ Stencil c_st2;   // 2D (x-y plane) stencil tables
 
 __device__ __forceinline__ const Stencil &stencil(int dims) { return dims == 2 ? c_st2 : c_st; }
 
-enum Mode : int { kColour = 0, kAtomic = 1, kFullShell = 2, kBuffer = 3, kDag = 4 };
+// kColourQ: cell tasks in colour order on a device queue (LC_SCHED_COLOUR)
+enum Mode : int { kAtomic = 1, kFullShell = 2, kBuffer = 3, kDag = 4, kColourQ = 5 };
 
 constexpr int kJCap = 512;      // neighbour slots listed per batch (per warp)
 constexpr int kMaxNb = 27;      // neighbour cells per task
@@ -65,6 +67,16 @@ struct ForceArgs {
     long long *warp_pairs;      // [W]
     int group, colour;          // colour phase
     int ntasks;
+    // colour queue: per-cell completion flags, the queue counter, the limit
+    // of one wait for a cell, per-cell energy partials
+    int *cs_done;
+    int *cs_ctrl;
+    int *err;
+    long long wait_ns;
+    double *cell_acc;
+    long long *cell_pairs;
+    const int4 *cs_items;       // batch: (box, colour, first cell of the colour, cells) per queue item
+    int withhold;               // test of the bounded waits: no task publishes its completion
     int stats;                  // accumulate energy, virial and pair count
     int pairx;                  // 2D atomic: a task is two x-adjacent cells (see single_task)
     float sh[27][3];            // o * h rounded to FP32, offset index (ox+1) + 3 (oy+1) + 9 (oz+1)
@@ -95,16 +107,6 @@ struct TaskCells {
 
 __device__ __forceinline__ void cell_xyz(const Grid &g, int c, int out[3]) { cell_coords(g, c, out); }
 
-// Task t of a colour phase: the t-th cell (x fastest) of colour `colour`.
-__device__ __forceinline__ int colour_task_cell(const Grid &g, int colour, int t, int cA[3]) {
-    int raw = g.raw_of_colour[colour];
-    int a[3] = {raw % 3, (raw / 3) % 3, raw / 9};
-    int n0 = g.class_count[0][a[0]], n1 = g.class_count[1][a[1]];
-    int t3[3] = {t % n0, (t / n0) % n1, t / (n0 * n1)};
-    for (int d = 0; d < 3; ++d) cA[d] = (a[d] == 2) ? g.nc[d] - 1 : 2 * t3[d] + a[d];
-    return cA[0] + g.nc[0] * (cA[1] + g.nc[1] * cA[2]);
-}
-
 // Neighbour k of the task (k < nnb): offset and periodic image.
 // Entries of a two-cell task (cells A and A + x of the 2D atomic schedule),
 // as offsets from A: the two cells themselves (both ordered by slot), the
@@ -127,18 +129,15 @@ __device__ __forceinline__ void task_offset(int group, int k, bool self, int dim
     const Stencil &S = stencil(dims);
     if (MODE == kFullShell) {            // all offsets, centre first
         o[0] = S.full[k + 1][0]; o[1] = S.full[k + 1][1]; o[2] = S.full[k + 1][2];
-    } else if (MODE == kAtomic || MODE == kBuffer) {
+    } else if (MODE == kAtomic || MODE == kBuffer || MODE == kColourQ) {
         o[0] = S.hs[k][0]; o[1] = S.hs[k][1]; o[2] = S.hs[k][2];
-    } else if (MODE == kDag) {           // one neighbour: half-shell offset `group`
+    } else {                             // kDag: one neighbour, half-shell offset `group`
         o[0] = S.hs[group][0]; o[1] = S.hs[group][1]; o[2] = S.hs[group][2];
-    } else {
-        int kk = S.group_list[S.group_first[group] + k];
-        o[0] = S.hs[kk][0]; o[1] = S.hs[kk][1]; o[2] = S.hs[kk][2];
     }
 }
 
-// Single-box task t: the cell (colour schedule: the t-th cell of the phase's
-// colour) and its neighbour count; used by the force and check kernels.
+// Single-box task t: the cell and its neighbour count (2D atomic: a pair of
+// x-adjacent cells); used by the force and check kernels.
 template <int MODE>
 __device__ __forceinline__ void single_task(const Grid &g, int group, int colour, int t, TaskCells &tc,
                                             int pairx = 0) {
@@ -146,12 +145,7 @@ __device__ __forceinline__ void single_task(const Grid &g, int group, int colour
     tc.dims = g.dims;
     tc.pairx = 0;
     const Stencil &S = stencil(g.dims);
-    if (MODE == kColour) {
-        tc.A = colour_task_cell(g, colour, t, tc.cA);
-        tc.self = (group == 0);
-        tc.nnb = (S.group_first[group + 1] - S.group_first[group]) + (tc.self ? 1 : 0);
-        tc.nself = tc.self ? 1 : 0;
-    } else if (MODE == kAtomic && pairx) {
+    if (MODE == kAtomic && pairx) {
         // 2D atomic: task t = cells (2 tx, ty) and (2 tx + 1, ty); an odd
         // row's last cell is a task of its own (the one-cell half-shell)
         const int nhx = (g.nc[0] + 1) >> 1;
@@ -201,7 +195,8 @@ struct alignas(16) WarpSmem {
     float4 ipb[16];             // mixed: (z, z', rz, rz') with r the rounding residual
     float4 ipc[16];             // mixed: (rx, rx', ry, ry')
     int2 islot2[16];            // mixed: (slot, slot')
-    float corr[32][3];          // mixed: i-side forces of near-r_c pairs
+    float corr[32][3];          // mixed: i-side forces of the band pairs around r_c
+    double corr64[16][3];       // mixed: i-side forces of the close pairs (FP64)
     T ix[32], iy[32], iz[32];   // FP64: centre-cell particles
     int islot[32];
     int jl[kJCap];              // slot | (neighbour index << 26)
@@ -213,100 +208,27 @@ struct alignas(16) WarpSmem {
     float4 nb_sl[kMaxNb];       // o * h - nb_sh, rounded to FP32
 };
 
-__device__ __forceinline__ double image_shift(const Grid &g, int img, int d) {
-    const int s = ((img >> (2 * d)) & 3) - 1;
-    return s == 0 ? 0.0 : (s > 0 ? g.L[d] : -g.L[d]);
-}
-
-// Shared-memory vector load kept inside the loop (volatile): the centre-cell
-// particles are re-read per candidate instead of being pinned in registers,
-// which keeps the kernel at two resident blocks per SM.
-__device__ __forceinline__ float4 lds4(const float4 *p) {
-    float4 v;
-    const unsigned addr = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
-    return v;
-}
-
-// Reciprocal: hardware approximation refined by one Newton-Raphson step
-// y <- y (2 - r y), written as two FMAs.
-__device__ __forceinline__ float rcp_nr(float r) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(r));
-    float e = fmaf(-r, y, 1.0f);
-    return fmaf(y, e, y);
-}
-
-// Butterfly reduce-scatter of v[NI] over the 32 lanes of a warp.  On return
-// lane l holds in v[0] the warp-wide sum of element e(l), where fold k (lane
-// bit 4 - k) picks bit log2(NI) - 1 - k of e; lanes that differ only in the
-// low log2(32 / NI) bits hold the same element.
-template <typename T, int NI>
-__device__ __forceinline__ void reduce_scatter(T (&v)[NI], int lane) {
-#pragma unroll
-    for (int half = NI / 2, m = 16; half >= 1; half >>= 1, m >>= 1) {
-        const bool up = (lane & m) != 0;
-        if constexpr (std::is_same<T, float>::value) {
-            if (half >= 2) {   // pairs of adjacent elements: one f32x2 add per pair
-#pragma unroll
-                for (int k = 0; k < half; k += 2) {
-                    const float2 keep = make_float2(up ? v[k + half] : v[k], up ? v[k + half + 1] : v[k + 1]);
-                    const float2 recv = make_float2(__shfl_xor_sync(kFull, up ? v[k] : v[k + half], m),
-                                                    __shfl_xor_sync(kFull, up ? v[k + 1] : v[k + half + 1], m));
-                    const float2 sum = __fadd2_rn(keep, recv);
-                    v[k] = sum.x;
-                    v[k + 1] = sum.y;
-                }
-                continue;
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < half; ++k) {
-            T send = up ? v[k] : v[k + half];
-            T keep = up ? v[k + half] : v[k];
-            v[k] = keep + __shfl_xor_sync(kFull, send, m);
-        }
-    }
-#pragma unroll
-    for (int m = 16 / NI; m >= 1; m >>= 1) v[0] += __shfl_xor_sync(kFull, v[0], m);
-}
-
-template <int NI>
-__device__ __forceinline__ int scattered_element(int lane) {
-    int bits = 0;
-    for (int n = NI; n > 1; n >>= 1) ++bits;
-    int e = 0;
-    for (int k = 0; k < bits; ++k) e |= ((lane >> (4 - k)) & 1) << (bits - 1 - k);
-    return e;
-}
-
-// Kahan-compensated accumulation of v into (s, c): true sum ~ s - c.
-__device__ __forceinline__ void kahan_add(float2 &acc, float v) {
-    float y = v - acc.y;
-    float t = acc.x + y;
-    acc.y = (t - acc.x) - y;
-    acc.x = t;
-}
-
 template <typename T>
 __device__ __forceinline__ double to_f64(T v) {
     if constexpr (std::is_same<T, float>::value) return f32_to_f64_bits(v);
     else return v;
 }
 
-// One task's partial force on one particle enters its accumulator.
+// One task's partial force on one particle enters its accumulator: the FP32
+// partial v and, for the mixed path, the FP64 sum c of its close pairs.
 template <int MODE, bool MIXED, typename T>
-__device__ __forceinline__ void write_force(const ForceArgs &a, int slot, T vx, T vy, T vz) {
+__device__ __forceinline__ void write_force(const ForceArgs &a, int slot, T vx, T vy, T vz, double cx = 0.0,
+                                            double cy = 0.0, double cz = 0.0) {
     if constexpr (MODE == kAtomic) {
-        atomicAdd(a.fx + slot, to_f64(vx));
-        atomicAdd(a.fy + slot, to_f64(vy));
-        atomicAdd(a.fz + slot, to_f64(vz));
+        atomicAdd(a.fx + slot, to_f64(vx) + cx);
+        atomicAdd(a.fy + slot, to_f64(vy) + cy);
+        atomicAdd(a.fz + slot, to_f64(vz) + cz);
     } else if constexpr (MODE == kFullShell) {
-        a.fx[slot] = to_f64(vx); a.fy[slot] = to_f64(vy); a.fz[slot] = to_f64(vz);
+        a.fx[slot] = to_f64(vx) + cx; a.fy[slot] = to_f64(vy) + cy; a.fz[slot] = to_f64(vz) + cz;
     } else if constexpr (MIXED) {
         float2 kx = a.kx[slot], ky = a.ky[slot], kz = a.kz[slot];
         kahan_add(kx, (float)vx); kahan_add(ky, (float)vy); kahan_add(kz, (float)vz);
+        if (cx != 0.0 || cy != 0.0 || cz != 0.0) { kahan_add64(kx, cx); kahan_add64(ky, cy); kahan_add64(kz, cz); }
         a.kx[slot] = kx; a.ky[slot] = ky; a.kz[slot] = kz;
     } else {
         a.fx[slot] += vx; a.fy[slot] += vy; a.fz[slot] += vz;
@@ -627,83 +549,19 @@ __device__ __forceinline__ void write_i_chunk(const ForceArgs &a, S &sm, T (&ax)
     if ((lane & ((32 / NI) - 1)) == 0) {
         const int ii = i0 + elem;
         if (ii < na) {
+            double c[3] = {0.0, 0.0, 0.0};
             if constexpr (MIXED) {
                 ax[0] += sm.corr[elem][0]; ay[0] += sm.corr[elem][1]; az[0] += sm.corr[elem][2];
+                c[0] = sm.corr64[elem][0]; c[1] = sm.corr64[elem][1]; c[2] = sm.corr64[elem][2];
             }
-            if constexpr (MODE == kBuffer) buffer_store<T>(a, kIBuf, a0 + ii, false, ax[0], ay[0], az[0]);
-            else write_force<MODE, MIXED, T>(a, a0 + ii, ax[0], ay[0], az[0]);
+            if constexpr (MODE == kBuffer)
+                buffer_store<T>(a, kIBuf, a0 + ii, false, ax[0] + (T)c[0], ay[0] + (T)c[1], az[0] + (T)c[2]);
+            else write_force<MODE, MIXED, T>(a, a0 + ii, ax[0], ay[0], az[0], c[0], c[1], c[2]);
         }
     }
     __syncwarp();
 }
 
-// Mixed-precision candidate loop of one 32-slot neighbour chunk against the
-// NI staged centre-cell particles, two of them per packed f32x2 operation.
-// SELF: the chunk holds intra-cell entries (slot order decides the pair);
-// STATS: accumulate energy partials and the pair count.
-template <int NI, bool N3, bool SELF, bool STATS>
-__device__ __forceinline__ void pair_loop(const WarpSmem<float> &sm, const float (&pj)[3], const float (&lj)[3],
-                                          int jlim, int jexcl, float rc2lo, float rc2hi,
-                                          float2 (&ax2)[NI / 2], float2 (&ay2)[NI / 2], float2 (&az2)[NI / 2],
-                                          float2 &gx, float2 &gy, float2 &gz, float2 &e6, float2 &e12,
-                                          int &npair, bool &amb, int kpairs) {
-    const float2 one2 = make_float2(1.0f, 1.0f);
-    const float2 c48 = make_float2(48.0f, 48.0f), cm24 = make_float2(-24.0f, -24.0f);
-    const float2 npx = make_float2(-pj[0], -pj[0]), npy = make_float2(-pj[1], -pj[1]), npz = make_float2(-pj[2], -pj[2]);
-    const float2 nlx = make_float2(-lj[0], -lj[0]), nly = make_float2(-lj[1], -lj[1]), nlz = make_float2(-lj[2], -lj[2]);
-#pragma unroll
-    for (int m = 0; m < NI / 2; ++m) {
-        if (m >= kpairs) break;   // the rest of the tile holds only sentinels (warp-uniform)
-        const float4 A = lds4(&sm.ipa[m]);
-        const float4 B = lds4(&sm.ipb[m]);
-        const float4 C = lds4(&sm.ipc[m]);
-        bool oka = true, okb = true;
-        if (SELF) {
-            const int2 sl = sm.islot2[m];
-            oka = N3 ? (sl.x < jlim) : (sl.x != jexcl);
-            okb = N3 ? (sl.y < jlim) : (sl.y != jexcl);
-        }
-        // d = (x_i - x_j,hi) + (r_i - x_j,lo): both residuals carried
-        const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), npx), __fadd2_rn(make_float2(C.x, C.y), nlx));
-        const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), npy), __fadd2_rn(make_float2(C.z, C.w), nly));
-        const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), npz), __fadd2_rn(make_float2(B.z, B.w), nlz));
-        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-        const bool neara = oka && (r2.x < rc2hi), nearb = okb && (r2.y < rc2hi);
-        const bool hita = neara && (r2.x < rc2lo), hitb = nearb && (r2.y < rc2lo);
-        amb |= (neara && !hita) || (nearb && !hitb);
-        float2 y;
-        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y.x) : "f"(r2.x));
-        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y.y) : "f"(r2.y));
-        const float2 e = __ffma2_rn(make_float2(-r2.x, -r2.y), y, one2);   // Newton step
-        y = __ffma2_rn(y, e, y);
-        y.x = hita ? y.x : 0.0f;   // masks misses and r2 = 0 (i == j)
-        y.y = hitb ? y.y : 0.0f;
-        const float2 s6 = __fmul2_rn(__fmul2_rn(y, y), y);
-        const float2 f = __fmul2_rn(__fmul2_rn(s6, y), __ffma2_rn(s6, c48, cm24));
-        ax2[m] = __ffma2_rn(f, dx, ax2[m]);
-        ay2[m] = __ffma2_rn(f, dy, ay2[m]);
-        az2[m] = __ffma2_rn(f, dz, az2[m]);
-        if (N3) {
-            gx = __ffma2_rn(f, dx, gx);
-            gy = __ffma2_rn(f, dy, gy);
-            gz = __ffma2_rn(f, dz, gz);
-        }
-        if (STATS) {
-            e6 = __fadd2_rn(e6, s6);
-            e12 = __ffma2_rn(s6, s6, e12);
-            npair += (hita ? 1 : 0) + (hitb ? 1 : 0);
-        }
-    }
-}
-
-__device__ __forceinline__ float staged(const float4 *arr, int k, int comp) {
-    // component comp (0: x or z, 1: y or slot) of staged particle k
-    const float *f = reinterpret_cast<const float *>(arr);
-    return f[4 * (k >> 1) + 2 * comp + (k & 1)];
-}
-
-// Mixed precision: FP32 pair arithmetic, two centre-cell particles per
-// packed f32x2 operation (the lane's j is the same for both).
 // Per-box statistics of one i chunk (batched kernels): warp sums, one set
 // of FP64 / integer atomics per chunk into the box's accumulators.
 __device__ __forceinline__ void box_stats(const ForceArgs &a, int box, double s6, double s12, long long np) {
@@ -768,6 +626,7 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
             C[4 * m + 2 + h] = lo_residual(q, 1);
             S[2 * m + h] = ii < na ? a0 + ii : 0x7fffffff;
             sm.corr[lane][0] = sm.corr[lane][1] = sm.corr[lane][2] = 0.f;
+            sm.corr64[lane][0] = sm.corr64[lane][1] = sm.corr64[lane][2] = 0.0;
         }
         // the box is only used by the prune (lists longer than one chunk)
         if (total > kWarp) {
@@ -842,10 +701,12 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
                     pair_loop<NI, N3, false, STATS>(sm, pj, lj, jlim, jexcl, rc2lo, rc2hi, ax2, ay2, az2, gx, gy, gz,
                                                     e6, e12, npair, amb, kpairs);
                 float fjx = -(gx.x + gx.y), fjy = -(gy.x + gy.y), fjz = -(gz.x + gz.y);
+                double cj[3] = {0.0, 0.0, 0.0};   // the j side of its close pairs (FP64)
                 if (__any_sync(kFull, amb)) {
                     // rare: candidates within the band around r_c^2 are decided
-                    // with the FP64 definition; the ones inside are added here
-                    // (i side through the warp's shared correction slots)
+                    // with the FP64 definition and the ones inside added in
+                    // FP32; pairs closer than kClose are computed and summed in
+                    // FP64 (i side through the warp's shared correction slots)
                     double sL[3];
                     for (int d = 0; d < 3; ++d) sL[d] = image_shift(g, sm.nb_img[nb], d);
 #pragma unroll 1
@@ -856,7 +717,21 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
                         const float dy = (staged(sm.ipa, k, 1) + -pj[1]) + (staged(sm.ipc, k, 1) + -lj[1]);
                         const float dz = (staged(sm.ipb, k, 0) + -pj[2]) + (staged(sm.ipb, k, 1) + -lj[2]);
                         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        if (valid && ok && r2 < rc2hi && !(r2 < rc2lo) && exact_inside(a, g.rc2, si, sj, sL)) {
+                        if (!(valid && ok && r2 < rc2hi) || loop_hit(r2, rc2lo)) continue;
+                        if (loop_close(r2, rc2lo)) {
+                            double F[3];
+                            const double s6d = pair_force_f64(a.x, a.y, a.z, si, sj, sL, F);
+                            atomicAdd(&sm.corr64[k][0], F[0]);
+                            atomicAdd(&sm.corr64[k][1], F[1]);
+                            atomicAdd(&sm.corr64[k][2], F[2]);
+                            cj[0] -= F[0]; cj[1] -= F[1]; cj[2] -= F[2];
+                            if (STATS) {
+                                const float s6 = (float)s6d;
+                                e6.x += s6;
+                                e12.x = fmaf(s6, s6, e12.x);
+                                npair += 1;
+                            }
+                        } else if (exact_inside(a, g.rc2, si, sj, sL)) {   // the band around r_c^2
                             const float inv = rcp_nr(r2);
                             const float s6 = inv * inv * inv;
                             const float f = (s6 * inv) * fmaf(48.0f, s6, -24.0f);
@@ -864,15 +739,18 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
                             atomicAdd(&sm.corr[k][1], f * dy);
                             atomicAdd(&sm.corr[k][2], f * dz);
                             fjx = fmaf(-f, dx, fjx); fjy = fmaf(-f, dy, fjy); fjz = fmaf(-f, dz, fjz);
-                            e6.x += s6;
-                            e12.x = fmaf(s6, s6, e12.x);
-                            npair += 1;
+                            if (STATS) {
+                                e6.x += s6;
+                                e12.x = fmaf(s6, s6, e12.x);
+                                npair += 1;
+                            }
                         }
                     }
                 }
                 if (N3 && valid) {
-                    if constexpr (MODE == kBuffer) buffer_store<float>(a, nb, sj, i0 > 0, fjx, fjy, fjz);
-                    else write_force<MODE, true, float>(a, sj, fjx, fjy, fjz);
+                    if constexpr (MODE == kBuffer)
+                        buffer_store<float>(a, nb, sj, i0 > 0, fjx + (float)cj[0], fjy + (float)cj[1], fjz + (float)cj[2]);
+                    else write_force<MODE, true, float>(a, sj, fjx, fjy, fjz, cj[0], cj[1], cj[2]);
                 }
             }
             __syncwarp();
@@ -977,6 +855,99 @@ __device__ void run_task_fp64(const ForceArgs &a, WarpSmem<double> &sm, const Ta
     }
 }
 
+// Colour schedule: task t of colour k of one box (grid g, shift tables sh /
+// sl, first global cell cell_off).  Waits until the earlier-coloured tasks
+// whose written cells can meet this task's have published their completion
+// (the cells at the stencil's dependency offsets), runs the cell task with
+// plain writes, stores the task's energy partials (summed in a fixed order
+// afterwards) and publishes.  Returns false if a wait ran out (error flag
+// set).
+template <bool MIXED, int NI, bool STATS>
+__device__ bool colour_task(const ForceArgs &a, WarpSmem<typename std::conditional<MIXED, float, double>::type> &sm,
+                            const Grid &g, const float (*sh)[3], const float (*sl)[3], int cell_off, int k, int t,
+                            int lane) {
+    const Stencil &S = stencil(g.dims);
+    const int raw = g.cs_raw_of_colour[k];
+    const int cls[3] = {raw % 5, (raw / 5) % 5, raw / 25};
+    const int n0 = cs_count(cls[0], g.nc[0], g.cs_p[0]), n1 = cs_count(cls[1], g.nc[1], g.cs_p[1]);
+    const int t3[3] = {t % n0, (t / n0) % n1, t / (n0 * n1)};
+    int cA[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) cA[d] = cs_coord(cls[d], t3[d], g.nc[d], g.cs_p[d]);
+    const int A = cell_off + cA[0] + g.nc[0] * (cA[1] + g.nc[1] * cA[2]);
+    bool timed_out = false;
+    for (int e = lane; e < S.ndep; e += kWarp) {
+        int cn[3], ncl[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            cn[d] = cA[d] + S.dep[e][d];
+            cn[d] = cn[d] < 0 ? cn[d] + g.nc[d] : (cn[d] >= g.nc[d] ? cn[d] - g.nc[d] : cn[d]);
+            ncl[d] = cs_class(cn[d], g.nc[d], g.cs_p[d]);
+        }
+        // every class triple with a_d < cs_ncls[d] is present: the colour
+        // (rank in code order) is the mixed-radix number of the triple
+        if (ncl[0] + g.cs_ncls[0] * (ncl[1] + g.cs_ncls[1] * ncl[2]) >= k) continue;
+        const int N = cell_off + cn[0] + g.nc[0] * (cn[1] + g.nc[1] * cn[2]);
+        if (ld_relaxed(a.cs_done + N) != 0) continue;
+        const unsigned long long t0 = global_ns();
+        unsigned sleep = 64;
+        timed_out = true;
+        for (unsigned it = 0; it < (1u << 22); ++it) {
+            __nanosleep(sleep);
+            if (sleep < 2048) sleep <<= 1;   // back off: few loads on the flag
+            if (ld_relaxed(a.cs_done + N) != 0) { timed_out = false; break; }
+            if ((it & 7) == 7) {
+                if (ld_relaxed(a.err) & kErrTimeout) break;
+                if ((long long)(global_ns() - t0) > a.wait_ns) break;
+            }
+        }
+        if (timed_out) break;
+    }
+    if (__any_sync(kFull, timed_out)) {
+        if (lane == 0) atomicOr(a.err, kErrTimeout);
+        return false;
+    }
+    // the flags seen set were published with release stores: one acquire
+    // fence orders those tasks' writes before this task's reads and writes
+    fence_acquire();
+    __syncwarp();
+    TaskCells tc;
+    tc.g = &g; tc.sh = sh; tc.sl = sl; tc.cell_off = cell_off; tc.box = 0;
+    tc.A = A; tc.cA[0] = cA[0]; tc.cA[1] = cA[1]; tc.cA[2] = cA[2];
+    tc.group = 0; tc.dims = g.dims; tc.self = true; tc.nself = 1; tc.pairx = 0; tc.nnb = S.nh + 1;
+    LaneEnergy lt;
+    lt.s6 = make_float2(0.f, 0.f);
+    lt.s12 = make_float2(0.f, 0.f);
+    lt.d6 = lt.d12 = 0.0;
+    lt.pairs = 0;
+    if constexpr (MIXED) {
+        const NbPre pre = load_neighbours<kColourQ>(a, tc, lane);
+        commit_neighbours<WarpSmem<float>>(sm, tc, pre, lane);
+        run_task_mixed<NI, kColourQ, STATS, false>(a, sm, tc, pre, lane, lt);
+    } else {
+        run_task_fp64<NI, kColourQ, false>(a, sm, tc, lane, lt);
+    }
+    if (STATS) {
+        double s6 = MIXED ? (f32_to_f64_bits(lt.s6.x) - f32_to_f64_bits(lt.s6.y)) : lt.d6;
+        double s12 = MIXED ? (f32_to_f64_bits(lt.s12.x) - f32_to_f64_bits(lt.s12.y)) : lt.d12;
+        long long np = lt.pairs;
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) {
+            s6 += __shfl_xor_sync(kFull, s6, m);
+            s12 += __shfl_xor_sync(kFull, s12, m);
+            np += __shfl_xor_sync(kFull, np, m);
+        }
+        if (lane == 0) {
+            a.cell_acc[4 * (size_t)A + 0] = s6;
+            a.cell_acc[4 * (size_t)A + 1] = s12;
+            a.cell_pairs[A] = np;
+        }
+    }
+    __syncwarp();   // every lane's writes ordered before lane 0's release (cumulative)
+    if (lane == 0 && !a.withhold) st_release(a.cs_done + A, 1);
+    return true;
+}
+
 template <bool MIXED, int NI, int MODE, bool STATS, bool BATCHED, bool PX = false>
 __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
     using T = typename std::conditional<MIXED, float, double>::type;
@@ -991,7 +962,32 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
     le.s12 = make_float2(0.f, 0.f);
     le.d6 = le.d12 = 0.0;
     le.pairs = 0;
-    if constexpr (MIXED) {
+    if constexpr (MODE == kColourQ) {
+        // Colour schedule: the queue holds cell tasks in colour order
+        // (colour-major; a batch: colour, then box, then chunks of up to 8
+        // cells).  Cells of one colour write disjoint cells; a task first
+        // waits (bounded) until the earlier-coloured tasks of its box that
+        // could share a written cell have published -- they were claimed
+        // earlier, so running warps hold them -- then runs with plain writes.
+        for (;;) {
+            int q = 0;
+            if (lane == 0) q = atomicAdd(a.cs_ctrl, 1);
+            q = __shfl_sync(kFull, q, 0);
+            if (q >= a.ntasks) break;
+            bool ok = true;
+            if constexpr (BATCHED) {
+                const int4 it = a.cs_items[q];
+                const BoxDev &bd = a.boxes[it.x];
+                for (int i = 0; i < it.w && ok; ++i)
+                    ok = colour_task<MIXED, NI, STATS>(a, sm, bd.g, bd.sh, bd.sl, bd.cell_off, it.y, it.z + i, lane);
+            } else {
+                int k = 0;
+                while (q >= a.g.cs_first[k + 1]) ++k;
+                ok = colour_task<MIXED, NI, STATS>(a, sm, a.g, a.sh, a.sl, 0, k, q - a.g.cs_first[k], lane);
+            }
+            if (!ok) break;
+        }
+    } else if constexpr (MIXED) {
         for (int t = w; t < a.ntasks; t += W) {
             const TaskCells tc = make_task<MODE, BATCHED, PX>(a, t);
             const NbPre pre = load_neighbours<MODE, PX>(a, tc, lane);
@@ -1037,20 +1033,6 @@ struct DagArgs {
 };
 
 constexpr unsigned kDagMaxSpins = 1u << 24;   // second bound on one wait
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ int ld_acquire(const int *p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release(int *p, int v) {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 // Task (A, k): k = 0 the intra-cell interaction of A, k = 1..13 the pair
 // (A, A + half-shell offset k - 1).
@@ -1199,14 +1181,33 @@ __global__ void k_check(Grid g, int group, int colour, int ntasks, int phase, in
             int B = c[0] + g.nc[0] * (c[1] + g.nc[1] * c[2]);
             int oi = (o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1);   // 0..26
             atomicAdd(visit + (size_t)tc.A * 27 + oi, 1ull);
-            if (MODE == kColour && B != tc.A) {
-                int old = atomicExch(stamp + B, phase);
-                if (old == phase) atomicAdd(counters + 0, 1ull);
-            }
+            (void)B;
         }
-        if (MODE == kColour) {
-            int old = atomicExch(stamp + tc.A, phase);
-            if (old == phase) atomicAdd(counters + 0, 1ull);
+    }
+}
+
+// Replays the colour schedule's colour k: every cell A of colour k stamps the
+// cells its task writes (A and A + o for the forward offsets, all distinct)
+// with k; a cell stamped twice within one colour is written by two tasks of
+// that colour (a conflict).  Each task counts its visits of (A, o).
+__global__ void k_check_cs(Grid g, int k, int *stamp, unsigned long long *visit, unsigned long long *counters) {
+    const int raw = g.cs_raw_of_colour[k];
+    const int cls[3] = {raw % 5, (raw / 5) % 5, raw / 25};
+    const int n0 = cs_count(cls[0], g.nc[0], g.cs_p[0]), n1 = cs_count(cls[1], g.nc[1], g.cs_p[1]);
+    const int ntask = g.cs_first[k + 1] - g.cs_first[k];
+    const Stencil &S = stencil(g.dims);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntask; t += gridDim.x * blockDim.x) {
+        const int t3[3] = {t % n0, (t / n0) % n1, t / (n0 * n1)};
+        int cA[3];
+        for (int d = 0; d < 3; ++d) cA[d] = cs_coord(cls[d], t3[d], g.nc[d], g.cs_p[d]);
+        const size_t A = (size_t)cA[0] + g.nc[0] * ((size_t)cA[1] + g.nc[1] * (size_t)cA[2]);
+        for (int h = -1; h < S.nh; ++h) {
+            int o[3] = {0, 0, 0};
+            if (h >= 0) { o[0] = S.hs[h][0]; o[1] = S.hs[h][1]; o[2] = S.hs[h][2]; }
+            int c[3];
+            for (int d = 0; d < 3; ++d) c[d] = (cA[d] + o[d] + g.nc[d]) % g.nc[d];
+            if (atomicExch(stamp + c[0] + g.nc[0] * (c[1] + g.nc[1] * c[2]), k) == k) atomicAdd(counters + 0, 1ull);
+            atomicAdd(visit + A * 27 + (o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1), 1ull);
         }
     }
 }
@@ -1263,7 +1264,13 @@ template <bool MIXED, int NI, int MODE>
 static cudaError_t launch_mode(Ctx *c, ForceArgs &a, cudaStream_t s, bool stats) {
     // the FP64 comparator always accumulates its statistics; batches run
     // the centre-cell tile of 16 (atomic and full-shell schedules)
-    if constexpr (MODE != kColour && NI == 16) {
+    if constexpr (MODE == kColourQ && NI == 16) {
+        if (c->nbox > 0) {   // the colour queue over the boxes' cells
+            if (!MIXED || stats) return launch_one<MIXED, NI, MODE, true, true>(c, a, s);
+            return launch_one<MIXED, NI, MODE, (MIXED ? false : true), true>(c, a, s);
+        }
+    }
+    if constexpr (MODE != kColourQ && NI == 16) {
         if (c->nbox > 0) {
             if (!MIXED || stats) return launch_one<MIXED, NI, MODE, true, true>(c, a, s);
             return launch_one<MIXED, NI, MODE, (MIXED ? false : true), true>(c, a, s);
@@ -1316,26 +1323,27 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
     cudaError_t e = cudaSuccess;
     const size_t nbytes = sizeof(double) * (size_t)c->n;
     if (sched == LC_SCHED_COLOUR) {
+        // cell tasks in colour order on the device queue, plain writes
         if (MIXED) {
             e = cudaMemsetAsync(c->kx, 0, 3 * sizeof(float2) * (size_t)c->n, s);
         } else {
             e = cudaMemsetAsync(c->fx, 0, 3 * nbytes, s);
         }
         if (e) return e;
-        Stencil st;
-        make_stencil(&st, c->g.dims);
-        for (int g = 0; g < 4; ++g) {
-            if (g > 0 && st.group_first[g + 1] == st.group_first[g]) continue;   // no offsets (2D)
-            for (int k = 0; k < c->g.ncolours; ++k) {
-                a.group = g; a.colour = k;
-                int raw = c->g.raw_of_colour[k];
-                a.ntasks = c->g.class_count[0][raw % 3] * c->g.class_count[1][(raw / 3) % 3] *
-                           c->g.class_count[2][raw / 9];
-                e = launch_mode<MIXED, NI, kColour>(c, a, s, stats);
-                if (e) return e;
-                ++*launches;
-            }
-        }
+        a.ntasks = c->nbox > 0 ? c->cs_nitems : c->g.ncell;   // batch: items of up to 8 cells
+        if ((e = cudaMemsetAsync(c->d_cs_done, 0, sizeof(int) * (size_t)c->g.ncell, s))) return e;
+        if ((e = cudaMemsetAsync(c->d_cs_ctrl, 0, sizeof(int) * 2, s))) return e;
+        a.cs_done = c->d_cs_done;
+        a.cs_ctrl = c->d_cs_ctrl;
+        a.err = c->d_err;
+        a.wait_ns = (long long)(c->cs_wait_s * 1.0e9);
+        a.withhold = c->cs_withhold;
+        a.cell_acc = c->d_cell_acc;
+        a.cell_pairs = c->d_cell_pairs;
+        a.cs_items = c->d_cs_items;
+        e = launch_mode<MIXED, NI, kColourQ>(c, a, s, stats);
+        if (e) return e;
+        ++*launches;
         if (MIXED) {
             k_kahan_finalize<<<c->num_sms * 8, 256, 0, s>>>((int)c->n, c->kx, c->ky, c->kz, c->fx, c->fy, c->fz);
             ++*launches;
@@ -1464,7 +1472,11 @@ cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launch
     if (e) return e;
     if (stats) {
         c->stats_full = (sched == LC_SCHED_FULLSHELL);
-        e = c->nbox > 0 ? launch_box_energy(c, s, sched == LC_SCHED_FULLSHELL) : launch_energy_reduce(c, s, sched == LC_SCHED_FULLSHELL);
+        if (c->nbox > 0 && sched == LC_SCHED_COLOUR) e = launch_box_energy_cells(c, s);
+        else if (c->nbox > 0) e = launch_box_energy(c, s, sched == LC_SCHED_FULLSHELL);
+        else if (sched == LC_SCHED_COLOUR)   // per-cell partials, reduced in cell order
+            e = launch_energy_reduce_parts(c, s, 0, c->d_cell_acc, c->d_cell_pairs, c->g.ncell);
+        else e = launch_energy_reduce(c, s, sched == LC_SCHED_FULLSHELL);
         ++*launches;
     }
     return e;
@@ -1479,18 +1491,8 @@ cudaError_t launch_schedule_check(Ctx *c, lc_schedule sched, cudaStream_t s) {
     if (e) return e;
     const int blocks = c->num_sms * 4;
     if (sched == LC_SCHED_COLOUR) {
-        int phase = 0;
-        Stencil st;
-        make_stencil(&st, c->g.dims);
-        for (int g = 0; g < 4; ++g) {
-            if (g > 0 && st.group_first[g + 1] == st.group_first[g]) continue;
-            for (int k = 0; k < c->g.ncolours; ++k, ++phase) {
-                int raw = c->g.raw_of_colour[k];
-                int nt = c->g.class_count[0][raw % 3] * c->g.class_count[1][(raw / 3) % 3] *
-                         c->g.class_count[2][raw / 9];
-                k_check<kColour><<<blocks, 256, 0, s>>>(c->g, g, k, nt, phase, c->d_stamp, c->d_visit, c->d_counters);
-            }
-        }
+        for (int k = 0; k < c->g.cs_ncolours; ++k)
+            k_check_cs<<<blocks, 256, 0, s>>>(c->g, k, c->d_stamp, c->d_visit, c->d_counters);
     } else if (sched == LC_SCHED_ATOMIC || sched == LC_SCHED_BUFFER) {
         k_check<kAtomic><<<blocks, 256, 0, s>>>(c->g, 0, 0, c->g.ncell, 0, c->d_stamp, c->d_visit, c->d_counters);
     } else {
@@ -1504,13 +1506,14 @@ template <bool MIXED, int NI, bool STATS>
 static cudaError_t attrs_for() {
     cudaError_t e;
     const int bytes = (int)smem_bytes<MIXED, NI>(8);
-    if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kColour, STATS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kColourQ, STATS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
     if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kAtomic, STATS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
     if constexpr (MIXED)
         if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kAtomic, STATS, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
     if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kFullShell, STATS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
     if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kBuffer, STATS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
     if constexpr (NI == 16) {
+        if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kColourQ, STATS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
         if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kAtomic, STATS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
         if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kFullShell, STATS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
         if ((e = cudaFuncSetAttribute(k_force<MIXED, NI, kBuffer, STATS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;

@@ -51,6 +51,18 @@ struct Grid {
     int class_count[3][3];   // cells of colour class a along dimension d
     int colour_of_raw[27];   // raw colour cx + 3 cy + 9 cz -> colour rank (-1 absent)
     int raw_of_colour[27];   // inverse
+    // colour schedule (LC_SCHED_COLOUR): a cell's class along dimension d is
+    // c mod cs_p[d] for the cells of the full periods and a class of its own
+    // for each cell past the last full period; cs_p = 3 where the half-shell
+    // reaches both neighbours (x, y; x in 2D), 2 where it reaches one (z; y
+    // in 2D), so two cells of one class triple never write the same cell.
+    // Colour = rank of the triple's code a0 + 5 a1 + 25 a2 among those present.
+    int cs_p[3];
+    int cs_ncls[3];               // classes per dimension (at most cs_p + 2)
+    int cs_ncolours;
+    int cs_colour_of_raw[125];    // -1: absent
+    int cs_raw_of_colour[125];
+    int cs_first[126];            // queue position of the first cell of each colour
     // ceil(2^64 / nc_x) and ceil(2^64 / (nc_x nc_y)): the high word of
     // c * div is the exact quotient for every 32-bit cell index c
     unsigned long long divx, divxy;
@@ -75,6 +87,10 @@ struct Stencil {
     int group_first[5]; // offsets of group g are group_list[group_first[g] .. group_first[g+1])
     int group_list[13];
     int full[27][3];    // all offsets, centre first
+    // offsets between two cells whose half-shell tasks (centre + forward
+    // offsets) can write a common cell: differences of two stencil entries
+    int ndep;           // 62 (3D) / 12 (2D)
+    int dep[62][3];
 };
 
 void make_stencil(Stencil *s, int dims = 3);
@@ -149,6 +165,18 @@ struct Ctx {
     void *h_out;           // page-locked host copy of the block
     int nwarp_max;
     int nwarp_used;        // warps of the last force evaluation (their partials are reduced)
+    // colour schedule: per-cell completion flags, the queue counter and the
+    // per-cell energy partials (s6, s12, spare, spare) and pair counts
+    int *d_cs_done;        // [ncell]
+    int *d_cs_ctrl;        // [2]: next queue item, spare
+    double *d_cell_acc;    // [ncell][4]
+    long long *d_cell_pairs;   // [ncell]
+    double cs_wait_s;      // limit of one wait of the colour queue (seconds)
+    int cs_withhold;       // test: no task publishes its completion
+    // batch: colour-queue items (box, colour, first cell of the colour, cells),
+    // ordered by colour, then box
+    int4 *d_cs_items;
+    int cs_nitems;
     // check buffers
     int *d_stamp;
     unsigned long long *d_visit;
@@ -207,7 +235,12 @@ cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launch
 cudaError_t launch_kick(Ctx *c, double dt, cudaStream_t s);
 cudaError_t launch_kinetic(Ctx *c, cudaStream_t s);
 cudaError_t launch_energy_reduce(Ctx *c, cudaStream_t s, int full);
+// the same reduction over n partials given as [n][4] doubles and [n] pair counts
+cudaError_t launch_energy_reduce_parts(Ctx *c, cudaStream_t s, int full, const double *acc, const long long *pairs,
+                                       int n);
 cudaError_t launch_box_energy(Ctx *c, cudaStream_t s, int full);
+// per-box U, W and pairs from per-cell partials (colour schedule), fixed order
+cudaError_t launch_box_energy_cells(Ctx *c, cudaStream_t s);
 // Forces by executing a task DAG on the device (dependency counting, bounded
 // waits); trace: optional [2T] start / end stamps.
 // withhold != 0 publishes no ready task (a test of the bounded waits).
@@ -344,6 +377,18 @@ __device__ __forceinline__ bool cell_coord_fast(const Split &s, float Lf_lo, flo
 
 __host__ __device__ __forceinline__ int colour_class(int c, int nc) {
     return ((nc & 1) && c == nc - 1) ? 2 : (c & 1);
+}
+
+// Colour schedule: class of cell coordinate c along a dimension of nc cells
+// with class stride p, the number of cells of class a, and the coordinate of
+// the t-th cell of class a.
+__host__ __device__ __forceinline__ int cs_class(int c, int nc, int p) {
+    const int full = p * (nc / p);
+    return c < full ? c % p : p + (c - full);
+}
+__host__ __device__ __forceinline__ int cs_count(int a, int nc, int p) { return a < p ? nc / p : 1; }
+__host__ __device__ __forceinline__ int cs_coord(int a, int t, int nc, int p) {
+    return a < p ? a + p * t : p * (nc / p) + (a - p);
 }
 
 // Offset x - (c + 1/2) h of one coordinate from the centre of its cell c,

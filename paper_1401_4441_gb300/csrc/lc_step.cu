@@ -121,6 +121,44 @@ __global__ void __launch_bounds__(256) k_box_kinetic(const BoxDev *__restrict__ 
     if (threadIdx.x == 0) out[4 * blockIdx.x + 3] = 0.5 * red[0];
 }
 
+// Per-box statistics from per-cell partials: one block per box, its cells in
+// order, a fixed reduction tree (the same bits on every run).
+__global__ void __launch_bounds__(256) k_box_energy_cells(const BoxDev *__restrict__ boxes,
+                                                          const double *__restrict__ acc,
+                                                          const long long *__restrict__ pairs,
+                                                          double *__restrict__ out) {
+    __shared__ double r6[256], r12[256];
+    __shared__ long long rp[256];
+    const BoxDev &bd = boxes[blockIdx.x];
+    double a6 = 0.0, a12 = 0.0;
+    long long ap = 0;
+    for (int c = bd.cell_off + threadIdx.x; c < bd.cell_off + bd.g.ncell; c += blockDim.x) {
+        a6 += acc[4 * (size_t)c];
+        a12 += acc[4 * (size_t)c + 1];
+        ap += pairs[c];
+    }
+    r6[threadIdx.x] = a6; r12[threadIdx.x] = a12; rp[threadIdx.x] = ap;
+    __syncthreads();
+    for (int m = 128; m > 0; m >>= 1) {
+        if (threadIdx.x < m) {
+            r6[threadIdx.x] += r6[threadIdx.x + m];
+            r12[threadIdx.x] += r12[threadIdx.x + m];
+            rp[threadIdx.x] += rp[threadIdx.x + m];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[4 * blockIdx.x + 0] = 4.0 * (r12[0] - r6[0]);
+        out[4 * blockIdx.x + 1] = 24.0 * (2.0 * r12[0] - r6[0]);
+        out[4 * blockIdx.x + 2] = (double)rp[0];
+    }
+}
+
+cudaError_t launch_box_energy_cells(Ctx *c, cudaStream_t s) {
+    k_box_energy_cells<<<c->nbox, 256, 0, s>>>(c->d_boxes, c->d_cell_acc, c->d_cell_pairs, c->d_box_out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_box_energy(Ctx *c, cudaStream_t s, int full) {
     k_box_energy<<<(c->nbox + 255) / 256, 256, 0, s>>>(c->nbox, full, c->d_box_acc, c->d_box_pairs, c->d_box_out);
     return cudaGetLastError();
@@ -149,6 +187,12 @@ cudaError_t launch_kinetic(Ctx *c, cudaStream_t s) {
     cudaError_t e = cudaGetLastError();
     if (!e) c->kin_valid = true;
     return e;
+}
+
+cudaError_t launch_energy_reduce_parts(Ctx *c, cudaStream_t s, int full, const double *acc, const long long *pairs,
+                                       int n) {
+    k_final_pot<<<1, kRedThreads, 0, s>>>(n, acc, pairs, full, c->d_result, c->d_npairs);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_energy_reduce(Ctx *c, cudaStream_t s, int full) {

@@ -17,6 +17,7 @@ SCHED = {"colour": 0, "atomic": 1, "fullshell": 2, "buffer": 3, "list": 4}
 PREC = {"fp64": 0, "mixed": 1}
 ORDER = {"cell": 0, "loopex": 1}
 DAG_WITHHOLD = 1
+QUEUE_WITHHOLD = 1
 GET = {"cell_count": 0, "cell_start": 1, "perm": 2, "colour": 3, "forces": 4, "pos": 5, "vel": 6}
 STATUS = {0: "LC_OK", 1: "LC_ERR_INVALID_ARG", 2: "LC_ERR_BOX_TOO_SMALL", 3: "LC_ERR_CUDA",
           4: "LC_ERR_OOM", 5: "LC_ERR_NONFINITE", 6: "LC_ERR_TIMEOUT", 7: "LC_ERR_STATE",
@@ -69,6 +70,8 @@ def _load():
         "lc_result_decode": ([vp, dp, dp, dp, lp], ctypes.c_int),
         "lc_set_skin": ([vp, ctypes.c_double, ctypes.c_int32], ctypes.c_int),
         "lc_list_info": ([vp, lp, lp, lp, lp, lp, ip, vp], ctypes.c_int),
+        "lc_batch_step": ([vp, ctypes.c_double, ctypes.c_int32, vp], ctypes.c_int),
+        "lc_set_queue_wait": ([vp, ctypes.c_double, ctypes.c_int32], ctypes.c_int),
         "lc_destroy": ([vp], None),
         "lc_status_str": ([ctypes.c_int], ctypes.c_char_p),
     }
@@ -303,6 +306,12 @@ class Box:
         return {"builds": v[0].value, "long_rows": v[1].value, "longest_row": v[2].value,
                 "rebuild_steps": v[3].value, "entries": v[4].value, "kmax": km.value}
 
+    def set_queue_wait(self, seconds=2.0, withhold=False):
+        """Limit of one wait of the colour schedule's queue; withhold: no task
+        publishes its completion (a test of the bounded waits)."""
+        _check(self._lib.lc_set_queue_wait(self._h, float(seconds), QUEUE_WITHHOLD if withhold else 0),
+               "lc_set_queue_wait")
+
     def set_tile(self, ni=0, warps=0):
         _check(self._lib.lc_set_tile(self._h, int(ni), int(warps)), "lc_set_tile")
 
@@ -314,7 +323,7 @@ class Box:
 
 class Batch(Box):
     """Independent periodic boxes in one context (lc_batch_create): particles
-    numbered box after box; atomic or full-shell schedule."""
+    numbered box after box; every schedule but the lists."""
 
     def __init__(self, boxes, rcs, ns, precision="mixed"):
         self._lib = _load()
@@ -334,6 +343,11 @@ class Batch(Box):
                                          ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                          PREC[precision], ctypes.byref(h)), "lc_batch_create")
         self._h = h
+
+    def step(self, dt, nsteps, stream=None):
+        """lc_batch_step: Verlet steps of every box, colour schedule on the
+        device work queue."""
+        _check(self._lib.lc_batch_step(self._h, float(dt), int(nsteps), _stream(stream)), "lc_batch_step")
 
     def energies(self, stream=None):
         """Per-box (U, K, W, npairs) arrays."""

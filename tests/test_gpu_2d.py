@@ -10,6 +10,7 @@ import pytest
 import oracle
 from oracle import dag as odag
 from paper_1401_4441_gb300 import inputs
+from test_colour_cells import colours as schedule_colours
 
 pytestmark = pytest.mark.gpu
 
@@ -72,7 +73,7 @@ def test_2d_perfect_lattice_and_grid(lc):
     with lc.Box(b["box"], RC, b["pos"].shape[0], "mixed", dims=2) as g:
         g.set_state(b["pos"])
         nc, ncol, nph = g.grid()
-        assert nc[2] == 1 and ncol == 4 and nph == 8       # 2 offset groups x 4 colours
+        assert nc[2] == 1 and ncol == 4 and nph == schedule_colours(nc, dims=2)
         for sched in SCHEDS:
             g.forces(sched)
             f = g.get("forces")
