@@ -165,8 +165,9 @@ __device__ __forceinline__ void single_task(const Grid &g, int group, int colour
     }
 }
 
+// sh / sl: the single box's shift tables (a shared-memory copy of a.sh / a.sl)
 template <int MODE, bool BATCHED, bool PX = false>
-__device__ __forceinline__ TaskCells make_task(const ForceArgs &a, int t) {
+__device__ __forceinline__ TaskCells make_task(const ForceArgs &a, int t, const float (*sh)[3], const float (*sl)[3]) {
     TaskCells tc;
     if constexpr (BATCHED) {
         // task t = global cell t of the batch (atomic and full-shell schedules)
@@ -182,7 +183,7 @@ __device__ __forceinline__ TaskCells make_task(const ForceArgs &a, int t) {
         tc.pairx = 0;
         tc.nnb = (MODE == kFullShell) ? 27 : 14;
     } else {
-        tc.g = &a.g; tc.sh = a.sh; tc.sl = a.sl; tc.cell_off = 0; tc.box = 0;
+        tc.g = &a.g; tc.sh = sh; tc.sl = sl; tc.cell_off = 0; tc.box = 0;
         single_task<MODE>(a.g, a.group, a.colour, t, tc, PX ? 1 : 0);
     }
     return tc;
@@ -216,19 +217,36 @@ __device__ __forceinline__ double to_f64(T v) {
 
 // One task's partial force on one particle enters its accumulator: the FP32
 // partial v and, for the mixed path, the FP64 sum c of its close pairs.
+// (The close-pair sum is nonzero only for the rare close pairs: it is added
+// on a separate path, so the common one does no FP64 arithmetic, which runs
+// at a small fraction of the FP32 rate on this GPU.)
 template <int MODE, bool MIXED, typename T>
 __device__ __forceinline__ void write_force(const ForceArgs &a, int slot, T vx, T vy, T vz, double cx = 0.0,
                                             double cy = 0.0, double cz = 0.0) {
-    if constexpr (MODE == kAtomic) {
-        atomicAdd(a.fx + slot, to_f64(vx) + cx);
-        atomicAdd(a.fy + slot, to_f64(vy) + cy);
-        atomicAdd(a.fz + slot, to_f64(vz) + cz);
+    const bool close = MIXED && nonzero3(cx, cy, cz);
+    // kColourQ: the tasks that touch a cell never run at the same time and
+    // run in the order the queue's dependences fix, so these adds neither
+    // conflict nor change order from run to run; the L2's reduction units
+    // perform them (RED), so the warp does not wait for the read
+    if constexpr (MODE == kAtomic || MODE == kColourQ) {
+        atomicAdd(a.fx + slot, to_f64(vx));
+        atomicAdd(a.fy + slot, to_f64(vy));
+        atomicAdd(a.fz + slot, to_f64(vz));
+        if (close) {
+            atomicAdd(a.fx + slot, cx);
+            atomicAdd(a.fy + slot, cy);
+            atomicAdd(a.fz + slot, cz);
+        }
     } else if constexpr (MODE == kFullShell) {
-        a.fx[slot] = to_f64(vx) + cx; a.fy[slot] = to_f64(vy) + cy; a.fz[slot] = to_f64(vz) + cz;
+        if (close) {
+            a.fx[slot] = to_f64(vx) + cx; a.fy[slot] = to_f64(vy) + cy; a.fz[slot] = to_f64(vz) + cz;
+        } else {
+            a.fx[slot] = to_f64(vx); a.fy[slot] = to_f64(vy); a.fz[slot] = to_f64(vz);
+        }
     } else if constexpr (MIXED) {
         float2 kx = a.kx[slot], ky = a.ky[slot], kz = a.kz[slot];
         kahan_add(kx, (float)vx); kahan_add(ky, (float)vy); kahan_add(kz, (float)vz);
-        if (cx != 0.0 || cy != 0.0 || cz != 0.0) { kahan_add64(kx, cx); kahan_add64(ky, cy); kahan_add64(kz, cz); }
+        if (close) { kahan_add64(kx, cx); kahan_add64(ky, cy); kahan_add64(kz, cz); }
         a.kx[slot] = kx; a.ky[slot] = ky; a.kz[slot] = kz;
     } else {
         a.fx[slot] += vx; a.fy[slot] += vy; a.fz[slot] += vz;
@@ -511,6 +529,7 @@ __device__ __forceinline__ int prune_list(const ForceArgs &a, WarpSmem<float> &s
         // kPruneRounds rounds per step: all their loads in flight before any test
         int w[kPruneRounds];
         float4 p[kPruneRounds];
+        const int rounds = min(kPruneRounds, (total - e0 + kWarp - 1) / kWarp);   // warp-uniform
 #pragma unroll
         for (int r = 0; r < kPruneRounds; ++r) {
             const int e = e0 + r * kWarp + lane;
@@ -520,6 +539,7 @@ __device__ __forceinline__ int prune_list(const ForceArgs &a, WarpSmem<float> &s
         }
 #pragma unroll
         for (int r = 0; r < kPruneRounds; ++r) {
+            if (r >= rounds) break;   // rounds past the list's end
             const int e = e0 + r * kWarp + lane;
             bool k;
             prune_test<MODE>(a, sm, e, total, bmin, bmax, keep2, first_chunk, w[r], p[r], k);
@@ -554,9 +574,14 @@ __device__ __forceinline__ void write_i_chunk(const ForceArgs &a, S &sm, T (&ax)
                 ax[0] += sm.corr[elem][0]; ay[0] += sm.corr[elem][1]; az[0] += sm.corr[elem][2];
                 c[0] = sm.corr64[elem][0]; c[1] = sm.corr64[elem][1]; c[2] = sm.corr64[elem][2];
             }
-            if constexpr (MODE == kBuffer)
-                buffer_store<T>(a, kIBuf, a0 + ii, false, ax[0] + (T)c[0], ay[0] + (T)c[1], az[0] + (T)c[2]);
-            else write_force<MODE, MIXED, T>(a, a0 + ii, ax[0], ay[0], az[0], c[0], c[1], c[2]);
+            if constexpr (MODE == kBuffer) {
+                if (nonzero3(c[0], c[1], c[2])) {
+                    ax[0] += (T)c[0]; ay[0] += (T)c[1]; az[0] += (T)c[2];
+                }
+                buffer_store<T>(a, kIBuf, a0 + ii, false, ax[0], ay[0], az[0]);
+            } else {
+                write_force<MODE, MIXED, T>(a, a0 + ii, ax[0], ay[0], az[0], c[0], c[1], c[2]);
+            }
         }
     }
     __syncwarp();
@@ -748,9 +773,14 @@ __device__ void run_task_mixed(const ForceArgs &a, WarpSmem<float> &sm, const Ta
                     }
                 }
                 if (N3 && valid) {
-                    if constexpr (MODE == kBuffer)
-                        buffer_store<float>(a, nb, sj, i0 > 0, fjx + (float)cj[0], fjy + (float)cj[1], fjz + (float)cj[2]);
-                    else write_force<MODE, true, float>(a, sj, fjx, fjy, fjz, cj[0], cj[1], cj[2]);
+                    if constexpr (MODE == kBuffer) {
+                        if (nonzero3(cj[0], cj[1], cj[2])) {
+                            fjx += (float)cj[0]; fjy += (float)cj[1]; fjz += (float)cj[2];
+                        }
+                        buffer_store<float>(a, nb, sj, i0 > 0, fjx, fjy, fjz);
+                    } else {
+                        write_force<MODE, true, float>(a, sj, fjx, fjy, fjz, cj[0], cj[1], cj[2]);
+                    }
                 }
             }
             __syncwarp();
@@ -962,6 +992,14 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
     le.s12 = make_float2(0.f, 0.f);
     le.d6 = le.d12 = 0.0;
     le.pairs = 0;
+    // the single box's shift tables in shared memory: the lanes of a task
+    // read them with 14 different indices, which parameter space serialises
+    __shared__ float s_sh[27][3], s_sl[27][3];
+    for (int k = threadIdx.x; k < 81; k += blockDim.x) {
+        (&s_sh[0][0])[k] = (&a.sh[0][0])[k];
+        (&s_sl[0][0])[k] = (&a.sl[0][0])[k];
+    }
+    __syncthreads();
     if constexpr (MODE == kColourQ) {
         // Colour schedule: the queue holds cell tasks in colour order
         // (colour-major; a batch: colour, then box, then chunks of up to 8
@@ -983,20 +1021,20 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
             } else {
                 int k = 0;
                 while (q >= a.g.cs_first[k + 1]) ++k;
-                ok = colour_task<MIXED, NI, STATS>(a, sm, a.g, a.sh, a.sl, 0, k, q - a.g.cs_first[k], lane);
+                ok = colour_task<MIXED, NI, STATS>(a, sm, a.g, s_sh, s_sl, 0, k, q - a.g.cs_first[k], lane);
             }
             if (!ok) break;
         }
     } else if constexpr (MIXED) {
         for (int t = w; t < a.ntasks; t += W) {
-            const TaskCells tc = make_task<MODE, BATCHED, PX>(a, t);
+            const TaskCells tc = make_task<MODE, BATCHED, PX>(a, t, s_sh, s_sl);
             const NbPre pre = load_neighbours<MODE, PX>(a, tc, lane);
             commit_neighbours<WarpSmem<float>, PX>(sm, tc, pre, lane);
             run_task_mixed<NI, MODE, STATS, BATCHED, PX>(a, sm, tc, pre, lane, le);
         }
     } else {
         for (int t = w; t < a.ntasks; t += W) {
-            TaskCells tc = make_task<MODE, BATCHED>(a, t);
+            TaskCells tc = make_task<MODE, BATCHED>(a, t, s_sh, s_sl);
             run_task_fp64<NI, MODE, BATCHED>(a, sm, tc, lane, le);
         }
     }
@@ -1323,12 +1361,8 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
     cudaError_t e = cudaSuccess;
     const size_t nbytes = sizeof(double) * (size_t)c->n;
     if (sched == LC_SCHED_COLOUR) {
-        // cell tasks in colour order on the device queue, plain writes
-        if (MIXED) {
-            e = cudaMemsetAsync(c->kx, 0, 3 * sizeof(float2) * (size_t)c->n, s);
-        } else {
-            e = cudaMemsetAsync(c->fx, 0, 3 * nbytes, s);
-        }
+        // cell tasks in colour order on the device queue
+        e = cudaMemsetAsync(c->fx, 0, 3 * nbytes, s);
         if (e) return e;
         a.ntasks = c->nbox > 0 ? c->cs_nitems : c->g.ncell;   // batch: items of up to 8 cells
         if ((e = cudaMemsetAsync(c->d_cs_done, 0, sizeof(int) * (size_t)c->g.ncell, s))) return e;
@@ -1344,11 +1378,6 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
         e = launch_mode<MIXED, NI, kColourQ>(c, a, s, stats);
         if (e) return e;
         ++*launches;
-        if (MIXED) {
-            k_kahan_finalize<<<c->num_sms * 8, 256, 0, s>>>((int)c->n, c->kx, c->ky, c->kz, c->fx, c->fy, c->fz);
-            ++*launches;
-            e = cudaGetLastError();
-        }
     } else if (sched == LC_SCHED_ATOMIC) {
         e = cudaMemsetAsync(c->fx, 0, 3 * nbytes, s);
         if (e) return e;

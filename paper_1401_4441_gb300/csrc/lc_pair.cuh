@@ -213,6 +213,16 @@ __device__ __forceinline__ double pair_force_f64(const double *x, const double *
     return s6;
 }
 
+// Whether any of three FP64 values is nonzero, by integer operations on
+// their bits (a zero of either sign has no bit set below the sign): FP64
+// compares would run on the FP64 pipe, a small fraction of the FP32 rate.
+__device__ __forceinline__ bool nonzero3(double a, double b, double c) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(a) |
+                                    (unsigned long long)__double_as_longlong(b) |
+                                    (unsigned long long)__double_as_longlong(c);
+    return (bits << 1) != 0ull;
+}
+
 // Adds an FP64 value to an FP32 Kahan pair (sum, compensation): as its
 // rounded FP32 value and the FP32 rounding of the rest.
 __device__ __forceinline__ void kahan_add64(float2 &acc, double v) {
