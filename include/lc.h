@@ -332,8 +332,10 @@ lc_status lc_launch_counts(const lc_ctx *ctx, int32_t *per_force, int32_t *per_s
  * edges, cutoff and particle count) and runs every stage over all boxes in
  * one launch: binning, the force sweep, integration.  With LC_SCHED_COLOUR
  * the force sweep is one persistent launch fed by a device work queue whose
- * items are (colour, box, up to 8 cells of that colour), ordered by colour
- * and then box, so that the boxes interleave: a cell task waits only for the
+ * items are single cell tasks (box, colour, cell).  The (box, colour) groups
+ * are ordered by the colour's position k / colours(box) in its box's chain,
+ * so the boxes interleave and every box's chain advances at the same pace;
+ * within a box the order is colour-major.  A cell task waits only for the
  * earlier-coloured tasks of its own box that could write a common cell
  * (bounded waits, LC_ERR_TIMEOUT), and the per-box energies are summed in a
  * fixed order.

@@ -6,6 +6,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+#include <algorithm>
+#include <utility>
 #include "lc_internal.cuh"
 
 namespace lc {
@@ -193,7 +196,7 @@ static cudaError_t dalloc(T **p, size_t count) {
 static void free_ctx(Ctx *c) {
     if (!c) return;
     void *ptrs[] = {c->cur.x, c->cur.vx, c->cur.id, c->nxt.x, c->nxt.vx, c->nxt.id, c->d_cell, c->d_rank,
-                    c->d_count, c->d_start, c->d_src, c->d_key, c->d_blocksums, c->d_colour, c->d_p4, c->fx, c->kx,
+                    c->d_count, c->d_start, c->d_src, c->d_key, c->d_cellt, c->d_blocksums, c->d_colour, c->d_p4, c->fx, c->kx,
                     c->d_warp_acc, c->d_warp_pairs, c->d_kin_part, c->d_result,
                     c->d_stamp, c->d_visit, c->d_counters, c->d_boxes, c->d_cell_box, c->d_slot_box,
                     c->d_box_acc, c->d_box_pairs, c->d_box_out, c->d_fbuf, c->d_nbr, c->d_nn, c->d_q4,
@@ -238,7 +241,7 @@ static cudaError_t alloc_common(Ctx *c) {
     c->nwarp_max = c->num_sms * 64;
     if ((e = upload_stencil(st, st2)) || (e = alloc_state(&c->cur, n)) || (e = alloc_state(&c->nxt, n)) ||
         (e = dalloc(&c->d_cell, N)) || (e = dalloc(&c->d_rank, N)) || (e = dalloc(&c->d_count, NC)) ||
-        (e = dalloc(&c->d_start, 2 * (NC + 1))) || (e = dalloc(&c->d_src, N)) || (e = dalloc(&c->d_key, N)) ||
+        (e = dalloc(&c->d_start, 2 * (NC + 1))) || (e = dalloc(&c->d_src, N)) || (e = dalloc(&c->d_key, N)) || (e = dalloc(&c->d_cellt, N)) ||
         (e = dalloc(&c->d_blocksums, (size_t)ntiles + 1)) || (e = dalloc(&c->d_colour, NC)) ||
         (e = dalloc(&c->d_p4, N)) || (e = dalloc(&c->fx, 3 * N)) || (e = dalloc(&c->kx, 3 * N)) ||
         (e = dalloc(&c->d_warp_acc, 4 * (size_t)c->nwarp_max)) || (e = dalloc(&c->d_warp_pairs, (size_t)c->nwarp_max)) ||
@@ -394,25 +397,35 @@ lc_status lc_batch_create(int32_t nbox, const double *box, const double *rc, con
         for (int k = 0; k < bd.g.ncell; ++k) cb[bd.cell_off + k] = (unsigned short)b;
         for (int k = 0; k < bd.n; ++k) sb[bd.part_off + k] = (unsigned short)b;
     }
-    // colour-queue items: for each colour rank, every box that has it, its
-    // cells of that colour in chunks of up to 8
-    int maxcol = 0;
+    // colour-queue items, one cell each.  A box's colours form a chain (a
+    // cell waits for its earlier-coloured neighbours), and boxes have from 8
+    // to 48 colours: the (box, colour) groups are ordered by the colour's
+    // position within its box's chain, k / colours(box), so every box's chain
+    // advances at the same pace through the queue and the long chains of the
+    // many-coloured small boxes do not end up alone at its tail.  Within a
+    // box the order stays colour-major, so a waited-for task was claimed
+    // earlier (no deadlock).
+    std::vector<std::pair<double, std::pair<int, int>>> groups;
     int64_t nitems = 0;
     for (int b = 0; b < nbox; ++b) {
         const Grid &gb = c->h_boxes[b].g;
-        if (gb.cs_ncolours > maxcol) maxcol = gb.cs_ncolours;
-        for (int k = 0; k < gb.cs_ncolours; ++k) nitems += (gb.cs_first[k + 1] - gb.cs_first[k] + 7) / 8;
+        for (int k = 0; k < gb.cs_ncolours; ++k) {
+            groups.push_back({(double)k / gb.cs_ncolours, {b, k}});
+            nitems += gb.cs_first[k + 1] - gb.cs_first[k];
+        }
     }
+    std::stable_sort(groups.begin(), groups.end(),
+                     [](const std::pair<double, std::pair<int, int>> &x,
+                        const std::pair<double, std::pair<int, int>> &y) { return x.first < y.first; });
     int4 *items = (int4 *)malloc(sizeof(int4) * (size_t)(nitems > 0 ? nitems : 1));
     if (!items) { free(cb); free(sb); free_ctx(c); return LC_ERR_OOM; }
     int64_t q = 0;
-    for (int k = 0; k < maxcol; ++k)
-        for (int b = 0; b < nbox; ++b) {
-            const Grid &gb = c->h_boxes[b].g;
-            if (k >= gb.cs_ncolours) continue;
-            const int cells = gb.cs_first[k + 1] - gb.cs_first[k];
-            for (int t0 = 0; t0 < cells; t0 += 8) items[q++] = make_int4(b, k, t0, cells - t0 < 8 ? cells - t0 : 8);
-        }
+    for (const auto &gr : groups) {
+        const int b = gr.second.first, k = gr.second.second;
+        const Grid &gb = c->h_boxes[b].g;
+        const int cells = gb.cs_first[k + 1] - gb.cs_first[k];
+        for (int t = 0; t < cells; ++t) items[q++] = make_int4(b, k, t, 1);
+    }
     c->cs_nitems = (int)nitems;
     e = dalloc(&c->d_cs_items, (size_t)(nitems > 0 ? nitems : 1));
     if (!e && nitems > 0) e = cudaMemcpy(c->d_cs_items, items, sizeof(int4) * (size_t)nitems, cudaMemcpyHostToDevice);

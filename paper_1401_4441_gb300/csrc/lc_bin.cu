@@ -205,32 +205,33 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles_ticket(int ncell, c
 __global__ void k_scatter_starts(int n, int ncell, const int *__restrict__ cell, const int *__restrict__ rank,
                                  const int *__restrict__ local, const int *__restrict__ partial,
                                  const int *__restrict__ id, int *__restrict__ src, int *__restrict__ key,
-                                 int *__restrict__ start) {
+                                 int *__restrict__ start, int *__restrict__ cellt) {
     const int stride = gridDim.x * blockDim.x;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += stride) {
         const int c = cell[s];
         const int t = local[c] + partial[c / kScanTile] + rank[s];
         src[t] = s;
         key[t] = id ? id[s] : s;
+        if (cellt) cellt[t] = c;
     }
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += stride)
         start[c] = local[c] + partial[c / kScanTile];
     if (blockIdx.x == 0 && threadIdx.x == 0) start[ncell] = n;
 }
 
-// One thread per slot t of the new order.  Rank = number of the cell's
+// One thread per slot t of the new order (its cell from the scatter).  Rank = number of the cell's
 // particles with a smaller ID (IDs are unique), so slot = start + rank is
 // stable by ID whatever order the atomics were served in.
 template <bool BATCHED>
 __global__ void k_rank_gather(Grid g1, const BoxDev *__restrict__ boxes, const unsigned short *__restrict__ slot_box,
                               int n, int write_p4, const int *__restrict__ start,
-                              const int *__restrict__ count, const int *__restrict__ cell,
+                              const int *__restrict__ count, const int *__restrict__ cellt,
                               const int *__restrict__ src, const int *__restrict__ key, State in, State out,
                               float4 *__restrict__ p4) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         const int s = src[t];
         const int my_id = key[t];
-        const int c = cell[s];
+        const int c = cellt[t];   // written by the scatter: no dependent gather through src
         // the particle's state is loaded before the rank loop so that its
         // latency overlaps the key loads
         double X[3] = {in.x[s], in.y[s], in.z[s]};
@@ -330,17 +331,17 @@ cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches, int kicks, double 
     unsigned *ticket = reinterpret_cast<unsigned *>(c->d_blocksums + ntiles);
     k_scan_tiles_ticket<<<ntiles, kScanThreads, 0, s>>>(ncell, c->d_count, local, c->d_blocksums, ticket);
     k_scatter_starts<<<grid_n, 256, 0, s>>>(n, ncell, c->d_cell, c->d_rank, local, c->d_blocksums, c->cur.id,
-                                            c->d_src, c->d_key, c->d_start);
+                                            c->d_src, c->d_key, c->d_start, c->d_cellt);
     *launches += 2;
     if (n > 0) {
         static int per_sm_b = 0, per_sm_s = 0;
         if (c->nbox > 0)
             k_rank_gather<true><<<one_wave(c, k_rank_gather<true>, &per_sm_b), 256, 0, s>>>(
-                c->g, c->d_boxes, c->d_slot_box, n, c->prec == LC_PREC_MIXED, c->d_start, c->d_count, c->d_cell,
+                c->g, c->d_boxes, c->d_slot_box, n, c->prec == LC_PREC_MIXED, c->d_start, c->d_count, c->d_cellt,
                 c->d_src, c->d_key, c->cur, c->nxt, c->d_p4);
         else
             k_rank_gather<false><<<one_wave(c, k_rank_gather<false>, &per_sm_s), 256, 0, s>>>(
-                c->g, nullptr, nullptr, n, c->prec == LC_PREC_MIXED, c->d_start, c->d_count, c->d_cell, c->d_src,
+                c->g, nullptr, nullptr, n, c->prec == LC_PREC_MIXED, c->d_start, c->d_count, c->d_cellt, c->d_src,
                 c->d_key, c->cur, c->nxt, c->d_p4);
         *launches += 1;
     }

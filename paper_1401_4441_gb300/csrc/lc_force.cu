@@ -556,11 +556,40 @@ __device__ __forceinline__ int prune_list(const ForceArgs &a, WarpSmem<float> &s
     return nk;
 }
 
-// Reduce-scatter the i chunk's per-lane partials and let the owner lanes
-// write them (plus the near-r_c corrections of the mixed path).
+// Sum the i chunk's per-lane partials over the lanes and let the owner
+// lanes write them (plus the near-r_c corrections of the mixed path).
+// Mixed: column sums through the pruned-data scratch (free once the chunk
+// loop has run; the next i chunk prunes again), lane l < NI owning element
+// l.  FP64: a shuffle reduce-scatter.
 template <bool MIXED, int NI, int MODE, typename T, typename S>
 __device__ __forceinline__ void write_i_chunk(const ForceArgs &a, S &sm, T (&ax)[NI], T (&ay)[NI], T (&az)[NI],
                                               int a0, int i0, int na, int lane) {
+    if constexpr (MIXED) {
+        float *scratch = reinterpret_cast<float *>(sm.jd);
+        static_assert(sizeof(sm.jd) >= sizeof(float) * 32 * kColStride, "column-sum scratch");
+        const float sx = column_sum<NI>(ax, scratch, lane);
+        const float sy = column_sum<NI>(ay, scratch, lane);
+        const float sz = column_sum<NI>(az, scratch, lane);
+        __syncwarp();   // order the j-side writes to A before the i-side ones; the scratch is free again
+        if (lane < NI) {
+            const int ii = i0 + lane;
+            if (ii < na) {
+                const float vx = sx + sm.corr[lane][0], vy = sy + sm.corr[lane][1], vz = sz + sm.corr[lane][2];
+                const double c[3] = {sm.corr64[lane][0], sm.corr64[lane][1], sm.corr64[lane][2]};
+                if constexpr (MODE == kBuffer) {
+                    float wx = vx, wy = vy, wz = vz;
+                    if (nonzero3(c[0], c[1], c[2])) {
+                        wx += (float)c[0]; wy += (float)c[1]; wz += (float)c[2];
+                    }
+                    buffer_store<float>(a, kIBuf, a0 + ii, false, wx, wy, wz);
+                } else {
+                    write_force<MODE, true, float>(a, a0 + ii, vx, vy, vz, c[0], c[1], c[2]);
+                }
+            }
+        }
+        __syncwarp();
+        return;
+    }
     reduce_scatter<T, NI>(ax, lane);
     reduce_scatter<T, NI>(ay, lane);
     reduce_scatter<T, NI>(az, lane);
@@ -569,18 +598,10 @@ __device__ __forceinline__ void write_i_chunk(const ForceArgs &a, S &sm, T (&ax)
     if ((lane & ((32 / NI) - 1)) == 0) {
         const int ii = i0 + elem;
         if (ii < na) {
-            double c[3] = {0.0, 0.0, 0.0};
-            if constexpr (MIXED) {
-                ax[0] += sm.corr[elem][0]; ay[0] += sm.corr[elem][1]; az[0] += sm.corr[elem][2];
-                c[0] = sm.corr64[elem][0]; c[1] = sm.corr64[elem][1]; c[2] = sm.corr64[elem][2];
-            }
             if constexpr (MODE == kBuffer) {
-                if (nonzero3(c[0], c[1], c[2])) {
-                    ax[0] += (T)c[0]; ay[0] += (T)c[1]; az[0] += (T)c[2];
-                }
                 buffer_store<T>(a, kIBuf, a0 + ii, false, ax[0], ay[0], az[0]);
             } else {
-                write_force<MODE, MIXED, T>(a, a0 + ii, ax[0], ay[0], az[0], c[0], c[1], c[2]);
+                write_force<MODE, MIXED, T>(a, a0 + ii, ax[0], ay[0], az[0]);
             }
         }
     }
@@ -1002,8 +1023,9 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
     __syncthreads();
     if constexpr (MODE == kColourQ) {
         // Colour schedule: the queue holds cell tasks in colour order
-        // (colour-major; a batch: colour, then box, then chunks of up to 8
-        // cells).  Cells of one colour write disjoint cells; a task first
+        // (colour-major; a batch: (box, colour) groups by the colour's
+        // position in its box's chain, one cell per item).  Cells of one
+        // colour write disjoint cells; a task first
         // waits (bounded) until the earlier-coloured tasks of its box that
         // could share a written cell have published -- they were claimed
         // earlier, so running warps hold them -- then runs with plain writes.
@@ -1364,7 +1386,7 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
         // cell tasks in colour order on the device queue
         e = cudaMemsetAsync(c->fx, 0, 3 * nbytes, s);
         if (e) return e;
-        a.ntasks = c->nbox > 0 ? c->cs_nitems : c->g.ncell;   // batch: items of up to 8 cells
+        a.ntasks = c->nbox > 0 ? c->cs_nitems : c->g.ncell;   // batch: one item per cell
         if ((e = cudaMemsetAsync(c->d_cs_done, 0, sizeof(int) * (size_t)c->g.ncell, s))) return e;
         if ((e = cudaMemsetAsync(c->d_cs_ctrl, 0, sizeof(int) * 2, s))) return e;
         a.cs_done = c->d_cs_done;

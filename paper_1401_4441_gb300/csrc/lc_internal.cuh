@@ -146,6 +146,7 @@ struct Ctx {
     int *d_count;          // [ncell]
     int *d_start;          // [ncell + 1]
     int *d_src;            // slot -> index in the previous order
+    int *d_cellt;          // slot -> its cell (written with d_src)
     int *d_key;            // slot -> particle ID (before the final ranking)
     int *d_blocksums;      // scan partials
     int8_t *d_colour;      // [ncell]
@@ -275,10 +276,12 @@ constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanThreads * kScanItems;
 __global__ void k_scan_tiles_ticket(int ncell, const int *__restrict__ count, int *__restrict__ local, int *partial,
                                     unsigned *ticket);
+// cellt (optional): the cell of each provisional slot, read by k_rank_gather
+// instead of a dependent gather of cell[src[t]]
 __global__ void k_scatter_starts(int n, int ncell, const int *__restrict__ cell, const int *__restrict__ rank,
                                  const int *__restrict__ local, const int *__restrict__ partial,
                                  const int *__restrict__ id, int *__restrict__ src, int *__restrict__ key,
-                                 int *__restrict__ start);
+                                 int *__restrict__ start, int *__restrict__ cellt = nullptr);
 
 // ---- small device helpers ----------------------------------------------------
 // v^2 of one particle, each operation rounded once (no contraction), and the

@@ -75,6 +75,31 @@ __device__ __forceinline__ void reduce_scatter(T (&v)[NI], int lane) {
     for (int m = 16 / NI; m >= 1; m >>= 1) v[0] += __shfl_xor_sync(kFull, v[0], m);
 }
 
+// Sum over the 32 lanes of every lane's NI partials through per-warp shared
+// scratch s (32 * 17 floats; the odd row stride makes both the row writes
+// and the column reads free of bank conflicts): lane (i, g) = (lane mod NI,
+// lane / NI) adds rows g NI .. g NI + NI - 1 of column i, then the 32 / NI
+// group sums are added by a butterfly over g.  Lanes l < NI return the sum
+// of element l.  A fixed order: the same bits on every run.  Unlike the
+// shuffle butterfly the loads and adds of one column are independent, so
+// they overlap.
+constexpr int kColStride = 17;
+template <int NI>
+__device__ __forceinline__ float column_sum(const float (&v)[NI], float *s, int lane) {
+    __syncwarp();   // the scratch's previous readers are done
+#pragma unroll
+    for (int i = 0; i < NI; ++i) s[lane * kColStride + i] = v[i];
+    __syncwarp();
+    const float *col = s + (lane / NI) * NI * kColStride + (lane & (NI - 1));
+    float t[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int r = 0; r < NI; ++r) t[r & 3] += col[r * kColStride];
+    float sum = (t[0] + t[1]) + (t[2] + t[3]);
+#pragma unroll
+    for (int m = NI; m < 32; m <<= 1) sum += __shfl_xor_sync(kFull, sum, m);
+    return sum;
+}
+
 template <int NI>
 __device__ __forceinline__ int scattered_element(int lane) {
     int bits = 0;

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "lc_internal.cuh"
 
 namespace lc {
@@ -189,9 +191,49 @@ cudaError_t launch_kinetic(Ctx *c, cudaStream_t s) {
     return e;
 }
 
+// First level of the per-cell partials' sum: block b takes the cells of
+// one contiguous range, its threads a fixed stride within it, then a fixed
+// tree: partials in the per-warp slots' layout for k_final_pot.
+__global__ void __launch_bounds__(256) k_cell_parts(int n, int per_block, const double *__restrict__ acc,
+                                                    const long long *__restrict__ pairs,
+                                                    double *__restrict__ part, long long *__restrict__ part_pairs) {
+    __shared__ double r6[256], r12[256];
+    __shared__ long long rp[256];
+    const int c0 = blockIdx.x * per_block, c1 = min(n, c0 + per_block);
+    double a6 = 0.0, a12 = 0.0;
+    long long ap = 0;
+    for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        a6 += acc[4 * (size_t)c];
+        a12 += acc[4 * (size_t)c + 1];
+        ap += pairs[c];
+    }
+    r6[threadIdx.x] = a6; r12[threadIdx.x] = a12; rp[threadIdx.x] = ap;
+    __syncthreads();
+    for (int m = 128; m > 0; m >>= 1) {
+        if (threadIdx.x < m) {
+            r6[threadIdx.x] += r6[threadIdx.x + m];
+            r12[threadIdx.x] += r12[threadIdx.x + m];
+            rp[threadIdx.x] += rp[threadIdx.x + m];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[4 * blockIdx.x + 0] = r6[0];
+        part[4 * blockIdx.x + 1] = r12[0];
+        part_pairs[blockIdx.x] = rp[0];
+    }
+}
+
+// U, W and the pair count from n per-cell partials (acc[4 c], acc[4 c + 1]:
+// sums of r^-6 and r^-12; pairs[c]) in two fixed-order levels: many blocks
+// over contiguous cell ranges into the per-warp slots, then k_final_pot.
 cudaError_t launch_energy_reduce_parts(Ctx *c, cudaStream_t s, int full, const double *acc, const long long *pairs,
                                        int n) {
-    k_final_pot<<<1, kRedThreads, 0, s>>>(n, acc, pairs, full, c->d_result, c->d_npairs);
+    int nb = std::min(c->nwarp_max, 2 * c->num_sms);
+    const int per_block = std::max(256, (n + nb - 1) / nb);
+    nb = std::max(1, (n + per_block - 1) / per_block);
+    k_cell_parts<<<nb, 256, 0, s>>>(n, per_block, acc, pairs, c->d_warp_acc, c->d_warp_pairs);
+    k_final_pot<<<1, kRedThreads, 0, s>>>(nb, c->d_warp_acc, c->d_warp_pairs, full, c->d_result, c->d_npairs);
     return cudaGetLastError();
 }
 
