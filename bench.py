@@ -332,6 +332,8 @@ def run_profile(args, dist):
     sched = "atomic" if args.schedule == "auto" else args.schedule
     if sched == "list":
         g.set_skin(args.skin)
+    if args.tile:
+        g.set_tile(*[int(v) for v in args.tile.split(",")])
     g.forces(sched)
     g.verlet(DT, args.warmup, sched)
     torch.cuda.synchronize()
@@ -518,6 +520,10 @@ def run_gb300(args, dist):
             g.set_tile(best["ni"], best["warps"])
         tile = {"ni": tuned["ni"], "warps": tuned["warps"]} if args.schedule == "auto" else \
             {"ni": best["ni"], "warps": best["warps"]}
+        if args.tile:
+            ni, warps = [int(v) for v in args.tile.split(",")]
+            g.set_tile(ni, warps)
+            tile = {"ni": ni, "warps": warps}
 
     # the first evaluation, at the initial positions: the precision report's sample
     g.set_state(dpos, dvel)
@@ -839,6 +845,9 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--workload", default="liquid1m", choices=sorted(inputs.WORKLOADS) + ["batch512"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", default=None,
+                    help="NI,WARPS: the force kernels' tile shape instead of the autotuner's choice "
+                         "(16,16: the atomic schedule's row-group kernel)")
     ap.add_argument("--profile", action="store_true",
                     help="only warm-up + timed steps of one schedule (for ncu captures)")
     ap.add_argument("--dag", action="store_true",

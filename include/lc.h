@@ -319,8 +319,13 @@ lc_status lc_dag_forces(lc_ctx *ctx, lc_order order, double wait_seconds, int fl
                         void *stream);
 
 /* Tile shape of the force kernels: ni = particles of the centre cell held
- * per warp (8 or 16), warps = warps per thread block (1 .. 8).  0 keeps
- * the current value.  Used by the autotuner. */
+ * per warp (8 or 16), warps = warps per thread block (1 .. 8), or 16: the
+ * atomic schedule of a single 3D box in mixed precision with ni = 16 then
+ * runs its row-group kernel (one block of 16 warps per SM; the neighbour
+ * cells of up to 21 x-consecutive centre cells copied into shared memory
+ * once, by bulk copies, and read from there by the cell tasks; the other
+ * schedules and contexts run 8 warps per block).  0 keeps the current value.
+ * Used by the autotuner.  Errors: LC_ERR_INVALID_ARG for other values. */
 lc_status lc_set_tile(lc_ctx *ctx, int ni, int warps);
 
 /* Number of kernels launched by the last lc_forces / lc_verlet_step call

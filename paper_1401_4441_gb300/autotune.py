@@ -15,6 +15,7 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tune
 
 TILES = (8, 16)            # centre-cell particles held per warp
 WARPS = (2, 4, 8)          # warps per thread block
+ROWS = 16                  # tile setting of the atomic schedule's row-group kernel (ni 16)
 
 
 def occupancy_bucket(n, ncell):
@@ -81,6 +82,10 @@ def tune(box, schedules=("atomic", "buffer", "fullshell", "colour"), use_cache=T
             for warps in WARPS:
                 box.set_tile(ni, warps)
                 table.append({"schedule": sched, "ni": ni, "warps": warps, "ms": time_forces(box, sched)})
+        if sched == "atomic" and not getattr(box, "nbox", 0) and box.precision == "mixed" \
+                and getattr(box, "dims", 3) == 3:
+            box.set_tile(16, ROWS)
+            table.append({"schedule": sched, "ni": 16, "warps": ROWS, "ms": time_forces(box, sched)})
     best = min(table, key=lambda r: r["ms"])
     box.set_tile(best["ni"], best["warps"])
     result = {"schedule": best["schedule"], "ni": best["ni"], "warps": best["warps"], "ms": best["ms"]}

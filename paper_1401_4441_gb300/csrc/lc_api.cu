@@ -1016,7 +1016,8 @@ lc_status lc_dag_forces(lc_ctx *c, lc_order order, double wait_seconds, int flag
 lc_status lc_set_tile(lc_ctx *c, int ni, int warps) {
     if (!c) return LC_ERR_INVALID_ARG;
     if (ni && ni != 8 && ni != 16) return LC_ERR_INVALID_ARG;
-    if (warps < 0 || warps > 8) return LC_ERR_INVALID_ARG;   // 256-thread launch bound
+    // 1 .. 8 warps per block; 16: the atomic schedule's row-group kernel
+    if (warps < 0 || (warps > 8 && warps != 16)) return LC_ERR_INVALID_ARG;
     if (ni) c->ni = ni;
     if (warps) c->warps = warps;
     for (int k = 0; k < 2 * kNumSched; ++k)

@@ -1077,6 +1077,542 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
     }
 }
 
+// ------------------------------------- row groups (atomic schedule, 3D) ----
+// The atomic schedule's single-box 3D sweep with the neighbour data of a
+// group of consecutive centre cells staged once per block.  A group is a run
+// of up to kRowGMax x-consecutive centre cells of one (y, z) row; the
+// forward half-shells of its cells lie in five rows of cells, (y, z),
+// (y + 1, z), (y - 1, z + 1), (y, z + 1), (y + 1, z + 1), over x0 - 1 ..
+// x0 + G, each row one to three contiguous runs of slots (cell order is x
+// fastest; a run breaks where the row wraps around the periodic boundary).
+// One warp copies them into a shared-memory slot by bulk copies (TMA,
+// cp.async.bulk, one per run) and the block's warps take the group's cells as
+// tasks, reading every neighbour from shared memory: each particle is read
+// from L2 once per group instead of once per task, and no warp waits on a
+// gather latency in its prune.  Two slots per block: the warp that finishes
+// a group's last task refills its slot with the block's next group while the
+// others work on the group in the other slot.  Runs that do not fit a slot
+// are read from global memory instead.  The task itself is the atomic
+// schedule's (the same pair loop, pruning, rare path and writes).
+#ifndef ROW_G
+#define ROW_G 21
+#define ROW_CAP 4096
+#define ROW_SLOTS 2
+#endif
+constexpr int kRowWarps = 16;
+constexpr int kRowGMax = ROW_G;                     // centre cells per group
+constexpr int kRowRows = 5;
+constexpr int kRowCells = kRowRows * (kRowGMax + 2);
+constexpr int kRowCap = ROW_CAP;                    // staged particles per slot
+constexpr int kRowSlots = ROW_SLOTS;                // groups staged ahead per block
+constexpr int kRowJl = 512;                         // listed neighbour entries per batch
+constexpr int kRowUnstaged = 1 << 25;               // list entry flag: data in global memory
+
+struct RowSlot {
+    float4 data[kRowCap];
+    int boff[kRowCells];      // buffer offset of each table cell (-1: not staged)
+    int gstart[kRowCells];    // its first slot
+    int count[kRowCells];
+    int img[kRowCells];       // its periodic image code seen from the group's centre row
+    int tag;                  // local group index whose data is in place
+    int group;                // its global group index (-1: past the last group)
+    int y, z, x0, ntask;
+    int done;                 // tasks of the group finished
+    int phase;                // parity of the mbarrier's next phase
+    unsigned long long bar;   // mbarrier of the bulk copies
+};
+
+struct alignas(16) RowWarp {
+    float4 ipa[8], ipb[8], ipc[8];   // the centre chunk in pairs, as in WarpSmem
+    int2 islot2[8];
+    float corr[16][3];
+    double corr64[16][3];
+    float4 nb_sh[14], nb_sl[14];
+    int nb_base[14];                 // slot = nb_base + entry index (staged or not)
+    int nb_boff[14], nb_count[14], nb_img[14];
+    union {
+        int jl[kRowJl];              // entry index | unstaged flag | neighbour << 26
+        float4 jd[(32 * kColStride + 3) / 4];   // the column sums' scratch (write_i_chunk)
+    };
+};
+
+struct RowArgs {
+    int G, nseg, ngroups;            // centre cells per group, groups per row, groups
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned:
+// float4 entries) from global to shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+// Row of the group's table for a half-shell offset (oy, oz).
+__device__ __forceinline__ int row_of(int oy, int oz) { return oz == 0 ? oy : 3 + oy; }
+__device__ __forceinline__ int row_oy(int r) { return r == 0 ? 0 : (r == 1 ? 1 : r - 3); }
+__device__ __forceinline__ int row_oz(int r) { return r < 2 ? 0 : 1; }
+
+// One warp stages local group li of the block into slot S: the block's
+// groups are blockIdx.x + li * gridDim.x (increasing in li, so once one is
+// past the last group all later ones are), fills the cell table, copies the
+// runs that fit, waits for the copies (bounded) and publishes the tag.
+// Returns false on a timeout.
+__device__ bool row_stage(const ForceArgs &a, const RowArgs &r, RowSlot &S, int li, int *s_end, int lane) {
+    const Grid &g = a.g;
+    const int gid = blockIdx.x + li * gridDim.x;
+    if (gid >= r.ngroups) {
+        if (lane == 0) {
+            S.group = -1;
+            atomicMin(s_end, li);
+            __threadfence_block();
+            *(volatile int *)&S.tag = li;
+        }
+        __syncwarp();
+        return true;
+    }
+    const int seg = gid % r.nseg, row = gid / r.nseg;
+    const int y = row % g.nc[1], z = row / g.nc[1];
+    const int x0 = seg * r.G;
+    const int ntask = min(r.G, g.nc[0] - x0);
+    const int nk = ntask + 2;   // table cells per row: x0 - 1 .. x0 + ntask
+    // the runs: per row, the cell before x0 when it wraps, the cells inside
+    // the box, the cell after the last when it wraps (lane p: row p / 3)
+    int p_first = 0, p_cells = 0, p_k0 = 0;   // first global cell, cells, first table column
+    int p_bytes = 0, p_gs = 0;
+    if (lane < 3 * kRowRows) {
+        const int rr = lane / 3, kind = lane % 3;
+        int yy = y + row_oy(rr), zz = z + row_oz(rr);
+        yy = yy < 0 ? yy + g.nc[1] : (yy >= g.nc[1] ? yy - g.nc[1] : yy);
+        zz = zz >= g.nc[2] ? zz - g.nc[2] : zz;
+        const int rbase = g.nc[0] * (yy + g.nc[1] * zz);
+        const int xlo = x0 - 1, xhi = x0 + ntask;
+        int xa = 0, xb = -1, k0 = 0;
+        if (kind == 0) {
+            if (xlo < 0) { xa = xb = g.nc[0] - 1; k0 = 0; }
+        } else if (kind == 1) {
+            xa = max(xlo, 0); xb = min(xhi, g.nc[0] - 1); k0 = xa - xlo;
+        } else {
+            if (xhi >= g.nc[0]) { xa = xb = 0; k0 = nk - 1; }
+        }
+        if (xb >= xa) {
+            p_first = rbase + xa;
+            p_cells = xb - xa + 1;
+            p_k0 = rr * (r.G + 2) + k0;
+            p_gs = a.start[p_first];
+            p_bytes = 16 * (a.start[p_first + p_cells - 1] + a.count[p_first + p_cells - 1] - p_gs);
+        }
+    }
+    // buffer offsets: inclusive scan of the run sizes in lane order
+    int incl = p_bytes;
+#pragma unroll
+    for (int o = 1; o < kWarp; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const bool fits = p_cells > 0 && incl <= 16 * kRowCap;
+    const int p_off = (incl - p_bytes) >> 4;   // entries
+    const unsigned total = __reduce_add_sync(kFull, fits ? (unsigned)p_bytes : 0u);
+    // the cell table: lane-parallel over the runs' cells
+    for (int p = 0; p < 3 * kRowRows; ++p) {
+        const int cells = __shfl_sync(kFull, p_cells, p);
+        if (cells == 0) continue;
+        const int first = __shfl_sync(kFull, p_first, p), k0 = __shfl_sync(kFull, p_k0, p);
+        const int gs = __shfl_sync(kFull, p_gs, p), off = __shfl_sync(kFull, p_off, p);
+        const bool st = __shfl_sync(kFull, fits, p);
+        for (int c = lane; c < cells; c += kWarp) {
+            const int ci = k0 + c, gc = first + c;
+            const int s0 = a.start[gc];
+            S.gstart[ci] = s0;
+            S.count[ci] = a.count[gc];
+            S.boff[ci] = st ? off + (s0 - gs) : -1;
+            // periodic image of the cell as the group's centres see it
+            const int rr = ci / (r.G + 2), k = ci - rr * (r.G + 2);
+            const int xi = x0 - 1 + k, yi = y + row_oy(rr), zi = z + row_oz(rr);
+            const int sx = xi < 0 ? -1 : (xi >= g.nc[0] ? 1 : 0);
+            const int sy = yi < 0 ? -1 : (yi >= g.nc[1] ? 1 : 0);
+            const int sz = zi >= g.nc[2] ? 1 : 0;
+            S.img[ci] = (sx + 1) | ((sy + 1) << 2) | ((sz + 1) << 4);
+        }
+    }
+    if (lane == 0) {
+        S.group = gid; S.y = y; S.z = z; S.x0 = x0; S.ntask = ntask; S.done = 0;
+    }
+    // the slot's previous readers finished before its last task was counted
+    // (release there, acquire by the counting atomic): order their generic
+    // reads before the asynchronous copies' writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) mbar_expect_tx(&S.bar, total);
+    __syncwarp();
+    if (fits && p_bytes > 0) bulk_g2s(&S.data[p_off], a.p4 + p_gs, (unsigned)p_bytes, &S.bar);
+    // wait for the copies (bounded: a second limit if the first runs out,
+    // so that no copy is in flight when the warp leaves)
+    bool ok = true;
+    if (lane == 0) {
+        const unsigned par = (unsigned)S.phase;
+        const unsigned long long t0 = global_ns();
+        unsigned it = 0;
+        while (!mbar_try_wait(&S.bar, par)) {
+            if ((++it & 255) == 0 && (long long)(global_ns() - t0) > a.wait_ns) { ok = false; break; }
+        }
+        if (!ok) {
+            atomicOr(a.err, kErrTimeout);
+            const unsigned long long t1 = global_ns();
+            while (!mbar_try_wait(&S.bar, par) && (long long)(global_ns() - t1) < 4 * a.wait_ns) {}
+        }
+        S.phase = (int)(par ^ 1u);
+        __threadfence_block();
+        *(volatile int *)&S.tag = li;
+    }
+    ok = __shfl_sync(kFull, ok, 0);
+    __syncwarp();
+    return ok;
+}
+
+// Waits (bounded) until slot S holds local group li.  Returns 1 when it
+// does, 0 past the block's last group, -1 on a timeout (error flag set).
+__device__ int row_wait(const ForceArgs &a, const RowSlot &S, int li, const int *s_end) {
+    int res = 1;
+    if ((threadIdx.x & 31) == 0) {
+        const unsigned long long t0 = global_ns();
+        unsigned sleep = 32, it = 0;
+        for (;;) {
+            if (*(volatile const int *)&S.tag == li) {
+                if (*(volatile const int *)&S.group < 0) res = 0;   // past the last group
+                break;
+            }
+            if (*(volatile const int *)s_end <= li) { res = 0; break; }
+            if ((++it & 15) == 0) {
+                if (*(volatile const int *)a.err & kErrTimeout) { res = -1; break; }
+                if ((long long)(global_ns() - t0) > a.wait_ns) { atomicOr(a.err, kErrTimeout); res = -1; break; }
+            }
+            __nanosleep(sleep);
+            if (sleep < 1024) sleep <<= 1;
+        }
+        __threadfence_block();
+    }
+    res = __shfl_sync(kFull, res, 0);
+    __syncwarp();
+    return res;
+}
+
+// Neighbour entry e of a listed batch: data from the slot or, flagged, from
+// global memory; its slot.
+__device__ __forceinline__ float4 row_data(const ForceArgs &a, const RowSlot &S, const RowWarp &W, int w) {
+    const int idx = w & (kRowUnstaged - 1);
+    return (w & kRowUnstaged) ? a.p4[W.nb_base[w >> 26] + idx] : S.data[idx];
+}
+
+// List neighbour entries from (b, kin) until kRowJl are listed; returns how many.
+__device__ __forceinline__ int row_list(RowWarp &W, int &b, int &kin, int lane) {
+    int nj = 0;
+    while (b < 14 && nj < kRowJl) {
+        const int cnt = W.nb_count[b] - kin;
+        const int take = min(cnt, kRowJl - nj);
+        const int boff = W.nb_boff[b];
+        const int tagb = (b << 26) | (boff < 0 ? kRowUnstaged : 0);
+        const int base = (boff < 0 ? 0 : boff) + kin;
+        for (int k = lane; k < take; k += kWarp) W.jl[nj + k] = (base + k) | tagb;
+        nj += take;
+        kin += take;
+        if (kin >= W.nb_count[b]) { ++b; kin = 0; }
+    }
+    __syncwarp();
+    return nj;
+}
+
+// One task: centre cell x0 + t of the slot's group, its 13 forward
+// neighbours and itself (the atomic schedule's task).
+template <bool STATS>
+__device__ __forceinline__ void row_task(const ForceArgs &a, const RowArgs &r, const RowSlot &S, RowWarp &W, int t, int lane,
+                         const float (*sh)[3], const float (*sl)[3], LaneEnergy &le) {
+    const Grid &g = a.g;
+    // neighbour table, in the stencil's order: self, then the forward offsets
+    if (lane < 14) {
+        int o[3] = {0, 0, 0};
+        if (lane > 0) {
+            const int k = lane - 1;   // forward offsets, z then y then x ascending
+            if (k == 0) { o[0] = 1; }
+            else if (k < 4) { o[0] = k - 2; o[1] = 1; }
+            else { o[0] = (k - 4) % 3 - 1; o[1] = (k - 4) / 3 - 1; o[2] = 1; }
+        }
+        const int ci = row_of(o[1], o[2]) * (r.G + 2) + t + 1 + o[0];
+        const int boff = S.boff[ci], gs = S.gstart[ci];
+        const int oi = (o[0] + 1) + 3 * (o[1] + 1) + 9 * (o[2] + 1);
+        W.nb_sh[lane] = make_float4(sh[oi][0], sh[oi][1], sh[oi][2], 0.f);
+        W.nb_sl[lane] = make_float4(sl[oi][0], sl[oi][1], sl[oi][2], 0.f);
+        W.nb_base[lane] = boff >= 0 ? gs - boff : gs;
+        W.nb_boff[lane] = boff;
+        W.nb_count[lane] = S.count[ci];
+        W.nb_img[lane] = S.img[ci];
+    }
+    __syncwarp();
+    const int na = W.nb_count[0];
+    const int a0 = W.nb_base[0] + (W.nb_boff[0] < 0 ? 0 : W.nb_boff[0]);   // first slot of the centre cell
+    const int c0 = W.nb_boff[0];                                              // its buffer offset (-1: global)
+    const float rc2lo = g.rc2f_lo, rc2hi = g.rc2f_hi;
+    constexpr int NI = 16;
+    for (int i0 = 0; i0 < na; i0 += NI) {
+        float3 bmin = make_float3(1.0e30f, 1.0e30f, 1.0e30f), bmax = make_float3(-1.0e30f, -1.0e30f, -1.0e30f);
+        if (lane < NI) {
+            const int ii = i0 + lane;
+            float4 p = make_float4(1.0e15f, 1.0e15f, 1.0e15f, 0.f);
+            unsigned q = 0x20080200u;   // all three residuals zero
+            if (ii < na) {
+                p = c0 >= 0 ? S.data[c0 + ii] : a.p4[a0 + ii];
+                q = __float_as_uint(p.w);
+                bmin = make_float3(p.x, p.y, p.z);
+                bmax = bmin;
+            }
+            float *A = reinterpret_cast<float *>(W.ipa);
+            float *B = reinterpret_cast<float *>(W.ipb);
+            float *C = reinterpret_cast<float *>(W.ipc);
+            int *Sl = reinterpret_cast<int *>(W.islot2);
+            const int m = lane >> 1, h = lane & 1;
+            A[4 * m + h] = p.x;
+            A[4 * m + 2 + h] = p.y;
+            B[4 * m + h] = p.z;
+            B[4 * m + 2 + h] = lo_residual(q, 2);
+            C[4 * m + h] = lo_residual(q, 0);
+            C[4 * m + 2 + h] = lo_residual(q, 1);
+            Sl[2 * m + h] = ii < na ? a0 + ii : 0x7fffffff;
+            W.corr[lane][0] = W.corr[lane][1] = W.corr[lane][2] = 0.f;
+            W.corr64[lane][0] = W.corr64[lane][1] = W.corr64[lane][2] = 0.0;
+        }
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) {
+            bmin.x = fminf(bmin.x, __shfl_xor_sync(kFull, bmin.x, m));
+            bmin.y = fminf(bmin.y, __shfl_xor_sync(kFull, bmin.y, m));
+            bmin.z = fminf(bmin.z, __shfl_xor_sync(kFull, bmin.z, m));
+            bmax.x = fmaxf(bmax.x, __shfl_xor_sync(kFull, bmax.x, m));
+            bmax.y = fmaxf(bmax.y, __shfl_xor_sync(kFull, bmax.y, m));
+            bmax.z = fmaxf(bmax.z, __shfl_xor_sync(kFull, bmax.z, m));
+        }
+        float2 ax2[NI / 2], ay2[NI / 2], az2[NI / 2];
+#pragma unroll
+        for (int k = 0; k < NI / 2; ++k) ax2[k] = ay2[k] = az2[k] = make_float2(0.f, 0.f);
+        float2 e6 = make_float2(0.f, 0.f), e12 = make_float2(0.f, 0.f);
+        int npair = 0;
+        __syncwarp();
+        const int kpairs = (min(NI, na - i0) + 1) >> 1;
+        const float keep2 = g.rc2f_hi * 1.0001f;
+        const unsigned below = (1u << lane) - 1u;
+        int b = 0, kin = 0;
+        while (b < 14) {
+            int nj = row_list(W, b, kin, lane);
+            if (nj > kWarp) {
+                // prune in place: keep the entries within r_c of the chunk's box
+                int nk = 0;
+                for (int e0 = 0; e0 < nj; e0 += kWarp) {
+                    const int e = e0 + lane;
+                    bool keep = false;
+                    int w = 0;
+                    if (e < nj) {
+                        w = W.jl[e];
+                        const float4 p = row_data(a, S, W, w);
+                        const float4 s4 = W.nb_sh[w >> 26];
+                        const float px = p.x + s4.x, py = p.y + s4.y, pz = p.z + s4.z;
+                        const float dx = fmaxf(fmaxf(bmin.x - px, px - bmax.x), 0.f);
+                        const float dy = fmaxf(fmaxf(bmin.y - py, py - bmax.y), 0.f);
+                        const float dz = fmaxf(fmaxf(bmin.z - pz, pz - bmax.z), 0.f);
+                        keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < keep2;
+                    }
+                    const unsigned mk = __ballot_sync(kFull, keep);
+                    if (keep) W.jl[nk + __popc(mk & below)] = w;   // nk + rank <= e: read before written
+                    nk += __popc(mk);
+                }
+                __syncwarp();
+                nj = nk;
+            }
+            int wn = lane < nj ? W.jl[lane] : -1;
+            float4 pn = wn >= 0 ? row_data(a, S, W, wn) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int jc = 0; jc < nj; jc += kWarp) {
+                const int w = wn;
+                const float4 pc = pn;
+                const int en = jc + kWarp + lane;   // prefetch the next chunk's entry
+                wn = en < nj ? W.jl[en] : -1;
+                pn = wn >= 0 ? row_data(a, S, W, wn) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const bool valid = w >= 0;
+                const int nb = valid ? (w >> 26) : 0;
+                const int sj = valid ? W.nb_base[nb] + (w & (kRowUnstaged - 1)) : 0x7fffffff;
+                const bool is_self = valid && nb == 0;
+                const int jlim = is_self ? sj : 0x7fffffff;   // Newton-3 intra: slot_i < slot_j
+                float pj[3] = {-1.0e15f, -1.0e15f, -1.0e15f}, lj[3] = {0.f, 0.f, 0.f};
+                if (valid) {
+                    const float4 Sh4 = W.nb_sh[nb], Sl4 = W.nb_sl[nb];
+                    const float pin[3] = {pc.x, pc.y, pc.z};
+                    const unsigned q = __float_as_uint(pc.w);
+                    const float res[3] = {lo_residual(q, 0), lo_residual(q, 1), lo_residual(q, 2)};
+                    const float Shv[3] = {Sh4.x, Sh4.y, Sh4.z}, Slv[3] = {Sl4.x, Sl4.y, Sl4.z};
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        const float sum = Shv[d] + pin[d];
+                        const float err = pin[d] - (sum - Shv[d]);
+                        pj[d] = sum;
+                        lj[d] = (err + res[d]) + Slv[d];
+                    }
+                }
+                float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
+                bool amb = false;
+                if (__any_sync(kFull, is_self))
+                    pair_loop<NI, true, true, STATS>(W, pj, lj, jlim, -1, rc2lo, rc2hi, ax2, ay2, az2, gx, gy, gz, e6,
+                                                     e12, npair, amb, kpairs);
+                else
+                    pair_loop<NI, true, false, STATS>(W, pj, lj, jlim, -1, rc2lo, rc2hi, ax2, ay2, az2, gx, gy, gz, e6,
+                                                      e12, npair, amb, kpairs);
+                float fjx = -(gx.x + gx.y), fjy = -(gy.x + gy.y), fjz = -(gz.x + gz.y);
+                double cj[3] = {0.0, 0.0, 0.0};
+                if (__any_sync(kFull, amb)) {
+                    // rare: the band around r_c^2 decided in FP64 and added in
+                    // FP32; pairs closer than kClose computed and summed in FP64
+                    double sL[3];
+                    for (int d = 0; d < 3; ++d) sL[d] = image_shift(g, W.nb_img[nb], d);
+#pragma unroll 1
+                    for (int k = 0; k < NI; ++k) {
+                        const int si = reinterpret_cast<const int *>(W.islot2)[k];
+                        const bool ok = si < jlim;
+                        const float dx = (staged(W.ipa, k, 0) + -pj[0]) + (staged(W.ipc, k, 0) + -lj[0]);
+                        const float dy = (staged(W.ipa, k, 1) + -pj[1]) + (staged(W.ipc, k, 1) + -lj[1]);
+                        const float dz = (staged(W.ipb, k, 0) + -pj[2]) + (staged(W.ipb, k, 1) + -lj[2]);
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        if (!(valid && ok && r2 < rc2hi) || loop_hit(r2, rc2lo)) continue;
+                        if (loop_close(r2, rc2lo)) {
+                            double F[3];
+                            const double s6d = pair_force_f64(a.x, a.y, a.z, si, sj, sL, F);
+                            atomicAdd(&W.corr64[k][0], F[0]);
+                            atomicAdd(&W.corr64[k][1], F[1]);
+                            atomicAdd(&W.corr64[k][2], F[2]);
+                            cj[0] -= F[0]; cj[1] -= F[1]; cj[2] -= F[2];
+                            if (STATS) {
+                                const float s6 = (float)s6d;
+                                e6.x += s6;
+                                e12.x = fmaf(s6, s6, e12.x);
+                                npair += 1;
+                            }
+                        } else if (exact_inside(a, g.rc2, si, sj, sL)) {
+                            const float inv = rcp_nr(r2);
+                            const float s6 = inv * inv * inv;
+                            const float f = (s6 * inv) * fmaf(48.0f, s6, -24.0f);
+                            atomicAdd(&W.corr[k][0], f * dx);
+                            atomicAdd(&W.corr[k][1], f * dy);
+                            atomicAdd(&W.corr[k][2], f * dz);
+                            fjx = fmaf(-f, dx, fjx); fjy = fmaf(-f, dy, fjy); fjz = fmaf(-f, dz, fjz);
+                            if (STATS) {
+                                e6.x += s6;
+                                e12.x = fmaf(s6, s6, e12.x);
+                                npair += 1;
+                            }
+                        }
+                    }
+                }
+                if (valid) write_force<kAtomic, true, float>(a, sj, fjx, fjy, fjz, cj[0], cj[1], cj[2]);
+            }
+            __syncwarp();
+        }
+        float ax[NI], ay[NI], az[NI];
+#pragma unroll
+        for (int k = 0; k < NI / 2; ++k) {
+            ax[2 * k] = ax2[k].x; ax[2 * k + 1] = ax2[k].y;
+            ay[2 * k] = ay2[k].x; ay[2 * k + 1] = ay2[k].y;
+            az[2 * k] = az2[k].x; az[2 * k + 1] = az2[k].y;
+        }
+        // the listing is rebuilt for the next centre chunk: its space holds
+        // the column sums
+        write_i_chunk<true, NI, kAtomic>(a, W, ax, ay, az, a0, i0, na, lane);
+        if (STATS) {
+            kahan_add(le.s6, e6.x + e6.y);
+            kahan_add(le.s12, e12.x + e12.y);
+            le.pairs += npair;
+        }
+    }
+}
+
+template <bool STATS>
+__global__ void __launch_bounds__(kRowWarps * 32, 1) k_force_rows(ForceArgs a, RowArgs r) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RowSlot *slot = reinterpret_cast<RowSlot *>(smem_raw);
+    RowWarp *wsm = reinterpret_cast<RowWarp *>(smem_raw + kRowSlots * sizeof(RowSlot));
+    __shared__ int s_next, s_end;
+    __shared__ float s_sh[27][3], s_sl[27][3];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int w = blockIdx.x * kRowWarps + wib;
+    for (int k = threadIdx.x; k < 81; k += blockDim.x) {
+        (&s_sh[0][0])[k] = (&a.sh[0][0])[k];
+        (&s_sl[0][0])[k] = (&a.sl[0][0])[k];
+    }
+    if (threadIdx.x == 0) {
+        s_next = 0;
+        s_end = 0x7fffffff;
+        for (int k = 0; k < kRowSlots; ++k) {
+            slot[k].tag = -1;
+            slot[k].group = -1;
+            slot[k].done = 0;
+            slot[k].phase = 0;
+            mbar_init(&slot[k].bar, 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    LaneEnergy le;
+    le.s6 = make_float2(0.f, 0.f);
+    le.s12 = make_float2(0.f, 0.f);
+    le.d6 = le.d12 = 0.0;
+    le.pairs = 0;
+    bool ok = true;
+    if (wib < kRowSlots) ok = row_stage(a, r, slot[wib], wib, &s_end, lane);
+    while (ok) {
+        int tl = 0;
+        if (lane == 0) tl = atomicAdd(&s_next, 1);
+        tl = __shfl_sync(kFull, tl, 0);
+        const int li = tl / r.G, t = tl - li * r.G;
+        RowSlot &S = slot[li % kRowSlots];
+        const int st = row_wait(a, S, li, &s_end);
+        if (st <= 0) break;
+        if (t < S.ntask) row_task<STATS>(a, r, S, wsm[wib], t, lane, s_sh, s_sl, le);
+        // count the task; the warp that counts the group's last one refills
+        // the slot with the block's group li + kRowSlots
+        __syncwarp();
+        int d = 0;
+        if (lane == 0) {
+            __threadfence_block();
+            d = atomicAdd(&S.done, 1) + 1;
+            __threadfence_block();
+        }
+        d = __shfl_sync(kFull, d, 0);
+        if (d == r.G) ok = row_stage(a, r, S, li + kRowSlots, &s_end, lane);
+    }
+    double s6 = f32_to_f64_bits(le.s6.x) - f32_to_f64_bits(le.s6.y);
+    double s12 = f32_to_f64_bits(le.s12.x) - f32_to_f64_bits(le.s12.y);
+    long long np = le.pairs;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        s6 += __shfl_xor_sync(kFull, s6, m);
+        s12 += __shfl_xor_sync(kFull, s12, m);
+        np += __shfl_xor_sync(kFull, np, m);
+    }
+    if (STATS && lane == 0) {
+        a.warp_acc[4 * w + 0] += s6;
+        a.warp_acc[4 * w + 1] += s12;
+        a.warp_pairs[w] += np;
+    }
+}
+
 // ------------------------------------------------ device task DAG ----
 // Sec. VI, Strategy 2 and Sec. III / V: the tasks of one creation order run
 // as a dependency-counted DAG.  A persistent warp claims the next queue slot,
@@ -1293,11 +1829,15 @@ static size_t smem_bytes(int warps) {
     return sizeof(WarpSmem<T>) * (size_t)warps;
 }
 
+// Warps per block of the per-warp-task kernels (a setting of 16 selects the
+// row-group kernel for the atomic schedule; the others run 8).
+static int task_warps(const Ctx *c) { return c->warps > 8 ? 8 : c->warps; }
+
 // One resident wave: SMs x the blocks that fit on an SM (cached per shape).
 template <bool MIXED, int NI, int MODE, bool STATS, bool BATCHED, bool PX = false>
 static int force_blocks(Ctx *c) {
     static int cache[17] = {0};
-    const int warps = c->warps;
+    const int warps = task_warps(c);
     if (!cache[warps]) {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force<MIXED, NI, MODE, STATS, BATCHED, PX>, warps * 32,
@@ -1312,7 +1852,7 @@ static int force_blocks(Ctx *c) {
 
 template <bool MIXED, int NI, int MODE, bool STATS, bool BATCHED, bool PX = false>
 static cudaError_t launch_one(Ctx *c, ForceArgs &a, cudaStream_t s) {
-    const int warps = c->warps;
+    const int warps = task_warps(c);
     const size_t sm = smem_bytes<MIXED, NI>(warps);
     const int blocks = force_blocks<MIXED, NI, MODE, STATS, BATCHED, PX>(c);
     if (blocks * warps > c->nwarp_used) c->nwarp_used = blocks * warps;
@@ -1344,6 +1884,36 @@ static cudaError_t launch_mode(Ctx *c, ForceArgs &a, cudaStream_t s, bool stats)
     }
     if (!MIXED || stats) return launch_one<MIXED, NI, MODE, true, false>(c, a, s);
     return launch_one<MIXED, NI, MODE, (MIXED ? false : true), false>(c, a, s);
+}
+
+// Row-group kernel of the atomic schedule: the group geometry (runs of up
+// to kRowGMax centre cells per row, equal lengths) and one block of 16 warps
+// per SM.
+static size_t rows_smem() { return kRowSlots * sizeof(RowSlot) + kRowWarps * sizeof(RowWarp); }
+
+static RowArgs row_args(const Ctx *c) {
+    RowArgs r;
+    r.nseg = (c->g.nc[0] + kRowGMax - 1) / kRowGMax;
+    r.G = (c->g.nc[0] + r.nseg - 1) / r.nseg;
+    r.ngroups = r.nseg * c->g.nc[1] * c->g.nc[2];
+    return r;
+}
+
+// The row-group kernel serves single 3D boxes in mixed precision with the
+// centre tile of 16 when the tile setting asks for it (warps = 16).
+static bool use_rows(const Ctx *c) {
+    return c->warps == 16 && c->ni == 16 && c->nbox == 0 && c->g.dims == 3 && c->prec == LC_PREC_MIXED;
+}
+
+static cudaError_t launch_rows(Ctx *c, ForceArgs &a, cudaStream_t s, bool stats) {
+    RowArgs r = row_args(c);
+    a.err = c->d_err;
+    a.wait_ns = (long long)(c->cs_wait_s * 1.0e9);
+    const int blocks = c->num_sms;
+    if (blocks * kRowWarps > c->nwarp_used) c->nwarp_used = blocks * kRowWarps;
+    if (stats) k_force_rows<true><<<blocks, kRowWarps * 32, rows_smem(), s>>>(a, r);
+    else k_force_rows<false><<<blocks, kRowWarps * 32, rows_smem(), s>>>(a, r);
+    return cudaGetLastError();
 }
 
 // FP32 shift tables o * h = sh + sl for the 27 offsets.
@@ -1409,7 +1979,8 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
             a.pairx = 1;
             a.ntasks = ((c->g.nc[0] + 1) / 2) * c->g.nc[1];
         }
-        e = launch_mode<MIXED, NI, kAtomic>(c, a, s, stats);
+        if (MIXED && NI == 16 && use_rows(c)) e = launch_rows(c, a, s, stats);
+        else e = launch_mode<MIXED, NI, kAtomic>(c, a, s, stats);
         ++*launches;
     } else if (sched == LC_SCHED_BUFFER) {
         // every buffer entry is written by its one task: no clearing
@@ -1449,7 +2020,7 @@ static cudaError_t launch_dag(Ctx *c, const DagDev *dd, long long wait_ns, int32
     d.trace = trace;
     d.ntasks = dd->ntasks;
     d.wait_ns = wait_ns;
-    const int warps = c->warps;
+    const int warps = task_warps(c);
     const size_t smem = smem_bytes<MIXED, 16>(warps);
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_force_dag<MIXED, 16>, warps * 32, smem);
@@ -1580,6 +2151,9 @@ cudaError_t init_force_kernels() {
                                   (int)smem_bytes<true, 16>(8))) ||
         (e = cudaFuncSetAttribute(k_force_dag<false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem_bytes<false, 16>(8))))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_force_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem())) ||
+        (e = cudaFuncSetAttribute(k_force_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem())))
         return e;
     if ((e = attrs_for<true, 8, true>()) || (e = attrs_for<true, 16, true>()) || (e = attrs_for<true, 8, false>()) ||
         (e = attrs_for<true, 16, false>()) || (e = attrs_for<false, 8, true>()) || (e = attrs_for<false, 16, true>()))

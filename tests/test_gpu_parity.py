@@ -17,8 +17,18 @@ from test_colour_cells import colours as schedule_colours
 pytestmark = pytest.mark.gpu
 
 RC = 2.5
-SCHEDS = ["colour", "atomic", "fullshell", "buffer"]
+# "rows": the atomic schedule through its row-group kernel (tile setting
+# ni = 16, warps = 16; mixed precision, single 3D boxes)
+SCHEDS = ["colour", "atomic", "fullshell", "buffer", "rows"]
 TOL = {"fp64": 1e-10, "mixed": 1e-5}
+
+
+def run(b, sched):
+    """The schedule's force evaluation ("rows": the row-group kernel)."""
+    if sched == "rows":
+        b.set_tile(16, 16)
+        sched = "atomic"
+    b.forces(sched)
 
 
 def rel_force_err(f, fref):
@@ -92,7 +102,7 @@ def forces_case(lc, pos, box, prec, sched):
     are both held to TOL."""
     fref, U, W, npairs = oracle.lc_forces(pos[:, 0], pos[:, 1], pos[:, 2], box, RC)
     with make(lc, pos, box, prec) as b:
-        b.forces(sched)
+        run(b, sched)
         f = b.get("forces")
         u, k, w, np_ = b.energy()
     err, rms = rel_force_err(f, fref)
@@ -137,7 +147,7 @@ def test_forces_overlap_stress(lc, sched):
     fref, U, W, npairs = oracle.lc_forces(pos[:, 0], pos[:, 1], pos[:, 2], box, RC)
     for prec, tol in (("fp64", 1e-10), ("mixed", 1e-5)):
         with make(lc, pos, box, prec) as g:
-            g.forces(sched)
+            run(g, sched)
             f = g.get("forces")
             u, k, w, np_ = g.energy()
         err, rms = rel_force_err(f, fref)
@@ -185,6 +195,45 @@ def test_forces_1m_mixed(lc, sched):
     print(f"1M {sched}: max |dF|/rms = {err:.3e}")
 
 
+def test_rows_unstaged_runs(lc):
+    """Row-group kernel with r_c = 4 (54 particles per cell): a group's rows
+    hold more particles than a shared-memory slot, so its later runs are
+    read from global memory; forces and the pair set as the oracle's."""
+    b = inputs.fcc_box(4 * 38 ** 3, 0.8442, 0.72, seed=12, jitter=0.08)
+    pos, box = b["pos"], b["box"]
+    rc = 4.0
+    assert np.floor(box / rc).min() >= 15
+    fref, U, W, npairs = oracle.lc_forces(pos[:, 0], pos[:, 1], pos[:, 2], box, rc)
+    with lc.Box(box, rc, pos.shape[0], "mixed") as g:
+        g.set_state(pos)
+        g.set_tile(16, 16)
+        g.forces("atomic")
+        f = g.get("forces")
+        u, k, w, np_ = g.energy()
+    err, rms = rel_force_err(f, fref)
+    assert np_ == npairs
+    assert err <= TOL["mixed"], err
+    assert u == pytest.approx(U, rel=1e-5) and w == pytest.approx(W, rel=1e-5)
+
+
+def test_rows_verlet_agrees_with_atomic(lc):
+    """Mixed Verlet steps through the row-group kernel (captured step graphs)
+    follow the per-warp atomic kernel's trajectory."""
+    b = inputs.fcc_box(32000, 0.8442, 0.72, seed=5, jitter=0.05)
+    with make(lc, b["pos"], b["box"], "mixed", b["vel"]) as g1, \
+            make(lc, b["pos"], b["box"], "mixed", b["vel"]) as g2:
+        g1.set_tile(16, 16)
+        for g in (g1, g2):
+            g.verlet(0.005, 3, "atomic")
+            g.verlet(0.005, 4, "atomic")
+        d = g1.get("pos") - g2.get("pos")
+        d -= b["box"] * np.rint(d / b["box"])
+        assert np.abs(d).max() < 1e-7
+        e1, e2 = g1.energy(), g2.energy()
+        assert e1[3] == e2[3]
+        assert e1[0] == pytest.approx(e2[0], rel=1e-6)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_buffer_schedule_reproducible(lc, prec):
     """Buffer schedule (Sec. VI, Strategy 3): every partial force has its own
@@ -212,7 +261,7 @@ def test_schedule_check(lc, sched):
     for box in (np.array([16.8, 16.8, 16.8]), np.array([7.6, 7.6, 7.6]), np.array([12.7, 10.2, 17.6]),
                 np.array([105.0, 27.6, 8.1]), np.array([22.6, 32.6, 12.6])):
         with lc.Box(box, RC, 10, "mixed") as b:
-            conflicts, cover = b.schedule_check(sched)
+            conflicts, cover = b.schedule_check("atomic" if sched == "rows" else sched)
             assert conflicts == 0 and cover == 0
 
 
@@ -222,7 +271,7 @@ def test_empty_and_single(lc):
         pos = np.full((n, 3), 1.0)
         with make(lc, pos, box, "mixed") as b:
             for s in SCHEDS:
-                b.forces(s)
+                run(b, s)
                 u, k, w, np_ = b.energy()
                 assert (u, w, np_) == (0.0, 0.0, 0)
                 if n:
@@ -276,6 +325,9 @@ def test_verlet_schedules_agree(lc, sched):
     b = inputs.fcc_box(4000, 0.8442, 0.72, jitter=0.05)
     x, v, f, e = oracle.verlet(b["pos"], b["vel"], b["box"], RC, 0.005, 7)
     with make(lc, b["pos"], b["box"], "fp64", b["vel"]) as g:
+        if sched == "rows":   # no effect in FP64 (the row kernel is mixed only)
+            g.set_tile(16, 16)
+            sched = "atomic"
         g.verlet(0.005, 3, sched)
         g.verlet(0.005, 1, sched)
         g.verlet(0.005, 3, sched)
