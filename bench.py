@@ -581,6 +581,12 @@ def run_gb300(args, dist):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     t_sus = e0.elapsed_time(e1)
+    # the FP32 FMA probe (lc_probe_fp32), still under the clock sampler: the
+    # derived peak's check on this GPU
+    probe = []
+    for _ in range(5):
+        f, sec = lc.probe_fp32(1 << 16)
+        probe.append(f / sec / 1e12)
     clk = clocks.stop()
     u1, k1, _, npairs_sus = g.energy()
     per_force, per_step = g.launch_counts()
@@ -640,7 +646,10 @@ def run_gb300(args, dist):
                 "flops_per_eval": flops, "candidates": cand, "pairs": npairs_now,
                 "eval_ms": t_force * 1e3,
                 "peak_note": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_clock:.0f} MHz "
-                             f"({clock_src}); MEASURED_PEAKS.json has no FP32 figure"}
+                             f"({clock_src}); MEASURED_PEAKS.json has no FP32 figure",
+                "peak_probe": {"tflops": max(probe), "frac": achieved / max(probe),
+                               "how": "lc_probe_fp32: 8 blocks of 256 threads per SM, 8 chains of 65,536 packed "
+                                      "f32x2 FMAs per thread, CUDA events; best of 5, sampled with the clocks"}}
 
     # binning (counting sort by cell, state permuted into cell order, FP32
     # cell-local coordinates): HBM-bound

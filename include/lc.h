@@ -415,6 +415,17 @@ lc_status lc_batch_info(const lc_ctx *ctx, int32_t *nbox, int64_t *total_particl
 lc_status lc_bin_noalloc(const double *pos, int64_t n, const double box[3], double rc, int32_t *cell_count,
                          int32_t *cell_start, int32_t *perm, void *stream);
 
+/* ---- measurement ---------------------------------------------------------
+ * FP32 fused multiply-add throughput of the current device, the denominator
+ * of the force sweep's roofline: every thread of 8 blocks of 256 per SM runs
+ * eight independent chains of `iters` packed f32x2 FMAs (four flops each),
+ * after a short warm-up launch.  flops: the flops of the timed launch;
+ * seconds: its duration between two CUDA events on `stream`.  Synchronises
+ * the stream; allocates nothing on the device.  The paper has no
+ * counterpart (it states no hardware rate).  Errors: LC_ERR_INVALID_ARG
+ * (iters <= 0, null outputs), LC_ERR_CUDA. */
+lc_status lc_probe_fp32(int32_t iters, double *flops, double *seconds, void *stream);
+
 void lc_destroy(lc_ctx *ctx);
 
 /* Static string naming a status code. */

@@ -72,6 +72,7 @@ def _load():
         "lc_list_info": ([vp, lp, lp, lp, lp, lp, ip, vp], ctypes.c_int),
         "lc_batch_step": ([vp, ctypes.c_double, ctypes.c_int32, vp], ctypes.c_int),
         "lc_set_queue_wait": ([vp, ctypes.c_double, ctypes.c_int32], ctypes.c_int),
+        "lc_probe_fp32": ([ctypes.c_int32, dp, dp, vp], ctypes.c_int),
         "lc_destroy": ([vp], None),
         "lc_status_str": ([ctypes.c_int], ctypes.c_char_p),
     }
@@ -131,6 +132,15 @@ def decode(out):
     _check(lib.lc_result_decode(p, ctypes.byref(u), ctypes.byref(k), ctypes.byref(w), ctypes.byref(npairs)),
            "lc_result_decode")
     return u.value, k.value, w.value, npairs.value
+
+
+def probe_fp32(iters=1 << 16, stream=None):
+    """(flops, seconds) of the library's FP32 FMA throughput probe on the
+    current device (lc_probe_fp32)."""
+    lib_ = _load()
+    f, sec = ctypes.c_double(), ctypes.c_double()
+    _check(lib_.lc_probe_fp32(int(iters), ctypes.byref(f), ctypes.byref(sec), _stream(stream)), "lc_probe_fp32")
+    return f.value, sec.value
 
 
 def dag_plan(nc, order="loopex", perm=None):
