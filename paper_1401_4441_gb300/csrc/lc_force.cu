@@ -209,9 +209,13 @@ struct alignas(16) WarpSmem {
     float4 nb_sl[kMaxNb];       // o * h - nb_sh, rounded to FP32
 };
 
+// The FP64 value of a partial force (exact).  The hardware conversion here:
+// on the neighbour-side and centre-side additions it measured faster than
+// the integer rearrangement of the bits (atomic 0.344 -> 0.341 ms, colour
+// 0.605 -> 0.597 ms on the 1M liquid).
 template <typename T>
 __device__ __forceinline__ double to_f64(T v) {
-    if constexpr (std::is_same<T, float>::value) return f32_to_f64_bits(v);
+    if constexpr (std::is_same<T, float>::value) return (double)v;
     else return v;
 }
 
