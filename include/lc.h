@@ -248,9 +248,12 @@ lc_status lc_grid(const lc_ctx *ctx, int32_t nc[3], int32_t *ncolours, int32_t *
 /* Race and coverage check of a schedule's work decomposition on the device
  * (Sec. IV-VI: the write sharing between cell pairs).  Runs the schedule's
  * own task enumeration without the force arithmetic.  For LC_SCHED_COLOUR
- * every block stamps the cells its tasks may write with its colour and the
- * cells stamped twice within one colour are counted (*conflicts: two blocks
- * of one colour whose writes could meet).  For every schedule each
+ * (the queue's own tables: the cells at each colour's queue positions) every
+ * cell task stamps the cells it may write with its colour and the cells
+ * stamped twice within one colour are counted (*conflicts: two tasks of one
+ * colour whose writes could meet), as is every queued cell whose entry in
+ * the per-cell colour table, which the dependence waits read, differs from
+ * the colour it is queued under.  For every schedule each
  * cell pair of the half-shell (the full shell for LC_SCHED_FULLSHELL) must be
  * visited exactly once; *coverage_errors counts the pairs that are not.
  * Its buffers (27 counters per cell) are allocated on the first call

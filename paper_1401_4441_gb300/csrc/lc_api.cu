@@ -200,7 +200,8 @@ static void free_ctx(Ctx *c) {
                     c->d_warp_acc, c->d_warp_pairs, c->d_kin_part, c->d_result,
                     c->d_stamp, c->d_visit, c->d_counters, c->d_boxes, c->d_cell_box, c->d_slot_box,
                     c->d_box_acc, c->d_box_pairs, c->d_box_out, c->d_fbuf, c->d_nbr, c->d_nn, c->d_q4,
-                    c->d_list_stats, c->d_cs_done, c->d_cs_ctrl, c->d_cell_acc, c->d_cell_pairs, c->d_cs_items};
+                    c->d_list_stats, c->d_cs_done, c->d_cs_ctrl, c->d_cell_acc, c->d_cell_pairs, c->d_cs_items,
+                    c->d_cs_cell, c->d_cs_rank};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k < 2 * kNumSched; ++k)
@@ -247,6 +248,7 @@ static cudaError_t alloc_common(Ctx *c) {
         (e = dalloc(&c->d_warp_acc, 4 * (size_t)c->nwarp_max)) || (e = dalloc(&c->d_warp_pairs, (size_t)c->nwarp_max)) ||
         (e = dalloc(&c->d_kin_part, (size_t)kinetic_blocks(c))) || (e = dalloc(&c->d_result, 8)) ||
         (e = dalloc(&c->d_cs_done, NC)) || (e = dalloc(&c->d_cs_ctrl, 2)) ||
+        (e = dalloc(&c->d_cs_cell, NC)) || (e = dalloc(&c->d_cs_rank, NC)) ||
         (e = dalloc(&c->d_cell_acc, 4 * NC)) || (e = dalloc(&c->d_cell_pairs, NC)) ||
         (e = cudaHostAlloc(&c->h_out, 64, cudaHostAllocDefault)))
         return e;
@@ -291,6 +293,30 @@ const char *lc_status_str(lc_status s) {
     return "unknown status";
 }
 
+// Colour-queue tables of one box's grid: the colour (rank) of every cell,
+// and the cells in queue order (colour-major, ascending cell index inside a
+// colour), offset by the box's first global cell.
+static void colour_tables(const Grid &g, int cell_off, int8_t *rank, int *cell_of_pos) {
+    std::vector<int> fill(g.cs_first, g.cs_first + g.cs_ncolours);
+    for (int c = 0; c < g.ncell; ++c) {
+        const int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
+        const int raw = cs_class(cx, g.nc[0], g.cs_p[0]) + 5 * cs_class(cy, g.nc[1], g.cs_p[1]) +
+                        25 * cs_class(cz, g.nc[2], g.cs_p[2]);
+        const int r = g.cs_colour_of_raw[raw];
+        rank[c] = (int8_t)r;
+        cell_of_pos[fill[r]++] = cell_off + c;
+    }
+}
+
+static cudaError_t upload_colour_tables(Ctx *c) {
+    std::vector<int8_t> rank((size_t)c->g.ncell);
+    std::vector<int> cells((size_t)c->g.ncell);
+    colour_tables(c->g, 0, rank.data(), cells.data());
+    cudaError_t e = cudaMemcpy(c->d_cs_rank, rank.data(), rank.size(), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(c->d_cs_cell, cells.data(), sizeof(int) * cells.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
 static lc_status create_single(const double box[3], double rc, int64_t n, lc_precision prec, int dims, lc_ctx **out) {
     if (!out) return LC_ERR_INVALID_ARG;
     *out = nullptr;
@@ -318,6 +344,7 @@ static lc_status create_single(const double box[3], double rc, int64_t n, lc_pre
     if (!e) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e) { cudaGetLastError(); free_ctx(c); return from_cuda(e); }
     cudaError_t e2 = alloc_common(c);
+    if (!e2) e2 = upload_colour_tables(c);
     if (e2) { cudaGetLastError(); free_ctx(c); return from_cuda(e2); }
     if ((e = launch_colour(c, 0)) || (e = cudaStreamSynchronize(0))) {
         cudaGetLastError();
@@ -419,18 +446,27 @@ lc_status lc_batch_create(int32_t nbox, const double *box, const double *rc, con
                         const std::pair<double, std::pair<int, int>> &y) { return x.first < y.first; });
     int4 *items = (int4 *)malloc(sizeof(int4) * (size_t)(nitems > 0 ? nitems : 1));
     if (!items) { free(cb); free(sb); free_ctx(c); return LC_ERR_OOM; }
+    // per box: the colour of every cell (at the box's global cells) and its
+    // cells in colour order
+    std::vector<int8_t> rank((size_t)(coff > 0 ? coff : 1));
+    std::vector<int> cell_of_pos((size_t)(coff > 0 ? coff : 1));
+    for (int b = 0; b < nbox; ++b) {
+        const BoxDev &bd = c->h_boxes[b];
+        colour_tables(bd.g, bd.cell_off, rank.data() + bd.cell_off, cell_of_pos.data() + bd.cell_off);
+    }
     int64_t q = 0;
     for (const auto &gr : groups) {
         const int b = gr.second.first, k = gr.second.second;
-        const Grid &gb = c->h_boxes[b].g;
-        const int cells = gb.cs_first[k + 1] - gb.cs_first[k];
-        for (int t = 0; t < cells; ++t) items[q++] = make_int4(b, k, t, 1);
+        const BoxDev &bd = c->h_boxes[b];
+        for (int t = bd.g.cs_first[k]; t < bd.g.cs_first[k + 1]; ++t)
+            items[q++] = make_int4(b, k, cell_of_pos[(size_t)bd.cell_off + t], 1);
     }
     c->cs_nitems = (int)nitems;
     e = dalloc(&c->d_cs_items, (size_t)(nitems > 0 ? nitems : 1));
     if (!e && nitems > 0) e = cudaMemcpy(c->d_cs_items, items, sizeof(int4) * (size_t)nitems, cudaMemcpyHostToDevice);
     free(items);
     if (!e) e = cudaMemcpy(c->d_boxes, c->h_boxes, sizeof(BoxDev) * (size_t)nbox, cudaMemcpyHostToDevice);
+    if (!e && coff > 0) e = cudaMemcpy(c->d_cs_rank, rank.data(), (size_t)coff, cudaMemcpyHostToDevice);
     if (!e) e = cudaMemcpy(c->d_cell_box, cb, sizeof(unsigned short) * (size_t)coff, cudaMemcpyHostToDevice);
     if (!e && ntot > 0) e = cudaMemcpy(c->d_slot_box, sb, sizeof(unsigned short) * (size_t)ntot, cudaMemcpyHostToDevice);
     if (!e) e = cudaMemset(c->d_box_out, 0, sizeof(double) * 4 * (size_t)nbox);

@@ -75,7 +75,9 @@ struct ForceArgs {
     long long wait_ns;
     double *cell_acc;
     long long *cell_pairs;
-    const int4 *cs_items;       // batch: (box, colour, first cell of the colour, cells) per queue item
+    const int4 *cs_items;       // batch: (box, colour, global cell, 1) per queue item
+    const int *cs_cell;         // single box: queue position -> cell (colour-major, cells ascending)
+    const int8_t *cs_rank;      // colour (rank) of every cell, per box
     int withhold;               // test of the bounded waits: no task publishes its completion
     int stats;                  // accumulate energy, virial and pair count
     int pairx;                  // 2D atomic: a task is two x-adjacent cells (see single_task)
@@ -919,30 +921,21 @@ __device__ void run_task_fp64(const ForceArgs &a, WarpSmem<double> &sm, const Ta
 // set).
 template <bool MIXED, int NI, bool STATS>
 __device__ bool colour_task(const ForceArgs &a, WarpSmem<typename std::conditional<MIXED, float, double>::type> &sm,
-                            const Grid &g, const float (*sh)[3], const float (*sl)[3], int cell_off, int k, int t,
+                            const Grid &g, const float (*sh)[3], const float (*sl)[3], int cell_off, int k, int A,
                             int lane) {
     const Stencil &S = stencil(g.dims);
-    const int raw = g.cs_raw_of_colour[k];
-    const int cls[3] = {raw % 5, (raw / 5) % 5, raw / 25};
-    const int n0 = cs_count(cls[0], g.nc[0], g.cs_p[0]), n1 = cs_count(cls[1], g.nc[1], g.cs_p[1]);
-    const int t3[3] = {t % n0, (t / n0) % n1, t / (n0 * n1)};
     int cA[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) cA[d] = cs_coord(cls[d], t3[d], g.nc[d], g.cs_p[d]);
-    const int A = cell_off + cA[0] + g.nc[0] * (cA[1] + g.nc[1] * cA[2]);
+    cell_coords(g, A - cell_off, cA);
     bool timed_out = false;
     for (int e = lane; e < S.ndep; e += kWarp) {
-        int cn[3], ncl[3];
+        int cn[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             cn[d] = cA[d] + S.dep[e][d];
             cn[d] = cn[d] < 0 ? cn[d] + g.nc[d] : (cn[d] >= g.nc[d] ? cn[d] - g.nc[d] : cn[d]);
-            ncl[d] = cs_class(cn[d], g.nc[d], g.cs_p[d]);
         }
-        // every class triple with a_d < cs_ncls[d] is present: the colour
-        // (rank in code order) is the mixed-radix number of the triple
-        if (ncl[0] + g.cs_ncls[0] * (ncl[1] + g.cs_ncls[1] * ncl[2]) >= k) continue;
         const int N = cell_off + cn[0] + g.nc[0] * (cn[1] + g.nc[1] * cn[2]);
+        if ((int)a.cs_rank[N] >= k) continue;   // only earlier colours are waited for
         if (ld_relaxed(a.cs_done + N) != 0) continue;
         const unsigned long long t0 = global_ns();
         unsigned sleep = 64;
@@ -1040,14 +1033,12 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
             if (q >= a.ntasks) break;
             bool ok = true;
             if constexpr (BATCHED) {
-                const int4 it = a.cs_items[q];
+                const int4 it = a.cs_items[q];   // (box, colour, global cell)
                 const BoxDev &bd = a.boxes[it.x];
-                for (int i = 0; i < it.w && ok; ++i)
-                    ok = colour_task<MIXED, NI, STATS>(a, sm, bd.g, bd.sh, bd.sl, bd.cell_off, it.y, it.z + i, lane);
+                ok = colour_task<MIXED, NI, STATS>(a, sm, bd.g, bd.sh, bd.sl, bd.cell_off, it.y, it.z, lane);
             } else {
-                int k = 0;
-                while (q >= a.g.cs_first[k + 1]) ++k;
-                ok = colour_task<MIXED, NI, STATS>(a, sm, a.g, s_sh, s_sl, 0, k, q - a.g.cs_first[k], lane);
+                const int A = a.cs_cell[q];
+                ok = colour_task<MIXED, NI, STATS>(a, sm, a.g, s_sh, s_sl, 0, (int)a.cs_rank[A], A, lane);
             }
             if (!ok) break;
         }
@@ -1790,17 +1781,18 @@ __global__ void k_check(Grid g, int group, int colour, int ntasks, int phase, in
 // cells its task writes (A and A + o for the forward offsets, all distinct)
 // with k; a cell stamped twice within one colour is written by two tasks of
 // that colour (a conflict).  Each task counts its visits of (A, o).
-__global__ void k_check_cs(Grid g, int k, int *stamp, unsigned long long *visit, unsigned long long *counters) {
-    const int raw = g.cs_raw_of_colour[k];
-    const int cls[3] = {raw % 5, (raw / 5) % 5, raw / 25};
-    const int n0 = cs_count(cls[0], g.nc[0], g.cs_p[0]), n1 = cs_count(cls[1], g.nc[1], g.cs_p[1]);
-    const int ntask = g.cs_first[k + 1] - g.cs_first[k];
+__global__ void k_check_cs(Grid g, int k, const int *cs_cell, const int8_t *cs_rank, int *stamp,
+                           unsigned long long *visit, unsigned long long *counters) {
+    // the queue's own tables: the cells at colour k's queue positions, each
+    // of which must carry colour k in the per-cell table the waits read
+    const int first = g.cs_first[k], ntask = g.cs_first[k + 1] - first;
     const Stencil &S = stencil(g.dims);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntask; t += gridDim.x * blockDim.x) {
-        const int t3[3] = {t % n0, (t / n0) % n1, t / (n0 * n1)};
+        const int Ai = cs_cell[first + t];
+        if ((int)cs_rank[Ai] != k) atomicAdd(counters + 0, 1ull);
         int cA[3];
-        for (int d = 0; d < 3; ++d) cA[d] = cs_coord(cls[d], t3[d], g.nc[d], g.cs_p[d]);
-        const size_t A = (size_t)cA[0] + g.nc[0] * ((size_t)cA[1] + g.nc[1] * (size_t)cA[2]);
+        cell_coords(g, Ai, cA);
+        const size_t A = (size_t)Ai;
         for (int h = -1; h < S.nh; ++h) {
             int o[3] = {0, 0, 0};
             if (h >= 0) { o[0] = S.hs[h][0]; o[1] = S.hs[h][1]; o[2] = S.hs[h][2]; }
@@ -1971,6 +1963,8 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
         a.cell_acc = c->d_cell_acc;
         a.cell_pairs = c->d_cell_pairs;
         a.cs_items = c->d_cs_items;
+        a.cs_cell = c->d_cs_cell;
+        a.cs_rank = c->d_cs_rank;
         e = launch_mode<MIXED, NI, kColourQ>(c, a, s, stats);
         if (e) return e;
         ++*launches;
@@ -2118,7 +2112,8 @@ cudaError_t launch_schedule_check(Ctx *c, lc_schedule sched, cudaStream_t s) {
     const int blocks = c->num_sms * 4;
     if (sched == LC_SCHED_COLOUR) {
         for (int k = 0; k < c->g.cs_ncolours; ++k)
-            k_check_cs<<<blocks, 256, 0, s>>>(c->g, k, c->d_stamp, c->d_visit, c->d_counters);
+            k_check_cs<<<blocks, 256, 0, s>>>(c->g, k, c->d_cs_cell, c->d_cs_rank, c->d_stamp, c->d_visit,
+                                              c->d_counters);
     } else if (sched == LC_SCHED_ATOMIC || sched == LC_SCHED_BUFFER) {
         k_check<kAtomic><<<blocks, 256, 0, s>>>(c->g, 0, 0, c->g.ncell, 0, c->d_stamp, c->d_visit, c->d_counters);
     } else {

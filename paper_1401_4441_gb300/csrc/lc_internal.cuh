@@ -150,6 +150,8 @@ struct Ctx {
     int *d_key;            // slot -> particle ID (before the final ranking)
     int *d_blocksums;      // scan partials
     int8_t *d_colour;      // [ncell]
+    int *d_cs_cell;        // colour queue of a single box: position -> cell
+    int8_t *d_cs_rank;     // colour of every cell (per box)
     float4 *d_p4;          // FP32 cell-centre offsets (sorted) + packed residuals
     // forces
     double *fx, *fy, *fz;  // FP64 forces in sorted order
