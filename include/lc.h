@@ -252,8 +252,10 @@ lc_status lc_grid(const lc_ctx *ctx, int32_t nc[3], int32_t *ncolours, int32_t *
  * cell task stamps the cells it may write with its colour and the cells
  * stamped twice within one colour are counted (*conflicts: two tasks of one
  * colour whose writes could meet), as is every queued cell whose entry in
- * the per-cell colour table, which the dependence waits read, differs from
- * the colour it is queued under.  For every schedule each
+ * the per-cell colour table differs from the colour it is queued under, and
+ * every dependence offset that the cell's wait mask includes or omits
+ * against that table (the waits must cover exactly the earlier-coloured
+ * cells that can share a written cell).  For every schedule each
  * cell pair of the half-shell (the full shell for LC_SCHED_FULLSHELL) must be
  * visited exactly once; *coverage_errors counts the pairs that are not.
  * Its buffers (27 counters per cell) are allocated on the first call

@@ -201,7 +201,7 @@ static void free_ctx(Ctx *c) {
                     c->d_stamp, c->d_visit, c->d_counters, c->d_boxes, c->d_cell_box, c->d_slot_box,
                     c->d_box_acc, c->d_box_pairs, c->d_box_out, c->d_fbuf, c->d_nbr, c->d_nn, c->d_q4,
                     c->d_list_stats, c->d_cs_done, c->d_cs_ctrl, c->d_cell_acc, c->d_cell_pairs, c->d_cs_items,
-                    c->d_cs_cell, c->d_cs_rank};
+                    c->d_cs_cell, c->d_cs_rank, c->d_cs_dep};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k < 2 * kNumSched; ++k)
@@ -248,7 +248,7 @@ static cudaError_t alloc_common(Ctx *c) {
         (e = dalloc(&c->d_warp_acc, 4 * (size_t)c->nwarp_max)) || (e = dalloc(&c->d_warp_pairs, (size_t)c->nwarp_max)) ||
         (e = dalloc(&c->d_kin_part, (size_t)kinetic_blocks(c))) || (e = dalloc(&c->d_result, 8)) ||
         (e = dalloc(&c->d_cs_done, NC)) || (e = dalloc(&c->d_cs_ctrl, 2)) ||
-        (e = dalloc(&c->d_cs_cell, NC)) || (e = dalloc(&c->d_cs_rank, NC)) ||
+        (e = dalloc(&c->d_cs_cell, NC)) || (e = dalloc(&c->d_cs_rank, NC)) || (e = dalloc(&c->d_cs_dep, NC)) ||
         (e = dalloc(&c->d_cell_acc, 4 * NC)) || (e = dalloc(&c->d_cell_pairs, NC)) ||
         (e = cudaHostAlloc(&c->h_out, 64, cudaHostAllocDefault)))
         return e;
@@ -296,7 +296,9 @@ const char *lc_status_str(lc_status s) {
 // Colour-queue tables of one box's grid: the colour (rank) of every cell,
 // and the cells in queue order (colour-major, ascending cell index inside a
 // colour), offset by the box's first global cell.
-static void colour_tables(const Grid &g, int cell_off, int8_t *rank, int *cell_of_pos) {
+// dep: per cell, bit e set when the cell at the stencil's dependence offset
+// e has an earlier colour (the cells a task waits for).
+static void colour_tables(const Grid &g, int cell_off, int8_t *rank, int *cell_of_pos, unsigned long long *dep) {
     std::vector<int> fill(g.cs_first, g.cs_first + g.cs_ncolours);
     for (int c = 0; c < g.ncell; ++c) {
         const int cx = c % g.nc[0], cy = (c / g.nc[0]) % g.nc[1], cz = c / (g.nc[0] * g.nc[1]);
@@ -306,14 +308,28 @@ static void colour_tables(const Grid &g, int cell_off, int8_t *rank, int *cell_o
         rank[c] = (int8_t)r;
         cell_of_pos[fill[r]++] = cell_off + c;
     }
+    Stencil st;
+    make_stencil(&st, g.dims);
+    for (int c = 0; c < g.ncell; ++c) {
+        const int cc[3] = {c % g.nc[0], (c / g.nc[0]) % g.nc[1], c / (g.nc[0] * g.nc[1])};
+        unsigned long long m = 0;
+        for (int e = 0; e < st.ndep; ++e) {
+            int n[3];
+            for (int d = 0; d < 3; ++d) n[d] = ((cc[d] + st.dep[e][d]) % g.nc[d] + g.nc[d]) % g.nc[d];
+            if (rank[n[0] + g.nc[0] * (n[1] + g.nc[1] * n[2])] < rank[c]) m |= 1ull << e;
+        }
+        dep[c] = m;
+    }
 }
 
 static cudaError_t upload_colour_tables(Ctx *c) {
     std::vector<int8_t> rank((size_t)c->g.ncell);
     std::vector<int> cells((size_t)c->g.ncell);
-    colour_tables(c->g, 0, rank.data(), cells.data());
+    std::vector<unsigned long long> dep((size_t)c->g.ncell);
+    colour_tables(c->g, 0, rank.data(), cells.data(), dep.data());
     cudaError_t e = cudaMemcpy(c->d_cs_rank, rank.data(), rank.size(), cudaMemcpyHostToDevice);
     if (!e) e = cudaMemcpy(c->d_cs_cell, cells.data(), sizeof(int) * cells.size(), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(c->d_cs_dep, dep.data(), sizeof(unsigned long long) * dep.size(), cudaMemcpyHostToDevice);
     return e;
 }
 
@@ -450,9 +466,11 @@ lc_status lc_batch_create(int32_t nbox, const double *box, const double *rc, con
     // cells in colour order
     std::vector<int8_t> rank((size_t)(coff > 0 ? coff : 1));
     std::vector<int> cell_of_pos((size_t)(coff > 0 ? coff : 1));
+    std::vector<unsigned long long> dep((size_t)(coff > 0 ? coff : 1));
     for (int b = 0; b < nbox; ++b) {
         const BoxDev &bd = c->h_boxes[b];
-        colour_tables(bd.g, bd.cell_off, rank.data() + bd.cell_off, cell_of_pos.data() + bd.cell_off);
+        colour_tables(bd.g, bd.cell_off, rank.data() + bd.cell_off, cell_of_pos.data() + bd.cell_off,
+                      dep.data() + bd.cell_off);
     }
     int64_t q = 0;
     for (const auto &gr : groups) {
@@ -467,6 +485,8 @@ lc_status lc_batch_create(int32_t nbox, const double *box, const double *rc, con
     free(items);
     if (!e) e = cudaMemcpy(c->d_boxes, c->h_boxes, sizeof(BoxDev) * (size_t)nbox, cudaMemcpyHostToDevice);
     if (!e && coff > 0) e = cudaMemcpy(c->d_cs_rank, rank.data(), (size_t)coff, cudaMemcpyHostToDevice);
+    if (!e && coff > 0)
+        e = cudaMemcpy(c->d_cs_dep, dep.data(), sizeof(unsigned long long) * (size_t)coff, cudaMemcpyHostToDevice);
     if (!e) e = cudaMemcpy(c->d_cell_box, cb, sizeof(unsigned short) * (size_t)coff, cudaMemcpyHostToDevice);
     if (!e && ntot > 0) e = cudaMemcpy(c->d_slot_box, sb, sizeof(unsigned short) * (size_t)ntot, cudaMemcpyHostToDevice);
     if (!e) e = cudaMemset(c->d_box_out, 0, sizeof(double) * 4 * (size_t)nbox);

@@ -78,6 +78,7 @@ struct ForceArgs {
     const int4 *cs_items;       // batch: (box, colour, global cell, 1) per queue item
     const int *cs_cell;         // single box: queue position -> cell (colour-major, cells ascending)
     const int8_t *cs_rank;      // colour (rank) of every cell, per box
+    const unsigned long long *cs_dep;   // per cell: bit e = dependence offset e has an earlier colour
     int withhold;               // test of the bounded waits: no task publishes its completion
     int stats;                  // accumulate energy, virial and pair count
     int pairx;                  // 2D atomic: a task is two x-adjacent cells (see single_task)
@@ -926,8 +927,10 @@ __device__ bool colour_task(const ForceArgs &a, WarpSmem<typename std::condition
     const Stencil &S = stencil(g.dims);
     int cA[3];
     cell_coords(g, A - cell_off, cA);
+    const unsigned long long waits = a.cs_dep[A];   // the dependence offsets with an earlier colour
     bool timed_out = false;
     for (int e = lane; e < S.ndep; e += kWarp) {
+        if (!((waits >> e) & 1ull)) continue;
         int cn[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -935,7 +938,6 @@ __device__ bool colour_task(const ForceArgs &a, WarpSmem<typename std::condition
             cn[d] = cn[d] < 0 ? cn[d] + g.nc[d] : (cn[d] >= g.nc[d] ? cn[d] - g.nc[d] : cn[d]);
         }
         const int N = cell_off + cn[0] + g.nc[0] * (cn[1] + g.nc[1] * cn[2]);
-        if ((int)a.cs_rank[N] >= k) continue;   // only earlier colours are waited for
         if (ld_relaxed(a.cs_done + N) != 0) continue;
         const unsigned long long t0 = global_ns();
         unsigned sleep = 64;
@@ -1781,8 +1783,9 @@ __global__ void k_check(Grid g, int group, int colour, int ntasks, int phase, in
 // cells its task writes (A and A + o for the forward offsets, all distinct)
 // with k; a cell stamped twice within one colour is written by two tasks of
 // that colour (a conflict).  Each task counts its visits of (A, o).
-__global__ void k_check_cs(Grid g, int k, const int *cs_cell, const int8_t *cs_rank, int *stamp,
-                           unsigned long long *visit, unsigned long long *counters) {
+__global__ void k_check_cs(Grid g, int k, const int *cs_cell, const int8_t *cs_rank,
+                           const unsigned long long *cs_dep, int *stamp, unsigned long long *visit,
+                           unsigned long long *counters) {
     // the queue's own tables: the cells at colour k's queue positions, each
     // of which must carry colour k in the per-cell table the waits read
     const int first = g.cs_first[k], ntask = g.cs_first[k + 1] - first;
@@ -1793,6 +1796,13 @@ __global__ void k_check_cs(Grid g, int k, const int *cs_cell, const int8_t *cs_r
         int cA[3];
         cell_coords(g, Ai, cA);
         const size_t A = (size_t)Ai;
+        // the waits' mask: exactly the dependence cells of an earlier colour
+        for (int e = 0; e < S.ndep; ++e) {
+            int n[3];
+            for (int d = 0; d < 3; ++d) n[d] = (cA[d] + S.dep[e][d] + g.nc[d]) % g.nc[d];
+            const bool earlier = (int)cs_rank[n[0] + g.nc[0] * (n[1] + g.nc[1] * n[2])] < k;
+            if (earlier != (((cs_dep[Ai] >> e) & 1ull) != 0)) atomicAdd(counters + 0, 1ull);
+        }
         for (int h = -1; h < S.nh; ++h) {
             int o[3] = {0, 0, 0};
             if (h >= 0) { o[0] = S.hs[h][0]; o[1] = S.hs[h][1]; o[2] = S.hs[h][2]; }
@@ -1965,6 +1975,7 @@ static cudaError_t launch_sched(Ctx *c, lc_schedule sched, cudaStream_t s, int *
         a.cs_items = c->d_cs_items;
         a.cs_cell = c->d_cs_cell;
         a.cs_rank = c->d_cs_rank;
+        a.cs_dep = c->d_cs_dep;
         e = launch_mode<MIXED, NI, kColourQ>(c, a, s, stats);
         if (e) return e;
         ++*launches;
@@ -2112,8 +2123,8 @@ cudaError_t launch_schedule_check(Ctx *c, lc_schedule sched, cudaStream_t s) {
     const int blocks = c->num_sms * 4;
     if (sched == LC_SCHED_COLOUR) {
         for (int k = 0; k < c->g.cs_ncolours; ++k)
-            k_check_cs<<<blocks, 256, 0, s>>>(c->g, k, c->d_cs_cell, c->d_cs_rank, c->d_stamp, c->d_visit,
-                                              c->d_counters);
+            k_check_cs<<<blocks, 256, 0, s>>>(c->g, k, c->d_cs_cell, c->d_cs_rank, c->d_cs_dep, c->d_stamp,
+                                              c->d_visit, c->d_counters);
     } else if (sched == LC_SCHED_ATOMIC || sched == LC_SCHED_BUFFER) {
         k_check<kAtomic><<<blocks, 256, 0, s>>>(c->g, 0, 0, c->g.ncell, 0, c->d_stamp, c->d_visit, c->d_counters);
     } else {

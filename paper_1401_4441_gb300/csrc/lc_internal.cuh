@@ -152,6 +152,7 @@ struct Ctx {
     int8_t *d_colour;      // [ncell]
     int *d_cs_cell;        // colour queue of a single box: position -> cell
     int8_t *d_cs_rank;     // colour of every cell (per box)
+    unsigned long long *d_cs_dep;   // per cell: dependence offsets with an earlier colour (bit e)
     float4 *d_p4;          // FP32 cell-centre offsets (sorted) + packed residuals
     // forces
     double *fx, *fy, *fz;  // FP64 forces in sorted order
