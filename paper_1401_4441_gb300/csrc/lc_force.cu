@@ -1698,13 +1698,17 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force_dag(ForceArgs a, D
         } else {
             run_task_fp64<NI, kDag, false>(a, sm, tc, lane, le);
         }
-        __threadfence();                // each lane: its force writes before the release
+        // the lanes' force writes are ordered before every lane's release
+        // below by the warp barrier (release is cumulative)
         __syncwarp();
         if (d.trace && lane == 0) d.trace[2 * tid + 1] = atomicAdd(d.ctrl + 2, 1);
         const int e1 = d.succ_start[tid + 1];
         for (int e = d.succ_start[tid] + lane; e < e1; e += kWarp) {
             const int sc = d.succ[e];
-            const bool ready = atomicSub(d.cnt + sc, 1) == 1;
+            // acquire-release decrement: it releases this task's writes, and
+            // the decrement that reaches zero acquires those of every
+            // predecessor (they released theirs on the same counter)
+            const bool ready = atom_add_acq_rel(d.cnt + sc, -1) == 1;
             // the first ready successor (lowest lane, first round) becomes
             // this warp's next task; the others are published
             const unsigned m = __ballot_sync(__activemask(), ready);
@@ -1719,10 +1723,9 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force_dag(ForceArgs a, D
         next = __shfl_sync(kFull, next, 0);
         if (lane == 0) atomicAdd(d.ctrl + 3, 1);   // tasks done
         if (next >= 0) {
-            // the other predecessors fenced their writes before their
-            // decrements, which the last decrement observed: fence here
-            // before reading them (the queued path's acquire load)
-            __threadfence();
+            // the lane whose decrement reached zero acquired the
+            // predecessors' writes; the warp barrier carries that order to
+            // the other lanes
             __syncwarp();
         }
     }
