@@ -69,11 +69,15 @@ typedef enum {
 
 /* How the write sharing between cell pairs is resolved (Sec. IV-VI). */
 typedef enum {
-    LC_SCHED_COLOUR = 0,    /* blocks of cells coloured 2-strided, run in colour
-                               order on a device queue: blocks of one colour
-                               write disjoint cells, a block waits for its
-                               earlier-coloured neighbours; plain writes, no
-                               atomics, forces bit-reproducible              */
+    LC_SCHED_COLOUR = 0,    /* cell tasks coloured 3-strided in x and y and
+                               2-strided in z, run in colour order on a device
+                               queue: tasks of one colour write disjoint
+                               cells, a task waits (bounded) for its
+                               earlier-coloured neighbours; the force
+                               additions reach the L2 in the order the waits
+                               fix, so forces are bit-reproducible.  A single
+                               box's queue tables (about 13 bytes per cell)
+                               are built on the first use of the schedule  */
     LC_SCHED_ATOMIC = 1,    /* one pass, both cells updated by atomic adds      */
     LC_SCHED_FULLSHELL = 2, /* all 27 cells, own cell written only, no Newton-3 */
     LC_SCHED_BUFFER = 3,    /* one pass into private per-(cell, offset) buffers,

@@ -248,7 +248,6 @@ static cudaError_t alloc_common(Ctx *c) {
         (e = dalloc(&c->d_warp_acc, 4 * (size_t)c->nwarp_max)) || (e = dalloc(&c->d_warp_pairs, (size_t)c->nwarp_max)) ||
         (e = dalloc(&c->d_kin_part, (size_t)kinetic_blocks(c))) || (e = dalloc(&c->d_result, 8)) ||
         (e = dalloc(&c->d_cs_done, NC)) || (e = dalloc(&c->d_cs_ctrl, 2)) ||
-        (e = dalloc(&c->d_cs_cell, NC)) || (e = dalloc(&c->d_cs_rank, NC)) || (e = dalloc(&c->d_cs_dep, NC)) ||
         (e = dalloc(&c->d_cell_acc, 4 * NC)) || (e = dalloc(&c->d_cell_pairs, NC)) ||
         (e = cudaHostAlloc(&c->h_out, 64, cudaHostAllocDefault)))
         return e;
@@ -360,7 +359,6 @@ static lc_status create_single(const double box[3], double rc, int64_t n, lc_pre
     if (!e) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e) { cudaGetLastError(); free_ctx(c); return from_cuda(e); }
     cudaError_t e2 = alloc_common(c);
-    if (!e2) e2 = upload_colour_tables(c);
     if (e2) { cudaGetLastError(); free_ctx(c); return from_cuda(e2); }
     if ((e = launch_colour(c, 0)) || (e = cudaStreamSynchronize(0))) {
         cudaGetLastError();
@@ -484,6 +482,8 @@ lc_status lc_batch_create(int32_t nbox, const double *box, const double *rc, con
     if (!e && nitems > 0) e = cudaMemcpy(c->d_cs_items, items, sizeof(int4) * (size_t)nitems, cudaMemcpyHostToDevice);
     free(items);
     if (!e) e = cudaMemcpy(c->d_boxes, c->h_boxes, sizeof(BoxDev) * (size_t)nbox, cudaMemcpyHostToDevice);
+    if (!e) e = dalloc(&c->d_cs_rank, (size_t)(coff > 0 ? coff : 1));
+    if (!e) e = dalloc(&c->d_cs_dep, (size_t)(coff > 0 ? coff : 1));
     if (!e && coff > 0) e = cudaMemcpy(c->d_cs_rank, rank.data(), (size_t)coff, cudaMemcpyHostToDevice);
     if (!e && coff > 0)
         e = cudaMemcpy(c->d_cs_dep, dep.data(), sizeof(unsigned long long) * (size_t)coff, cudaMemcpyHostToDevice);
@@ -629,6 +629,23 @@ lc_status lc_bin(lc_ctx *c, void *stream) {
 
 // The buffer schedule's private buffers, allocated on its first use (before
 // any stream capture, so that a captured step never allocates).
+// The colour queue's tables of a single box (queue position -> cell, cell
+// colour, wait masks), built on the schedule's first use: before any stream
+// capture, and contexts that never use the colour schedule hold none.
+static lc_status ensure_colour_tables(lc_ctx *c, lc_schedule sched) {
+    if (sched != LC_SCHED_COLOUR || c->nbox > 0 || c->d_cs_rank) return LC_OK;
+    const size_t NC = (size_t)c->g.ncell;
+    cudaError_t e;
+    if ((e = dalloc(&c->d_cs_cell, NC)) || (e = dalloc(&c->d_cs_rank, NC)) || (e = dalloc(&c->d_cs_dep, NC)) ||
+        (e = upload_colour_tables(c))) {
+        cudaGetLastError();
+        cudaFree(c->d_cs_cell); cudaFree(c->d_cs_rank); cudaFree(c->d_cs_dep);
+        c->d_cs_cell = nullptr; c->d_cs_rank = nullptr; c->d_cs_dep = nullptr;
+        return e == cudaErrorMemoryAllocation ? LC_ERR_OOM : LC_ERR_CUDA;
+    }
+    return LC_OK;
+}
+
 static lc_status ensure_fbuf(lc_ctx *c, lc_schedule sched) {
     if (sched != LC_SCHED_BUFFER || c->d_fbuf) return LC_OK;
     const size_t elem = c->prec == LC_PREC_MIXED ? sizeof(float) : sizeof(double);
@@ -640,6 +657,7 @@ static lc_status ensure_fbuf(lc_ctx *c, lc_schedule sched) {
 
 static lc_status do_forces(lc_ctx *c, lc_schedule sched, cudaStream_t s, int *launches) {
     LC_TRY_ST(ensure_fbuf(c, sched));
+    LC_TRY_ST(ensure_colour_tables(c, sched));
     if (!c->binned) {
         LC_TRY(launch_bin(c, s, launches));
         c->binned = true;
@@ -803,6 +821,7 @@ lc_status lc_verlet_step(lc_ctx *c, double dt, int nsteps, lc_schedule sched, vo
     }
     if (nsteps == 0) return LC_OK;
     LC_TRY_ST(ensure_fbuf(c, sched));
+    LC_TRY_ST(ensure_colour_tables(c, sched));
     // The step swaps the two state buffers once (in the binning), so one
     // graph holds two steps and returns the buffers to where they were; a
     // separate graph serves each buffer parity.
@@ -967,6 +986,7 @@ lc_status lc_grid(const lc_ctx *c, int32_t nc[3], int32_t *ncolours, int32_t *np
 
 lc_status lc_schedule_check(lc_ctx *c, lc_schedule sched, int64_t *conflicts, int64_t *coverage_errors, void *stream) {
     if (!c || sched < LC_SCHED_COLOUR || sched > LC_SCHED_BUFFER || c->nbox > 0) return LC_ERR_INVALID_ARG;
+    LC_TRY_ST(ensure_colour_tables(c, sched));
     if (!c->d_visit) {   // the check's buffers (27 counters per cell) on first use
         const size_t NC = (size_t)c->g.ncell;
         if (!c->d_stamp) LC_TRY(dalloc(&c->d_stamp, NC));
