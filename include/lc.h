@@ -14,12 +14,13 @@
  *     interaction (intra- or inter-cell) is the unit of work.
  *   - Sec. IV-V: two cell-cell interactions that share a cell write the same
  *     force accumulators; this write sharing is the race the paper analyses.
- *   - Sec. VI, Strategy 1, Fig. 6: 2-strided colouring makes the writes of
- *     same-coloured tasks disjoint (LC_SCHED_COLOUR, applied to blocks of
- *     cells whose tasks one warp runs in order); Strategy 2: tasks run as
- *     their dependences allow (the colour schedule's blocks wait only for
- *     their earlier-coloured neighbours; lc_dag_forces runs the cell-pair
- *     task DAG of a creation order).
+ *   - Sec. VI, Strategy 1, Fig. 6: colouring makes the writes of
+ *     same-coloured tasks disjoint (LC_SCHED_COLOUR: a cell task keeps its
+ *     whole half-shell, so the stride is 3 where the half-shell reaches both
+ *     neighbours, x and y, and 2 in z); Strategy 2: tasks run as their
+ *     dependences allow (the colour schedule's tasks wait only for their
+ *     earlier-coloured neighbours; lc_dag_forces runs the cell-pair task DAG
+ *     of a creation order).
  *   - Sec. VIII: commutative updates only need mutual exclusion, not an
  *     order (LC_SCHED_ATOMIC resolves the sharing with atomic adds).
  *   - Sec. VI, Strategy 3: every task writes private buffers, one per
@@ -63,7 +64,7 @@ typedef enum {
     LC_ERR_NONFINITE = 5,     /* a position or velocity was NaN or infinite    */
     LC_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up            */
     LC_ERR_STATE = 7,         /* call order violated (e.g. no state set)       */
-    LC_ERR_RACE = 8,          /* one colour's blocks write a cell twice        */
+    LC_ERR_RACE = 8,          /* one colour's tasks write a cell twice         */
     LC_ERR_TOO_LARGE = 9      /* size beyond a stated maximum                  */
 } lc_status;
 
@@ -115,7 +116,9 @@ typedef enum {
  *   rc      cutoff (> 0); cells per dimension nc_d = floor(L_d / rc) (Sec. IV)
  *   n       number of particles (>= 0, < 2^26)
  *   prec    arithmetic of the force sweep
- * Allocates every device buffer the context needs on the current device.
+ * Allocates the context's device buffers on the current device (those of
+ * particular schedules and options -- LC_SCHED_BUFFER, the colour queue's
+ * tables, LC_SCHED_LIST, the staging slots -- on their first use).
  * Errors: LC_ERR_INVALID_ARG, LC_ERR_BOX_TOO_SMALL, LC_ERR_TOO_LARGE,
  * LC_ERR_OOM, LC_ERR_CUDA.  *out is NULL on error. */
 lc_status lc_create(const double box[3], double rc, int64_t n, lc_precision prec, lc_ctx **out);
@@ -168,7 +171,9 @@ lc_status lc_bin(lc_ctx *ctx, void *stream);
 /* One force evaluation with the given schedule (bins first if the positions
  * changed since the last binning).  Also produces the potential energy,
  * the virial and the number of pairs inside r_c.  LC_ERR_OOM if the buffers
- * of LC_SCHED_BUFFER or the lists of LC_SCHED_LIST cannot be allocated;
+ * of LC_SCHED_BUFFER, the tables of LC_SCHED_COLOUR or the lists of
+ * LC_SCHED_LIST cannot be allocated (on the schedule's first use: make that
+ * first call before any stream capture);
  * LC_ERR_INVALID_ARG for LC_SCHED_LIST on a batch or an FP64 context;
  * LC_ERR_TIMEOUT if a wait of the colour schedule's queue ran out.  LC_SCHED_LIST evaluates
  * from the lists, which it first builds (binning on the list grid) when they
@@ -245,8 +250,8 @@ lc_status lc_result_decode(const void *out, double *u_pot, double *k_kin, double
 lc_status lc_get(lc_ctx *ctx, lc_get_what what, void *dst, int on_device, void *stream);
 
 /* Grid of the context: cells per dimension, number of cell colours (the
- * 2-strided classes of LC_GET_COLOUR), number of block colours of
- * LC_SCHED_COLOUR.  Any output may be NULL. */
+ * 2-strided classes of LC_GET_COLOUR), number of colours of LC_SCHED_COLOUR's
+ * cell tasks.  Any output may be NULL. */
 lc_status lc_grid(const lc_ctx *ctx, int32_t nc[3], int32_t *ncolours, int32_t *nphases);
 
 /* Race and coverage check of a schedule's work decomposition on the device
