@@ -647,6 +647,7 @@ def run_gb300(args, dist):
                 "eval_ms": t_force * 1e3,
                 "peak_note": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_clock:.0f} MHz "
                              f"({clock_src}); MEASURED_PEAKS.json has no FP32 figure",
+                "frac_by_schedule": {k: flops / (v * 1e-3) / 1e12 / peak for k, v in sched_ms.items()},
                 "peak_probe": {"tflops": max(probe), "frac": achieved / max(probe),
                                "how": "lc_probe_fp32: 8 blocks of 256 threads per SM, 8 chains of 65,536 packed "
                                       "f32x2 FMAs per thread, CUDA events; best of 5, sampled with the clocks"}}
