@@ -681,53 +681,67 @@ def run_gb300(args, dist):
 
     # end to end through the C ABI from page-locked host memory, in the unit
     # of `value` (velocity-Verlet steps): every job of K steps starts from
-    # the host state (copied in), reads each step's energies and pair count
-    # back (48 bytes, without waiting) and ends with the state read back.
+    # the host state (copied in) and ends with the state read back into
+    # host memory, and reads each step's energies and pair count back (48
+    # bytes, without waiting).  Consecutive jobs are pipelined through the
+    # library's two input staging slots: the next job's input copy and this
+    # job's output copy run on a copy stream while the compute stream works.
     hpos = torch.from_numpy(pos).pin_memory()
     hvel = torch.from_numpy(vel).pin_memory()
-    out_pos = torch.empty_like(hpos).pin_memory()
-    out_vel = torch.empty_like(hvel).pin_memory()
-    res = [torch.zeros(6, dtype=torch.float64).pin_memory() for _ in range(args.steps + 1)]
-    dpos_e, dvel_e = torch.empty_like(dpos), torch.empty_like(dvel)
+    out_pos = [torch.empty_like(hpos).pin_memory() for _ in range(2)]
+    out_vel = [torch.empty_like(hvel).pin_memory() for _ in range(2)]
+    dout = [(torch.empty_like(dpos), torch.empty_like(dvel)) for _ in range(2)]
+    copy_stream = torch.cuda.Stream(dev)
+    jobs = 5
+    res = [[torch.zeros(6, dtype=torch.float64).pin_memory() for _ in range(args.steps)] for _ in range(jobs)]
 
-    def e2e_job():
-        dpos_e.copy_(hpos, non_blocking=True)
-        dvel_e.copy_(hvel, non_blocking=True)
-        g.set_state(dpos_e, dvel_e)
-        pairs_job = 0
-        if forces_only:
-            for k in range(args.steps):
-                g.set_state(dpos_e, dvel_e)
+    def e2e_jobs(njobs):
+        cs = copy_stream.cuda_stream
+        g.stage_state(hpos, hvel, slot=0, copy_stream=cs)
+        for j in range(njobs):
+            b = j % 2
+            g.set_state_staged(b)
+            if j + 1 < njobs:
+                g.stage_state(hpos, hvel, slot=(j + 1) % 2, copy_stream=cs)
+            if forces_only:
+                for k in range(args.steps):
+                    if k:
+                        g.set_state_staged(b)   # the job's input again
+                    g.forces(sched)
+                    g.energy_async(res[j][k])
+            else:
                 g.forces(sched)
-                g.energy_async(res[k])
-        else:
-            g.forces(sched)
-            for k in range(args.steps):
-                g.verlet(DT, 1, sched)
-                g.energy_async(res[k])
-        g.get("pos", out=dpos_e)
-        g.get("vel", out=dvel_e)
-        out_pos.copy_(dpos_e, non_blocking=True)
-        out_vel.copy_(dvel_e, non_blocking=True)
+                for k in range(args.steps):
+                    g.verlet(DT, 1, sched)
+                    g.energy_async(res[j][k])
+            g.get("pos", out=dout[b][0])
+            g.get("vel", out=dout[b][1])
+            done = torch.cuda.Event()
+            done.record(stream)
+            copy_stream.wait_event(done)
+            with torch.cuda.stream(copy_stream):
+                out_pos[b].copy_(dout[b][0], non_blocking=True)
+                out_vel[b].copy_(dout[b][1], non_blocking=True)
         torch.cuda.synchronize(dev)
-        for k in range(args.steps):
-            pairs_job += lc.decode(res[k])[3]
-        return pairs_job
+        return sum(lc.decode(res[j][k])[3] for j in range(njobs) for k in range(args.steps))
 
-    e2e_job()
-    jobs = 3
+    e2e_jobs(2)
     t0 = time.perf_counter()
-    e2e_pairs = sum(e2e_job() for _ in range(jobs))
+    e2e_pairs = e2e_jobs(jobs)
     e2e_s = dist.max(time.perf_counter() - t0)
     state_bytes = int(hpos.numel() * 8 + hvel.numel() * 8)
     e2e = {"value": dist.sum(e2e_pairs) / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": state_bytes / args.steps,
            "d2h_bytes_per_step": 48 + state_bytes / args.steps,
-           "step": ("a job of K steps through the C ABI: host state (page-locked) copied in, lc_set_state, "
-                    "lc_forces, K x (lc_verlet_step of one step + lc_energy_virial_async of its 48-byte "
-                    "result), lc_get of positions and velocities copied out; bytes per step are the job's "
-                    "divided by K") if not forces_only else
-                   "K x (lc_set_state + lc_forces + lc_energy_virial_async), host state copied in and out"}
+           "jobs": jobs,
+           "step": ("jobs of K steps through the C ABI: host state (page-locked) copied in through a staging "
+                    "slot (lc_stage_state on a copy stream, lc_set_state_staged), lc_forces, K x (lc_verlet_step "
+                    "of one step + lc_energy_virial_async of its 48-byte result), lc_get of positions and "
+                    "velocities, copied out on the copy stream; the next job's input copy and this job's "
+                    "output copy overlap the compute; bytes per step are a job's divided by K")
+           if not forces_only else
+                   ("jobs of K x (lc_set_state_staged + lc_forces + lc_energy_virial_async), host state copied "
+                    "in through a staging slot and out on a copy stream, overlapping the compute")}
     g.close()
 
     if dist.rank == 0:

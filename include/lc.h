@@ -184,9 +184,13 @@ lc_status lc_forces(lc_ctx *ctx, lc_schedule sched, void *stream);
 /* nsteps velocity-Verlet steps of size dt (m = 1): v += dt/2 F; x += dt v;
  * bin; F = F(x); v += dt/2 F.  Computes the forces first if they are stale.
  * The step's kernels are captured once into a CUDA graph per (schedule, dt)
- * and replayed.  Potential energy, virial and pair count are accumulated in
- * the last step of the call (lc_energy_virial reports them); the other
- * steps skip that accumulation.  LC_SCHED_LIST: see the list section below
+ * and replayed: a graph of two steps, and for an odd nsteps a graph of one
+ * step at the end.  Potential energy, virial and pair count are accumulated
+ * in the last step of the call (lc_energy_virial reports them); the other
+ * steps skip that accumulation.  The one-step graph's closing half-kick also
+ * forms the kinetic energy of the new velocities, so K after a call with an
+ * odd nsteps needs no further pass over them (after an even nsteps,
+ * lc_energy_virial forms it: one pass over the velocities).  LC_SCHED_LIST: see the list section below
  * (steps between builds do no binning). */
 lc_status lc_verlet_step(lc_ctx *ctx, double dt, int nsteps, lc_schedule sched, void *stream);
 
@@ -232,7 +236,9 @@ lc_status lc_energy_virial(lc_ctx *ctx, double *u_pot, double *k_kin, double *vi
                            int64_t *npairs, void *stream);
 
 /* The same energies without waiting: queues on `stream` the kinetic-energy
- * reduction and the copy of the 48-byte result block into `out` and returns
+ * reduction (none after lc_verlet_step of an odd nsteps, whose closing
+ * kick formed K) and
+ * the copy of the 48-byte result block into `out` and returns
  * at once, so the next step can be queued before this one's result is read.
  * out: 48 bytes, 8-byte aligned host memory owned by the caller, valid until
  * the stream has passed the copy; page-locked memory keeps the call
@@ -382,7 +388,7 @@ lc_status lc_batch_energies(lc_ctx *ctx, double *u_pot, double *k_kin, double *v
  * with the colour schedule on the device work queue: Sec. VI, Strategy 1
  * (colouring) for the disjoint writes of concurrent tasks, Strategy 2 (tasks
  * run as their dependences allow) for the order, over all boxes at once.
- * Pairs of two steps are captured in a CUDA graph and replayed.
+ * Steps are captured in CUDA graphs (two steps, one step) and replayed.
  * LC_ERR_INVALID_ARG for a single-box context; LC_ERR_TIMEOUT if a wait of
  * the queue ran out (see lc_set_queue_wait). */
 lc_status lc_batch_step(lc_ctx *ctx, double dt, int32_t nsteps, void *stream);

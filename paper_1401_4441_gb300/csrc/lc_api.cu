@@ -204,7 +204,7 @@ static void free_ctx(Ctx *c) {
                     c->d_cs_cell, c->d_cs_rank, c->d_cs_dep};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    for (int k = 0; k < 2 * kNumSched; ++k)
+    for (int k = 0; k < kNumGraphs; ++k)
         if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
     for (DagDev *d : c->dag) free_dag(d);
     for (cudaGraphExec_t gx : c->list_graph)
@@ -253,6 +253,7 @@ static cudaError_t alloc_common(Ctx *c) {
         return e;
     c->d_npairs = reinterpret_cast<long long *>(c->d_result + 4);
     c->d_err = reinterpret_cast<int *>(c->d_result + 5);
+    c->d_kin_ticket = reinterpret_cast<unsigned *>(c->d_result + 6);
     c->state_a = c->cur.x;
     if ((e = init_force_kernels())) return e;
     c->fy = c->fx + N; c->fz = c->fx + 2 * N;
@@ -796,14 +797,48 @@ lc_status lc_forces(lc_ctx *c, lc_schedule sched, void *stream) {
 // pass; `pending`: the previous step's closing kick was left out and is
 // fused there too (same arithmetic); `close`: end with the closing kick.
 static cudaError_t step_launches(lc_ctx *c, double dt, lc_schedule sched, cudaStream_t s, int *launches,
-                                 bool stats, bool pending = false, bool close = true) {
+                                 bool stats, bool pending = false, bool close = true, bool kin = false) {
     cudaError_t e;
     if ((e = launch_bin(c, s, launches, pending ? 2 : 1, dt))) return e;
     if ((e = launch_forces(c, sched, s, launches, stats))) return e;
     if (close) {
-        if ((e = launch_kick(c, dt, s))) return e;
+        if ((e = launch_kick(c, dt, s, kin))) return e;
         ++*launches;
     }
+    return cudaSuccess;
+}
+
+// The instantiated graph of nst (1 or 2) steps from the current state
+// buffers into slot k, captured on first use and again when dt changes.
+// Capture leaves the buffers where they were (a launch of the one-step graph
+// swaps them afterwards, as the binning does).  The one-step graph's closing
+// kick also forms K (a call of one step is usually followed by a read of
+// its energies); the two-step graph's does not.
+static cudaError_t ensure_step_graph(lc_ctx *c, double dt, lc_schedule sched, int nst, int k) {
+    if (c->graph[k] && c->graph_dt[k] == dt) return cudaSuccess;
+    if (c->graph[k]) { cudaGraphExecDestroy(c->graph[k]); c->graph[k] = nullptr; }
+    cudaStream_t cap;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e) return e;
+    const State saved_cur = c->cur, saved_nxt = c->nxt;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    int per = 0;
+    if (nst == 2) {
+        if (!e) e = step_launches(c, dt, sched, cap, &per, false, false, false);
+        if (!e) e = step_launches(c, dt, sched, cap, &per, true, true, true);
+    } else {
+        if (!e) e = step_launches(c, dt, sched, cap, &per, true, false, true, true);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+    c->cur = saved_cur; c->nxt = saved_nxt;
+    if (!e) e = e2;
+    if (!e) e = cudaGraphInstantiate(&c->graph[k], graph, 0);
+    if (graph && !e2) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);
+    if (e) { cudaGetLastError(); c->graph[k] = nullptr; return e; }
+    c->graph_dt[k] = dt;
+    if (nst == 2) c->launches_step = per / 2;
     return cudaSuccess;
 }
 
@@ -811,7 +846,7 @@ lc_status lc_verlet_step(lc_ctx *c, double dt, int nsteps, lc_schedule sched, vo
     if (!c || nsteps < 0 || !isfinite(dt) || sched < LC_SCHED_COLOUR || sched > LC_SCHED_LIST)
         return LC_ERR_INVALID_ARG;
     if (!c->have_state) return LC_ERR_STATE;
-    if (nsteps > 0) c->kin_valid = false;   // the steps change the velocities
+    if (nsteps > 0) c->kin_valid = c->kin_final = false;   // the steps change the velocities
     if (sched == LC_SCHED_LIST) return list_verlet(c, dt, nsteps, (cudaStream_t)stream);
     cudaStream_t s = (cudaStream_t)stream;
     int launches = 0;
@@ -824,40 +859,26 @@ lc_status lc_verlet_step(lc_ctx *c, double dt, int nsteps, lc_schedule sched, vo
     LC_TRY_ST(ensure_colour_tables(c, sched));
     // The step swaps the two state buffers once (in the binning), so one
     // graph holds two steps and returns the buffers to where they were; a
-    // separate graph serves each buffer parity.
-    const int k = 2 * (int)sched + (c->cur.x == c->state_a ? 0 : 1);
-    if (!c->graph[k] || c->graph_dt[k] != dt) {
-        if (c->graph[k]) { cudaGraphExecDestroy(c->graph[k]); c->graph[k] = nullptr; }
-        cudaStream_t cap;
-        LC_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-        State saved_cur = c->cur, saved_nxt = c->nxt;
-        cudaGraph_t graph;
-        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-        int per2 = 0;
-        if (!e) e = step_launches(c, dt, sched, cap, &per2, false, false, false);
-        if (!e) e = step_launches(c, dt, sched, cap, &per2, true, true, true);
-        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
-        c->cur = saved_cur; c->nxt = saved_nxt;   // two swaps: same as before
-        if (!e) e = e2;
-        if (!e) e = cudaGraphInstantiate(&c->graph[k], graph, 0);
-        if (graph && !e2) cudaGraphDestroy(graph);
-        cudaStreamDestroy(cap);
-        if (e) { cudaGetLastError(); c->graph[k] = nullptr; return from_cuda(e); }
-        c->graph_dt[k] = dt;
-        c->launches_step = per2 / 2;
-    }
+    // separate graph serves each buffer parity.  An odd count ends with a
+    // graph of one step (its own per parity), after which the buffers are
+    // swapped.
+    const int par = c->cur.x == c->state_a ? 0 : 1;
+    if (nsteps >= 2) LC_TRY(ensure_step_graph(c, dt, sched, 2, 2 * (int)sched + par));
+    const int k1 = 2 * kNumSched + 2 * (int)sched + par;
+    if (nsteps & 1) LC_TRY(ensure_step_graph(c, dt, sched, 1, k1));
     int done = 0;
     while (done + 2 <= nsteps) {
-        LC_TRY(cudaGraphLaunch(c->graph[k], s));
+        LC_TRY(cudaGraphLaunch(c->graph[2 * (int)sched + par], s));
         done += 2;
     }
     if (done < nsteps) {
-        int l = 0;
-        LC_TRY(step_launches(c, dt, sched, s, &l, true));
+        LC_TRY(cudaGraphLaunch(c->graph[k1], s));
+        const State t = c->cur; c->cur = c->nxt; c->nxt = t;
         ++done;
     }
     c->binned = true;
     c->forces_valid = true;
+    if (c->n > 0 && (nsteps & 1)) c->kin_valid = c->kin_final = true;   // the one-step graph formed K
     return LC_OK;
 }
 
@@ -870,7 +891,7 @@ lc_status lc_set_queue_wait(lc_ctx *c, double seconds, int32_t flags) {
     if (!c || !(seconds > 0.0) || !isfinite(seconds) || seconds > 1.0e6 || (flags & ~LC_QUEUE_WITHHOLD))
         return LC_ERR_INVALID_ARG;
     LC_TRY(cudaDeviceSynchronize());   // no captured step in flight: the graphs hold the old values
-    for (int k = 0; k < 2 * kNumSched; ++k)
+    for (int k = 0; k < kNumGraphs; ++k)
         if (c->graph[k]) { cudaGraphExecDestroy(c->graph[k]); c->graph[k] = nullptr; }
     c->cs_wait_s = seconds;
     c->cs_withhold = (flags & LC_QUEUE_WITHHOLD) ? 1 : 0;
@@ -1096,7 +1117,7 @@ lc_status lc_set_tile(lc_ctx *c, int ni, int warps) {
     if (warps < 0 || (warps > 8 && warps != 16)) return LC_ERR_INVALID_ARG;
     if (ni) c->ni = ni;
     if (warps) c->warps = warps;
-    for (int k = 0; k < 2 * kNumSched; ++k)
+    for (int k = 0; k < kNumGraphs; ++k)
         if (c->graph[k]) { cudaGraphExecDestroy(c->graph[k]); c->graph[k] = nullptr; }
     return LC_OK;
 }

@@ -399,7 +399,7 @@ __global__ void k_unsort_vec(int n, Grid g1, const BoxDev *__restrict__ boxes, c
 
 cudaError_t launch_set_state(Ctx *c, const double *pos, const double *vel, cudaStream_t s) {
     const int n = (int)c->n;
-    c->kin_valid = false;
+    c->kin_valid = c->kin_final = false;
     if (n == 0) return cudaSuccess;
     k_set_state<<<kinetic_blocks(c), kKinThreads, 0, s>>>(n, pos, vel, c->g.dims == 2, 0.25 * c->g.L[2], c->cur,
                                                           c->d_kin_part);

@@ -18,6 +18,7 @@ constexpr int64_t kMaxParticles = int64_t(1) << 26;
 constexpr float kCutBand = 4.0e-6f;
 
 constexpr int kNumSched = 4;     // colour, atomic, full shell, buffer
+constexpr int kNumGraphs = 4 * kNumSched;   // captured steps: (two, one) x schedule x buffer parity
 constexpr int kNumFbuf = 15;     // buffer schedule: intra j side, 13 offsets, i side
 
 // Rounding residuals of the FP32 cell-local offsets are stored as
@@ -161,6 +162,8 @@ struct Ctx {
     long long *d_warp_pairs;
     double *d_kin_part;    // per-block partial sums of v^2 (kinetic_blocks of them)
     bool kin_valid;        // d_kin_part holds the partials of the current velocities
+    bool kin_final;        // d_result[3] holds their K (implies kin_valid)
+    unsigned *d_kin_ticket;   // k_kick's count of finished blocks (block + 48; zero between launches)
     // one 64-byte device block, read back in one copy: U, W, pairs (as
     // double), K, then the pair count and the error flags
     double *d_result;      // [4] U, W, npairs (as double), K  (block + 0)
@@ -210,9 +213,10 @@ struct Ctx {
     // buffer schedule: per-(cell, offset) private force buffers [15][3][n]
     // (float for the mixed path, double for FP64), allocated on first use
     void *d_fbuf;
-    // graphs of two Verlet steps: one per (schedule, state-buffer parity)
-    cudaGraphExec_t graph[2 * kNumSched];
-    double graph_dt[2 * kNumSched];
+    // graphs of Verlet steps: two steps at 2 * schedule + state-buffer
+    // parity, one step at 2 * kNumSched + the same
+    cudaGraphExec_t graph[kNumGraphs];
+    double graph_dt[kNumGraphs];
     double *state_a;       // cur.x of buffer set A (parity reference)
     // Verlet neighbour lists (LC_SCHED_LIST): a coarser list grid with
     // cells of side >= rc + skin, fixed-point offsets from the build cells'
@@ -236,7 +240,7 @@ struct Ctx {
 // step dt) / also the previous step's closing kick into the cell pass.
 cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches, int kicks = 0, double dt = 0.0);
 cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launches, bool stats = true);
-cudaError_t launch_kick(Ctx *c, double dt, cudaStream_t s);
+cudaError_t launch_kick(Ctx *c, double dt, cudaStream_t s, bool kin = false);
 cudaError_t launch_kinetic(Ctx *c, cudaStream_t s);
 cudaError_t launch_energy_reduce(Ctx *c, cudaStream_t s, int full);
 // the same reduction over n partials given as [n][4] doubles and [n] pair counts

@@ -15,12 +15,61 @@ namespace lc {
 constexpr int kRedThreads = 1024;
 static_assert(kRedThreads == 32 * 32, "k_final_pot reduces one value per warp in a single warp");
 
-__global__ void k_kick(int n, double half, State st, const double *__restrict__ fx,
-                       const double *__restrict__ fy, const double *__restrict__ fz) {
+// K = 1/2 sum of the block partials of v^2, in a fixed order: thread t adds
+// partials t, t + kKinThreads, ... ascending (four loads in flight; the
+// zeros past the end leave the non-negative sum unchanged), then the
+// block's tree.
+__device__ __forceinline__ double final_kin(int nb, const double *part, double *red) {
+    double a = 0.0;
+    for (int b0 = 0; b0 < nb; b0 += 4 * kKinThreads) {
+        double v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int b = b0 + r * kKinThreads + (int)threadIdx.x;
+            v[r] = b < nb ? __ldcg(part + b) : 0.0;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) a = __dadd_rn(a, v[r]);
+    }
+    return 0.5 * block_sum_kin(a, red);
+}
+
+// Closing half-kick v <- v + (dt/2) F.  KIN: fused with the kinetic energy
+// of the new velocities -- each block forms the partial sum of v^2 that
+// k_kinetic would (same grid, same particles per thread, same order), and
+// the block that finishes last (ticket) adds the partials with final_kin
+// into the result block, so K needs no further pass.
+template <bool KIN>
+__global__ void __launch_bounds__(kKinThreads) k_kick(int n, double half, State st, const double *__restrict__ fx,
+                                                      const double *__restrict__ fy, const double *__restrict__ fz,
+                                                      double *__restrict__ part, unsigned *ticket,
+                                                      double *__restrict__ out) {
+    double acc = 0.0;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        st.vx[s] = fma(half, fx[s], st.vx[s]);
-        st.vy[s] = fma(half, fy[s], st.vy[s]);
-        st.vz[s] = fma(half, fz[s], st.vz[s]);
+        const double vx = fma(half, fx[s], st.vx[s]);
+        const double vy = fma(half, fy[s], st.vy[s]);
+        const double vz = fma(half, fz[s], st.vz[s]);
+        st.vx[s] = vx;
+        st.vy[s] = vy;
+        st.vz[s] = vz;
+        if (KIN) acc = __dadd_rn(acc, kin_term(vx, vy, vz));
+    }
+    if constexpr (!KIN) return;
+    __shared__ double red[kKinThreads];
+    __shared__ bool last;
+    const double t = block_sum_kin(acc, red);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = t;
+        __threadfence();   // the partial is visible before the ticket counts it
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const double k = final_kin(gridDim.x, part, red);
+    if (threadIdx.x == 0) {
+        out[3] = k;
+        *ticket = 0u;   // ready for the next launch
     }
 }
 
@@ -78,18 +127,11 @@ __global__ void __launch_bounds__(kRedThreads) k_final_pot(int nw, const double 
     }
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_final_kin(int nb, const double *__restrict__ part,
+__global__ void __launch_bounds__(kKinThreads) k_final_kin(int nb, const double *__restrict__ part,
                                                            double *__restrict__ out) {
-    __shared__ double r[kRedThreads];
-    double a = 0.0;
-    for (int b = threadIdx.x; b < nb; b += kRedThreads) a += part[b];
-    r[threadIdx.x] = a;
-    __syncthreads();
-    for (int m = kRedThreads / 2; m > 0; m >>= 1) {
-        if (threadIdx.x < m) r[threadIdx.x] += r[threadIdx.x + m];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[3] = 0.5 * r[0];
+    __shared__ double red[kKinThreads];
+    const double k = final_kin(nb, part, red);
+    if (threadIdx.x == 0) out[3] = k;
 }
 
 // Per-box statistics of a batch: U, W and pair count from the box
@@ -171,23 +213,32 @@ cudaError_t launch_box_kinetic(Ctx *c, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_kick(Ctx *c, double dt, cudaStream_t s) {
+cudaError_t launch_kick(Ctx *c, double dt, cudaStream_t s, bool kin) {
     if (c->n == 0) return cudaSuccess;
-    k_kick<<<c->num_sms * 8, 256, 0, s>>>((int)c->n, 0.5 * dt, c->cur, c->fx, c->fy, c->fz);
+    if (kin)
+        k_kick<true><<<kinetic_blocks(c), kKinThreads, 0, s>>>((int)c->n, 0.5 * dt, c->cur, c->fx, c->fy, c->fz,
+                                                               c->d_kin_part, c->d_kin_ticket, c->d_result);
+    else
+        k_kick<false><<<kinetic_blocks(c), kKinThreads, 0, s>>>((int)c->n, 0.5 * dt, c->cur, c->fx, c->fy, c->fz,
+                                                                nullptr, nullptr, nullptr);
     return cudaGetLastError();
 }
 
 int kinetic_blocks(const Ctx *c) { return c->num_sms * 8; }
 
-// K into the result block; the pass over the velocities is skipped while
-// the partials still describe them (the state set-up forms them).
+// K into the result block.  Nothing to do when a closing kick with the
+// kinetic energy (k_kick<true>) or an earlier call already put the current
+// velocities' K there; the pass
+// over the velocities is skipped while the partials still describe them
+// (the state set-up and the kick form them).
 cudaError_t launch_kinetic(Ctx *c, cudaStream_t s) {
+    if (c->kin_final) return cudaSuccess;
     const int nb = kinetic_blocks(c);
     double *part = c->d_kin_part;
     if (!c->kin_valid) k_kinetic<<<nb, kKinThreads, 0, s>>>((int)c->n, c->cur, part);
-    k_final_kin<<<1, kRedThreads, 0, s>>>(nb, part, c->d_result);
+    k_final_kin<<<1, kKinThreads, 0, s>>>(nb, part, c->d_result);
     cudaError_t e = cudaGetLastError();
-    if (!e) c->kin_valid = true;
+    if (!e) c->kin_valid = c->kin_final = true;
     return e;
 }
 

@@ -318,6 +318,36 @@ def test_verlet_4k(lc, prec):
     assert k == pytest.approx(e[-1, 1], rel=tol)
 
 
+@pytest.mark.parametrize("prec,sched", [("fp64", "atomic"), ("mixed", "colour"), ("mixed", "list")])
+def test_kinetic_from_the_kick(lc, prec, sched):
+    """K after an odd step count comes from the one-step graph's closing
+    kick (fused partials and a last-block sum), after an even count and
+    after list steps from a pass over the velocities, after lc_set_state
+    from the set-up pass: each equal to 1/2 sum v^2 of the velocities read
+    back, and the same from lc_energy_virial and the asynchronous result
+    block."""
+    import torch
+    b = inputs.fcc_box(4000, 0.8442, 0.72, seed=3, jitter=0.05)
+    res = torch.zeros(6, dtype=torch.float64).pin_memory()
+
+    def half_v2(v):
+        return 0.5 * math.fsum((v.astype(np.float64) ** 2).ravel())
+
+    with make(lc, b["pos"], b["box"], prec, b["vel"]) as g:
+        g.forces(sched)
+        assert g.energy()[1] == pytest.approx(half_v2(b["vel"]), rel=1e-13)
+        for nsteps in (3, 2, 1):
+            g.verlet(0.005, nsteps, sched)
+            u, k, w, np_ = g.energy()
+            assert k == pytest.approx(half_v2(g.get("vel")), rel=1e-13)
+            g.energy_async(res)
+            torch.cuda.synchronize()
+            assert lc.decode(res) == (u, k, w, np_)
+        g.set_state(g.get("pos"), g.get("vel"))
+        g.forces("atomic" if sched == "list" else sched)
+        assert g.energy()[1] == pytest.approx(half_v2(g.get("vel")), rel=1e-13)
+
+
 @pytest.mark.parametrize("sched", SCHEDS)
 def test_verlet_schedules_agree(lc, sched):
     """Odd step counts (graph of two steps + one direct step) and repeated
