@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kKinThreads) k_set_state(int n, const double *
         st.x[s] = x; st.y[s] = y; st.z[s] = z;
         st.vx[s] = vx; st.vy[s] = vy; st.vz[s] = vz;
         st.id[s] = s;
-        acc = __dadd_rn(acc, kin_term(vx, vy, vz));
+        acc = kin_add(acc, vx, vy, vz);
     }
     const double t = block_sum_kin(acc, red);
     if (threadIdx.x == 0) kin_part[blockIdx.x] = t;

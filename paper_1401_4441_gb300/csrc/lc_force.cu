@@ -63,7 +63,7 @@ struct ForceArgs {
     float *bf;                  // buffer schedule, mixed: [15][3][n] private partial forces
     double *bd;                 // buffer schedule, FP64: [15][3][n]
     size_t n;                   // particles (buffer stride)
-    double *warp_acc;           // [W][4]
+    double *warp_acc;           // [W][4] (single-launch sweeps: one slot per block)
     long long *warp_pairs;      // [W]
     int group, colour;          // colour phase
     int ntasks;
@@ -999,6 +999,28 @@ __device__ bool colour_task(const ForceArgs &a, WarpSmem<typename std::condition
     return true;
 }
 
+// The statistics of a single-launch sweep (atomic, full shell, buffer)
+// summed per block: the block's warps' partials in warp order into slot
+// blockIdx.x (written, not added: no clearing before the launch), so the
+// final reduction reads one slot per block instead of one per warp.  A
+// shared-memory sum behind a block barrier; no fence, which would make the
+// compiler return a value from every force reduction of the sweep.
+__device__ __forceinline__ void block_stats(const ForceArgs &a, double s6, double s12, long long np, int wib,
+                                            int lane) {
+    __shared__ double f6[8], f12[8];   // k_force blocks hold at most 8 warps
+    __shared__ long long fp[8];
+    if (lane == 0) { f6[wib] = s6; f12[wib] = s12; fp[wib] = np; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t6 = f6[0], t12 = f12[0];
+        long long tp = fp[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { t6 += f6[w]; t12 += f12[w]; tp += fp[w]; }
+        a.warp_acc[4 * blockIdx.x + 0] = t6;
+        a.warp_acc[4 * blockIdx.x + 1] = t12;
+        a.warp_pairs[blockIdx.x] = tp;
+    }
+}
+
 template <bool MIXED, int NI, int MODE, bool STATS, bool BATCHED, bool PX = false>
 __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
     using T = typename std::conditional<MIXED, float, double>::type;
@@ -1068,7 +1090,9 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
         s12 += __shfl_xor_sync(kFull, s12, m);
         np += __shfl_xor_sync(kFull, np, m);
     }
-    if (STATS && !BATCHED && lane == 0) {
+    if constexpr (STATS && !BATCHED && MODE != kColourQ) {
+        block_stats(a, s6, s12, np, wib, lane);
+    } else if (STATS && !BATCHED && lane == 0) {
         a.warp_acc[4 * w + 0] += s6;
         a.warp_acc[4 * w + 1] += s12;
         a.warp_pairs[w] += np;
@@ -1865,7 +1889,8 @@ static cudaError_t launch_one(Ctx *c, ForceArgs &a, cudaStream_t s) {
     const int warps = task_warps(c);
     const size_t sm = smem_bytes<MIXED, NI>(warps);
     const int blocks = force_blocks<MIXED, NI, MODE, STATS, BATCHED, PX>(c);
-    if (blocks * warps > c->nwarp_used) c->nwarp_used = blocks * warps;
+    if (STATS && !BATCHED && MODE != kColourQ) c->nwarp_used = blocks;   // one statistics slot per block
+    else if (blocks * warps > c->nwarp_used) c->nwarp_used = blocks * warps;
     k_force<MIXED, NI, MODE, STATS, BATCHED, PX><<<blocks, warps * 32, sm, s>>>(a);
     return cudaGetLastError();
 }
@@ -2086,11 +2111,21 @@ cudaError_t launch_forces_dag(Ctx *c, const DagDev *d, long long wait_ns, int wi
     return e;
 }
 
+// The sweeps whose statistics come as one slot per block (block_stats),
+// written by the launch itself: one launch of k_force over a single box,
+// the colour queue excepted (its per-cell partials are summed in cell order
+// afterwards).  Their slots need no clearing.
+static bool block_slots(const Ctx *c, lc_schedule sched) {
+    if (c->nbox > 0) return false;
+    if (sched == LC_SCHED_ATOMIC) return !(c->ni == 16 && use_rows(c));
+    return sched == LC_SCHED_FULLSHELL || sched == LC_SCHED_BUFFER;
+}
+
 cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launches, bool stats) {
     cudaError_t e;
     const bool mixed = (c->prec == LC_PREC_MIXED);
     if (!mixed) stats = true;
-    if (stats) {
+    if (stats && !block_slots(c, sched)) {
         if (c->nbox > 0) {
             if ((e = cudaMemsetAsync(c->d_box_acc, 0, sizeof(double) * 2 * (size_t)c->nbox, s))) return e;
             if ((e = cudaMemsetAsync(c->d_box_pairs, 0, sizeof(unsigned long long) * (size_t)c->nbox, s))) return e;

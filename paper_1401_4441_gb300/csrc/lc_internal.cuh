@@ -291,21 +291,26 @@ __global__ void k_scatter_starts(int n, int ncell, const int *__restrict__ cell,
                                  int *__restrict__ start, int *__restrict__ cellt = nullptr);
 
 // ---- small device helpers ----------------------------------------------------
-// v^2 of one particle, each operation rounded once (no contraction), and the
-// block sum of 256 thread partials in a fixed tree: every kernel that forms
-// kinetic-energy partials gets the same bits for the same state.
+// A particle's v^2 added to a thread's partial as three fused multiply-adds
+// (the FP64 pipe is the scarce one: three operations instead of five
+// products and sums plus the addition), and the block sum of 256 thread
+// partials in a fixed order (butterfly inside each warp, then the eight warp
+// sums in warp order): every kernel that forms kinetic-energy partials gets
+// the same bits for the same state.
 constexpr int kKinThreads = 256;
-__device__ __forceinline__ double kin_term(double vx, double vy, double vz) {
-    return __dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz));
+__device__ __forceinline__ double kin_add(double acc, double vx, double vy, double vz) {
+    return fma(vz, vz, fma(vy, vy, fma(vx, vx, acc)));
 }
 __device__ __forceinline__ double block_sum_kin(double acc, double *red) {
-    red[threadIdx.x] = acc;
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, m));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
-    for (int m = kKinThreads / 2; m > 0; m >>= 1) {
-        if (threadIdx.x < m) red[threadIdx.x] = __dadd_rn(red[threadIdx.x], red[threadIdx.x + m]);
-        __syncthreads();
-    }
-    return red[0];
+    double t = red[0];
+#pragma unroll
+    for (int w = 1; w < kKinThreads / 32; ++w) t = __dadd_rn(t, red[w]);
+    __syncthreads();   // red is free again when the caller reuses it
+    return t;
 }
 
 // Periodic wrap into [0, L), each operation rounded once (no contraction):

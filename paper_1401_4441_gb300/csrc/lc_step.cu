@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kKinThreads) k_kick(int n, double half, State 
         st.vx[s] = vx;
         st.vy[s] = vy;
         st.vz[s] = vz;
-        if (KIN) acc = __dadd_rn(acc, kin_term(vx, vy, vz));
+        if (KIN) acc = kin_add(acc, vx, vy, vz);
     }
     if constexpr (!KIN) return;
     __shared__ double red[kKinThreads];
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kKinThreads) k_kinetic(int n, State st, double
     __shared__ double red[kKinThreads];
     double acc = 0.0;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
-        acc = __dadd_rn(acc, kin_term(st.vx[s], st.vy[s], st.vz[s]));
+        acc = kin_add(acc, st.vx[s], st.vy[s], st.vz[s]);
     const double t = block_sum_kin(acc, red);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
