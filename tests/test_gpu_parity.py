@@ -348,6 +348,32 @@ def test_kinetic_from_the_kick(lc, prec, sched):
         assert g.energy()[1] == pytest.approx(half_v2(g.get("vel")), rel=1e-13)
 
 
+def test_kinetic_magnitudes(lc):
+    """K of velocities whose components leave the double-float range of the
+    kinetic partials (|v| >= 2^40, tiny, zero) besides ordinary ones, through
+    the set-up pass, the kinetic pass (two steps of dt = 0) and the kick of a
+    one-step graph (dt = 0): 1/2 sum v^2 to 1e-13; all-zero velocities: 0."""
+    b = inputs.fcc_box(4000, 0.8442, 0.72, seed=5, jitter=0.05)
+    v = b["vel"].copy()
+    v[0, 0] = 3.0e13
+    v[1, 1] = -2.0e-15
+    v[2, :] = 0.0
+    v[3, 2] = 7.0e-13
+    want = 0.5 * math.fsum((v ** 2).ravel())
+    with make(lc, b["pos"], b["box"], "mixed", v) as g:
+        g.forces("atomic")
+        assert g.energy()[1] == pytest.approx(want, rel=1e-13)
+        g.verlet(0.0, 2, "atomic")
+        assert g.energy()[1] == pytest.approx(want, rel=1e-13)
+        g.verlet(0.0, 1, "atomic")
+        assert g.energy()[1] == pytest.approx(want, rel=1e-13)
+    with make(lc, b["pos"], b["box"], "mixed") as g:
+        g.forces("atomic")
+        assert g.energy()[1] == 0.0
+        g.verlet(0.0, 1, "atomic")
+        assert g.energy()[1] == 0.0
+
+
 @pytest.mark.parametrize("sched", SCHEDS)
 def test_verlet_schedules_agree(lc, sched):
     """Odd step counts (graph of two steps + one direct step) and repeated
