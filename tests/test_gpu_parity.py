@@ -349,10 +349,10 @@ def test_kinetic_from_the_kick(lc, prec, sched):
 
 
 def test_kinetic_magnitudes(lc):
-    """K of velocities whose components leave the double-float range of the
-    kinetic partials (|v| >= 2^40, tiny, zero) besides ordinary ones, through
-    the set-up pass, the kinetic pass (two steps of dt = 0) and the kick of a
-    one-step graph (dt = 0): 1/2 sum v^2 to 1e-13; all-zero velocities: 0."""
+    """K of velocities with components far from unit size (3e13, 2e-15,
+    7e-13, zero) among ordinary ones, through the set-up pass, the kinetic
+    pass (two steps of dt = 0) and the kick of a one-step graph (dt = 0):
+    1/2 sum v^2 to 1e-13; all-zero velocities: exactly 0."""
     b = inputs.fcc_box(4000, 0.8442, 0.72, seed=5, jitter=0.05)
     v = b["vel"].copy()
     v[0, 0] = 3.0e13
