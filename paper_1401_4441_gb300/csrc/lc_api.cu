@@ -799,10 +799,11 @@ lc_status lc_forces(lc_ctx *c, lc_schedule sched, void *stream) {
 static cudaError_t step_launches(lc_ctx *c, double dt, lc_schedule sched, cudaStream_t s, int *launches,
                                  bool stats, bool pending = false, bool close = true, bool kin = false) {
     cudaError_t e;
+    bool pot = false;   // the statistics' final sum left to the kick
     if ((e = launch_bin(c, s, launches, pending ? 2 : 1, dt))) return e;
-    if ((e = launch_forces(c, sched, s, launches, stats))) return e;
+    if ((e = launch_forces(c, sched, s, launches, stats, close ? &pot : nullptr))) return e;
     if (close) {
-        if ((e = launch_kick(c, dt, s, kin))) return e;
+        if ((e = launch_kick(c, dt, s, kin, pot))) return e;
         ++*launches;
     }
     return cudaSuccess;

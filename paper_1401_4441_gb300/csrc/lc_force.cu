@@ -2121,7 +2121,12 @@ static bool block_slots(const Ctx *c, lc_schedule sched) {
     return sched == LC_SCHED_FULLSHELL || sched == LC_SCHED_BUFFER;
 }
 
-cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launches, bool stats) {
+// pot_deferred (non-null): the final sum of a single box's statistics slots
+// is left to the caller's next kernel (the closing kick) and *pot_deferred
+// says whether it was.
+cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launches, bool stats,
+                          bool *pot_deferred) {
+    if (pot_deferred) *pot_deferred = false;
     cudaError_t e;
     const bool mixed = (c->prec == LC_PREC_MIXED);
     if (!mixed) stats = true;
@@ -2146,6 +2151,7 @@ cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launch
         else if (c->nbox > 0) e = launch_box_energy(c, s, sched == LC_SCHED_FULLSHELL);
         else if (sched == LC_SCHED_COLOUR)   // per-cell partials, reduced in cell order
             e = launch_energy_reduce_parts(c, s, 0, c->d_cell_acc, c->d_cell_pairs, c->g.ncell);
+        else if (pot_deferred) { *pot_deferred = true; return e; }
         else e = launch_energy_reduce(c, s, sched == LC_SCHED_FULLSHELL);
         ++*launches;
     }

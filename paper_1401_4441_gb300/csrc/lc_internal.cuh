@@ -239,8 +239,9 @@ struct Ctx {
 // Binning; kicks = 1 / 2 fuses the start of a Verlet step (kick + drift of
 // step dt) / also the previous step's closing kick into the cell pass.
 cudaError_t launch_bin(Ctx *c, cudaStream_t s, int *launches, int kicks = 0, double dt = 0.0);
-cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launches, bool stats = true);
-cudaError_t launch_kick(Ctx *c, double dt, cudaStream_t s, bool kin = false);
+cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launches, bool stats = true,
+                          bool *pot_deferred = nullptr);
+cudaError_t launch_kick(Ctx *c, double dt, cudaStream_t s, bool kin = false, bool pot = false);
 cudaError_t launch_kinetic(Ctx *c, cudaStream_t s);
 cudaError_t launch_energy_reduce(Ctx *c, cudaStream_t s, int full);
 // the same reduction over n partials given as [n][4] doubles and [n] pair counts

@@ -12,8 +12,6 @@
 
 namespace lc {
 
-constexpr int kRedThreads = 1024;
-static_assert(kRedThreads == 32 * 32, "k_final_pot reduces one value per warp in a single warp");
 
 // K = 1/2 sum of the block partials of v^2, in a fixed order: thread t adds
 // partials t, t + kKinThreads, ... ascending (four loads in flight; the
@@ -34,16 +32,65 @@ __device__ __forceinline__ double final_kin(int nb, const double *part, double *
     return 0.5 * block_sum_kin(a, red);
 }
 
+// U, W and the pair count from nw statistics slots (s6, s12 at [4 w],
+// [4 w + 1], the pair count in pairs[w]), summed by one block of kKinThreads
+// threads in a fixed order: thread t takes slots t, t + kKinThreads, ...,
+// then a butterfly inside each warp, then the warps in order.  The full
+// shell sees every pair twice.  out[0] = U, out[1] = W, out[2] = pairs.
+struct PotArgs {
+    int nw;                      // slots (0: nothing to sum)
+    int full;
+    const double *acc;
+    const long long *pairs;
+    double *out;
+    long long *npairs;
+};
+__device__ __forceinline__ void pot_sum(const PotArgs &p) {
+    __shared__ double r6[kKinThreads / 32], r12[kKinThreads / 32];
+    __shared__ long long rp[kKinThreads / 32];
+    double a6 = 0.0, a12 = 0.0;
+    long long ap = 0;
+    for (int w = threadIdx.x; w < p.nw; w += kKinThreads) {
+        a6 += p.acc[4 * w + 0];
+        a12 += p.acc[4 * w + 1];
+        ap += p.pairs[w];
+    }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        a6 += __shfl_xor_sync(0xffffffffu, a6, m);
+        a12 += __shfl_xor_sync(0xffffffffu, a12, m);
+        ap += __shfl_xor_sync(0xffffffffu, ap, m);
+    }
+    if ((threadIdx.x & 31) == 0) { r6[threadIdx.x >> 5] = a6; r12[threadIdx.x >> 5] = a12; rp[threadIdx.x >> 5] = ap; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s6 = r6[0], s12 = r12[0];
+        long long sp = rp[0];
+        for (int w = 1; w < kKinThreads / 32; ++w) { s6 += r6[w]; s12 += r12[w]; sp += rp[w]; }
+        const double scale = p.full ? 0.5 : 1.0;
+        p.out[0] = scale * 4.0 * (s12 - s6);          // U = 4 sum (r^-12 - r^-6)
+        p.out[1] = scale * 24.0 * (2.0 * s12 - s6);   // W = sum r.F = 24 sum (2 r^-12 - r^-6)
+        const long long np = p.full ? sp / 2 : sp;
+        p.out[2] = (double)np;
+        *p.npairs = np;
+    }
+}
+
+__global__ void __launch_bounds__(kKinThreads) k_final_pot(PotArgs p) { pot_sum(p); }
+
 // Closing half-kick v <- v + (dt/2) F.  KIN: fused with the kinetic energy
 // of the new velocities -- each block forms the partial sum of v^2 that
 // k_kinetic would (same grid, same particles per thread, same order), and
 // the block that finishes last (ticket) adds the partials with final_kin
-// into the result block, so K needs no further pass.
+// into the result block, so K needs no further pass.  pot.nw > 0: block 0
+// first sums the force sweep's statistics slots (pot_sum), in place of a
+// launch of k_final_pot between the sweep and the kick.
 template <bool KIN>
 __global__ void __launch_bounds__(kKinThreads) k_kick(int n, double half, State st, const double *__restrict__ fx,
                                                       const double *__restrict__ fy, const double *__restrict__ fz,
                                                       double *__restrict__ part, unsigned *ticket,
-                                                      double *__restrict__ out) {
+                                                      double *__restrict__ out, PotArgs pot) {
+    if (pot.nw > 0 && blockIdx.x == 0) pot_sum(pot);
     double acc = 0.0;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         const double vx = fma(half, fx[s], st.vx[s]);
@@ -82,49 +129,6 @@ __global__ void __launch_bounds__(kKinThreads) k_kinetic(int n, State st, double
         acc = kin_add(acc, st.vx[s], st.vy[s], st.vz[s]);
     const double t = block_sum_kin(acc, red);
     if (threadIdx.x == 0) part[blockIdx.x] = t;
-}
-
-// Sum of the per-warp partials in a fixed tree order.
-// out[0] = U, out[1] = W, out[2] = pairs, out[3] = K (kinetic pass only).
-__global__ void __launch_bounds__(kRedThreads) k_final_pot(int nw, const double *__restrict__ warp_acc,
-                                                           const long long *__restrict__ warp_pairs, int full,
-                                                           double *__restrict__ out, long long *__restrict__ npairs) {
-    // per thread, then butterfly within each warp, then over the warps:
-    // a fixed order, so the sums are reproducible
-    __shared__ double r6[kRedThreads / 32], r12[kRedThreads / 32];
-    __shared__ long long rp[kRedThreads / 32];
-    double a6 = 0.0, a12 = 0.0;
-    long long ap = 0;
-#pragma unroll 4
-    for (int w = threadIdx.x; w < nw; w += kRedThreads) {
-        a6 += warp_acc[4 * w + 0];
-        a12 += warp_acc[4 * w + 1];
-        ap += warp_pairs[w];
-    }
-    for (int m = 16; m >= 1; m >>= 1) {
-        a6 += __shfl_xor_sync(0xffffffffu, a6, m);
-        a12 += __shfl_xor_sync(0xffffffffu, a12, m);
-        ap += __shfl_xor_sync(0xffffffffu, ap, m);
-    }
-    if ((threadIdx.x & 31) == 0) { r6[threadIdx.x >> 5] = a6; r12[threadIdx.x >> 5] = a12; rp[threadIdx.x >> 5] = ap; }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        a6 = r6[threadIdx.x]; a12 = r12[threadIdx.x]; ap = rp[threadIdx.x];
-        for (int m = 16; m >= 1; m >>= 1) {
-            a6 += __shfl_xor_sync(0xffffffffu, a6, m);
-            a12 += __shfl_xor_sync(0xffffffffu, a12, m);
-            ap += __shfl_xor_sync(0xffffffffu, ap, m);
-        }
-    }
-    if (threadIdx.x == 0) {
-        double s6 = a6, s12 = a12;
-        double scale = full ? 0.5 : 1.0;       // the full shell sees each pair twice
-        out[0] = scale * 4.0 * (s12 - s6);      // U = 4 sum (r^-12 - r^-6)
-        out[1] = scale * 24.0 * (2.0 * s12 - s6);  // W = sum r.F = 24 sum (2 r^-12 - r^-6)
-        long long p = full ? ap / 2 : ap;
-        out[2] = (double)p;
-        *npairs = p;
-    }
 }
 
 __global__ void __launch_bounds__(kKinThreads) k_final_kin(int nb, const double *__restrict__ part,
@@ -213,14 +217,27 @@ cudaError_t launch_box_kinetic(Ctx *c, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_kick(Ctx *c, double dt, cudaStream_t s, bool kin) {
-    if (c->n == 0) return cudaSuccess;
+static PotArgs pot_args(const Ctx *c, int full) {
+    PotArgs p;
+    p.nw = c->nwarp_used > 0 ? c->nwarp_used : c->nwarp_max;   // the rest are zero
+    p.full = full;
+    p.acc = c->d_warp_acc;
+    p.pairs = c->d_warp_pairs;
+    p.out = c->d_result;
+    p.npairs = c->d_npairs;
+    return p;
+}
+
+cudaError_t launch_kick(Ctx *c, double dt, cudaStream_t s, bool kin, bool pot) {
+    if (c->n == 0) return pot ? launch_energy_reduce(c, s, c->stats_full) : cudaSuccess;
+    PotArgs p = pot_args(c, c->stats_full);
+    if (!pot) p.nw = 0;
     if (kin)
         k_kick<true><<<kinetic_blocks(c), kKinThreads, 0, s>>>((int)c->n, 0.5 * dt, c->cur, c->fx, c->fy, c->fz,
-                                                               c->d_kin_part, c->d_kin_ticket, c->d_result);
+                                                               c->d_kin_part, c->d_kin_ticket, c->d_result, p);
     else
         k_kick<false><<<kinetic_blocks(c), kKinThreads, 0, s>>>((int)c->n, 0.5 * dt, c->cur, c->fx, c->fy, c->fz,
-                                                                nullptr, nullptr, nullptr);
+                                                                nullptr, nullptr, nullptr, p);
     return cudaGetLastError();
 }
 
@@ -284,14 +301,14 @@ cudaError_t launch_energy_reduce_parts(Ctx *c, cudaStream_t s, int full, const d
     const int per_block = std::max(256, (n + nb - 1) / nb);
     nb = std::max(1, (n + per_block - 1) / per_block);
     k_cell_parts<<<nb, 256, 0, s>>>(n, per_block, acc, pairs, c->d_warp_acc, c->d_warp_pairs);
-    k_final_pot<<<1, kRedThreads, 0, s>>>(nb, c->d_warp_acc, c->d_warp_pairs, full, c->d_result, c->d_npairs);
+    PotArgs p = pot_args(c, full);
+    p.nw = nb;
+    k_final_pot<<<1, kKinThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_energy_reduce(Ctx *c, cudaStream_t s, int full) {
-    const int nw = c->nwarp_used > 0 ? c->nwarp_used : c->nwarp_max;   // the rest are zero
-    k_final_pot<<<1, kRedThreads, 0, s>>>(nw, c->d_warp_acc, c->d_warp_pairs, full,
-                                          c->d_result, c->d_npairs);
+    k_final_pot<<<1, kKinThreads, 0, s>>>(pot_args(c, full));
     return cudaGetLastError();
 }
 
