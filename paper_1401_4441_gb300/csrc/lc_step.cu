@@ -12,7 +12,6 @@
 
 namespace lc {
 
-
 // K = 1/2 sum of the block partials of v^2, in a fixed order: thread t adds
 // partials t, t + kKinThreads, ... ascending (four loads in flight; the
 // zeros past the end leave the non-negative sum unchanged), then the
@@ -245,9 +244,8 @@ int kinetic_blocks(const Ctx *c) { return c->num_sms * 8; }
 
 // K into the result block.  Nothing to do when a closing kick with the
 // kinetic energy (k_kick<true>) or an earlier call already put the current
-// velocities' K there; the pass
-// over the velocities is skipped while the partials still describe them
-// (the state set-up and the kick form them).
+// velocities' K there; the pass over the velocities is skipped while the
+// partials still describe them (the state set-up and the kick form them).
 cudaError_t launch_kinetic(Ctx *c, cudaStream_t s) {
     if (c->kin_final) return cudaSuccess;
     const int nb = kinetic_blocks(c);
