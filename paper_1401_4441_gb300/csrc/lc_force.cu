@@ -917,9 +917,9 @@ __device__ void run_task_fp64(const ForceArgs &a, WarpSmem<double> &sm, const Ta
 // sl, first global cell cell_off).  Waits until the earlier-coloured tasks
 // whose written cells can meet this task's have published their completion
 // (the cells at the stencil's dependency offsets), runs the cell task with
-// plain writes, stores the task's energy partials (summed in a fixed order
-// afterwards) and publishes.  Returns false if a wait ran out (error flag
-// set).
+// plain writes and stores the task's energy partials (summed in a fixed
+// order afterwards); the caller publishes its completion.  Returns false if
+// a wait ran out (error flag set).
 template <bool MIXED, int NI, bool STATS>
 __device__ bool colour_task(const ForceArgs &a, WarpSmem<typename std::conditional<MIXED, float, double>::type> &sm,
                             const Grid &g, const float (*sh)[3], const float (*sl)[3], int cell_off, int k, int A,
@@ -994,8 +994,7 @@ __device__ bool colour_task(const ForceArgs &a, WarpSmem<typename std::condition
             a.cell_pairs[A] = np;
         }
     }
-    __syncwarp();   // every lane's writes ordered before lane 0's release (cumulative)
-    if (lane == 0 && !a.withhold) st_release(a.cs_done + A, 1);
+    __syncwarp();   // every lane's writes ordered before lane 0's later release (cumulative)
     return true;
 }
 
@@ -1051,21 +1050,31 @@ __global__ void __launch_bounds__(256, MIXED ? 2 : 1) k_force(ForceArgs a) {
         // waits (bounded) until the earlier-coloured tasks of its box that
         // could share a written cell have published -- they were claimed
         // earlier, so running warps hold them -- then runs with plain writes.
+        // A finished task is published right after its warp's next claim
+        // is issued, so that its reductions drain while the claim's atomic
+        // is in flight; the warp waits for nothing in between, which keeps
+        // the argument above.
+        int pend = -1;   // finished task not yet published
         for (;;) {
             int q = 0;
             if (lane == 0) q = atomicAdd(a.cs_ctrl, 1);
+            if (lane == 0 && pend >= 0 && !a.withhold) st_release(a.cs_done + pend, 1);
+            pend = -1;
             q = __shfl_sync(kFull, q, 0);
             if (q >= a.ntasks) break;
             bool ok = true;
+            int A;
             if constexpr (BATCHED) {
                 const int4 it = a.cs_items[q];   // (box, colour, global cell)
                 const BoxDev &bd = a.boxes[it.x];
+                A = it.z;
                 ok = colour_task<MIXED, NI, STATS>(a, sm, bd.g, bd.sh, bd.sl, bd.cell_off, it.y, it.z, lane);
             } else {
-                const int A = a.cs_cell[q];
+                A = a.cs_cell[q];
                 ok = colour_task<MIXED, NI, STATS>(a, sm, a.g, s_sh, s_sl, 0, (int)a.cs_rank[A], A, lane);
             }
             if (!ok) break;
+            pend = A;
         }
     } else if constexpr (MIXED) {
         for (int t = w; t < a.ntasks; t += W) {
