@@ -566,23 +566,45 @@ __device__ __forceinline__ int prune_list(const ForceArgs &a, WarpSmem<float> &s
 // Sum the i chunk's per-lane partials over the lanes and let the owner
 // lanes write them (plus the near-r_c corrections of the mixed path).
 // Mixed: column sums through the pruned-data scratch (free once the chunk
-// loop has run; the next i chunk prunes again), lane l < NI owning element
-// l.  FP64: a shuffle reduce-scatter.
+// loop has run; the next i chunk prunes again): a chunk of 16 as packed
+// pairs (column_sum_pairs, the owner of element e on lane pair_element), a
+// chunk of 8 one element per lane (lane l < 8 owning element l).  FP64: a
+// shuffle reduce-scatter.
 template <bool MIXED, int NI, int MODE, typename T, typename S>
 __device__ __forceinline__ void write_i_chunk(const ForceArgs &a, S &sm, T (&ax)[NI], T (&ay)[NI], T (&az)[NI],
                                               int a0, int i0, int na, int lane) {
     if constexpr (MIXED) {
-        float *scratch = reinterpret_cast<float *>(sm.jd);
-        static_assert(sizeof(sm.jd) >= sizeof(float) * 32 * kColStride, "column-sum scratch");
-        const float sx = column_sum<NI>(ax, scratch, lane);
-        const float sy = column_sum<NI>(ay, scratch, lane);
-        const float sz = column_sum<NI>(az, scratch, lane);
+        float sx, sy, sz;
+        int e = lane;
+        bool owner = lane < NI;
+        if constexpr (NI == 16) {
+            float2 *scratch = reinterpret_cast<float2 *>(sm.jd);
+            static_assert(sizeof(sm.jd) >= sizeof(float2) * 32 * kPairStride, "column-sum scratch");
+            float2 px[8], py[8], pz[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                px[k] = make_float2(ax[2 * k], ax[2 * k + 1]);
+                py[k] = make_float2(ay[2 * k], ay[2 * k + 1]);
+                pz[k] = make_float2(az[2 * k], az[2 * k + 1]);
+            }
+            sx = column_sum_pairs(px, scratch, lane);
+            sy = column_sum_pairs(py, scratch, lane);
+            sz = column_sum_pairs(pz, scratch, lane);
+            e = pair_element(lane);
+            owner = pair_owner(lane);
+        } else {
+            float *scratch = reinterpret_cast<float *>(sm.jd);
+            static_assert(sizeof(sm.jd) >= sizeof(float) * 32 * kColStride, "column-sum scratch");
+            sx = column_sum<NI>(ax, scratch, lane);
+            sy = column_sum<NI>(ay, scratch, lane);
+            sz = column_sum<NI>(az, scratch, lane);
+        }
         __syncwarp();   // order the j-side writes to A before the i-side ones; the scratch is free again
-        if (lane < NI) {
-            const int ii = i0 + lane;
+        if (owner) {
+            const int ii = i0 + e;
             if (ii < na) {
-                const float vx = sx + sm.corr[lane][0], vy = sy + sm.corr[lane][1], vz = sz + sm.corr[lane][2];
-                const double c[3] = {sm.corr64[lane][0], sm.corr64[lane][1], sm.corr64[lane][2]};
+                const float vx = sx + sm.corr[e][0], vy = sy + sm.corr[e][1], vz = sz + sm.corr[e][2];
+                const double c[3] = {sm.corr64[e][0], sm.corr64[e][1], sm.corr64[e][2]};
                 if constexpr (MODE == kBuffer) {
                     float wx = vx, wy = vy, wz = vz;
                     if (nonzero3(c[0], c[1], c[2])) {
@@ -1163,7 +1185,7 @@ struct alignas(16) RowWarp {
     int nb_boff[14], nb_count[14], nb_img[14];
     union {
         int jl[kRowJl];              // entry index | unstaged flag | neighbour << 26
-        float4 jd[(32 * kColStride + 3) / 4];   // the column sums' scratch (write_i_chunk)
+        float4 jd[(32 * kPairStride * 2 + 3) / 4];   // the column sums' scratch (write_i_chunk)
     };
 };
 

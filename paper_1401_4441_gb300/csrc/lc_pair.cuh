@@ -100,6 +100,38 @@ __device__ __forceinline__ float column_sum(const float (&v)[NI], float *s, int 
     return sum;
 }
 
+// The same sums for a chunk of 16 held as 8 packed pairs per lane (pair k
+// = elements 2k, 2k + 1): every lane stores its pairs as one row of 8-byte
+// words (row stride kPairStride pairs, odd, so that neither the row stores
+// nor the column reads conflict); lane (p = l & 7, h = l >> 3) adds pair p
+// over rows 8h .. 8h + 7 with packed adds; two shuffle levels finish the sum
+// and split the pair on the way: lanes with h = 0 (l < 8) end with element
+// 2p, lanes with h = 2 (16 <= l < 24) with element 2p + 1 (pair_element).
+// A fixed order, so the bits are reproducible.  Returns the lane's sum,
+// valid on those 16 lanes.
+constexpr int kPairStride = 9;
+__device__ __forceinline__ int pair_element(int lane) { return 2 * (lane & 7) + ((lane >> 4) & 1); }
+__device__ __forceinline__ bool pair_owner(int lane) { return (lane & 8) == 0; }
+__device__ __forceinline__ float column_sum_pairs(const float2 (&v)[8], float2 *s, int lane) {
+    __syncwarp();   // the scratch's previous readers are done
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[lane * kPairStride + k] = v[k];
+    __syncwarp();
+    const float2 *col = s + 8 * (lane >> 3) * kPairStride + (lane & 7);
+    float2 t0 = col[0], t1 = col[kPairStride];
+#pragma unroll
+    for (int r = 2; r < 8; r += 2) {
+        t0 = __fadd2_rn(t0, col[r * kPairStride]);
+        t1 = __fadd2_rn(t1, col[(r + 1) * kPairStride]);
+    }
+    const float2 t = __fadd2_rn(t0, t1);
+    const bool keep_x = lane < 16;   // h < 2 keeps element 2p, h >= 2 element 2p + 1
+    const float mine = keep_x ? t.x : t.y;
+    float r = mine + __shfl_xor_sync(kFull, keep_x ? t.y : t.x, 16);
+    r += __shfl_xor_sync(kFull, r, 8);
+    return r;
+}
+
 template <int NI>
 __device__ __forceinline__ int scattered_element(int lane) {
     int bits = 0;
