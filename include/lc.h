@@ -349,8 +349,16 @@ lc_status lc_dag_forces(lc_ctx *ctx, lc_order order, double wait_seconds, int fl
 lc_status lc_set_tile(lc_ctx *ctx, int ni, int warps);
 
 /* Number of kernels launched by the last lc_forces / lc_verlet_step call
- * per force evaluation and per step (for accounting). */
+ * per force evaluation and per step (for accounting; per step: the
+ * two-step graph's kernels halved, rounded down). */
 lc_status lc_launch_counts(const lc_ctx *ctx, int32_t *per_force, int32_t *per_step);
+
+/* Kernels in the step graphs that lc_verlet_step launched last: the
+ * one-step graph (which ends an odd step count) and the two-step graph; 0
+ * for one not launched yet.  A call of n steps with the same schedule
+ * launches two_steps * (n / 2) + one_step * (n % 2) kernels.  Any output
+ * may be NULL. */
+lc_status lc_launch_counts_graphs(const lc_ctx *ctx, int32_t *one_step, int32_t *two_steps);
 
 /* ---- batches of independent boxes --------------------------------------
  * A batch context holds nbox independent periodic boxes (each with its own

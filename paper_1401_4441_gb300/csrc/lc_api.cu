@@ -739,8 +739,11 @@ static lc_status list_verlet(lc_ctx *c, double dt, int nsteps, cudaStream_t s) {
             LC_TRY(capture_list_steps(c, dt, k, &c->list_graph[gi], &per));
             c->list_graph_dt[gi] = dt;
             c->launches_step = per / k;
+            c->list_graph_launches[gi] = per;
         }
         LC_TRY(cudaGraphLaunch(c->list_graph[gi], s));
+        if (k == 2) c->launches_two = c->list_graph_launches[gi];
+        else c->launches_one = c->list_graph_launches[gi];
         done += k;
     }
     c->binned = false;
@@ -840,6 +843,7 @@ static cudaError_t ensure_step_graph(lc_ctx *c, double dt, lc_schedule sched, in
     if (e) { cudaGetLastError(); c->graph[k] = nullptr; return e; }
     c->graph_dt[k] = dt;
     if (nst == 2) c->launches_step = per / 2;
+    c->graph_launches[k] = per;
     return cudaSuccess;
 }
 
@@ -870,10 +874,12 @@ lc_status lc_verlet_step(lc_ctx *c, double dt, int nsteps, lc_schedule sched, vo
     int done = 0;
     while (done + 2 <= nsteps) {
         LC_TRY(cudaGraphLaunch(c->graph[2 * (int)sched + par], s));
+        c->launches_two = c->graph_launches[2 * (int)sched + par];
         done += 2;
     }
     if (done < nsteps) {
         LC_TRY(cudaGraphLaunch(c->graph[k1], s));
+        c->launches_one = c->graph_launches[k1];
         const State t = c->cur; c->cur = c->nxt; c->nxt = t;
         ++done;
     }
@@ -1127,6 +1133,13 @@ lc_status lc_launch_counts(const lc_ctx *c, int32_t *per_force, int32_t *per_ste
     if (!c) return LC_ERR_INVALID_ARG;
     if (per_force) *per_force = c->launches_force;
     if (per_step) *per_step = c->launches_step;
+    return LC_OK;
+}
+
+lc_status lc_launch_counts_graphs(const lc_ctx *c, int32_t *one_step, int32_t *two_steps) {
+    if (!c) return LC_ERR_INVALID_ARG;
+    if (one_step) *one_step = c->launches_one;
+    if (two_steps) *two_steps = c->launches_two;
     return LC_OK;
 }
 

@@ -2180,10 +2180,15 @@ cudaError_t launch_forces(Ctx *c, lc_schedule sched, cudaStream_t s, int *launch
         c->stats_full = (sched == LC_SCHED_FULLSHELL);
         if (c->nbox > 0 && sched == LC_SCHED_COLOUR) e = launch_box_energy_cells(c, s);
         else if (c->nbox > 0) e = launch_box_energy(c, s, sched == LC_SCHED_FULLSHELL);
-        else if (sched == LC_SCHED_COLOUR)   // per-cell partials, reduced in cell order
+        else if (sched == LC_SCHED_COLOUR) {   // per-cell partials, reduced in cell order (two kernels)
             e = launch_energy_reduce_parts(c, s, 0, c->d_cell_acc, c->d_cell_pairs, c->g.ncell);
-        else if (pot_deferred) { *pot_deferred = true; return e; }
-        else e = launch_energy_reduce(c, s, sched == LC_SCHED_FULLSHELL);
+            ++*launches;
+        } else if (pot_deferred) {
+            *pot_deferred = true;
+            return e;
+        } else {
+            e = launch_energy_reduce(c, s, sched == LC_SCHED_FULLSHELL);
+        }
         ++*launches;
     }
     return e;

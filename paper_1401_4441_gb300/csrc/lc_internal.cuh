@@ -191,6 +191,7 @@ struct Ctx {
     // status
     bool have_state, binned, forces_valid;
     int launches_force, launches_step;
+    int launches_one, launches_two;   // kernels of the one-step and two-step graphs last launched
     // batch of independent boxes (nbox > 0); single box: nbox == 0
     int nbox;
     BoxDev *h_boxes;          // host copy
@@ -217,6 +218,7 @@ struct Ctx {
     // parity, one step at 2 * kNumSched + the same
     cudaGraphExec_t graph[kNumGraphs];
     double graph_dt[kNumGraphs];
+    int graph_launches[kNumGraphs];   // kernels in each
     double *state_a;       // cur.x of buffer set A (parity reference)
     // Verlet neighbour lists (LC_SCHED_LIST): a coarser list grid with
     // cells of side >= rc + skin, fixed-point offsets from the build cells'
@@ -233,6 +235,7 @@ struct Ctx {
     bool list_valid;       // the lists match the current slot order and state
     cudaGraphExec_t list_graph[4];      // (one / two steps) x (state-buffer parity)
     double list_graph_dt[4];
+    int list_graph_launches[4];         // kernels in each
 };
 
 // ---- kernels / launchers (stream-ordered, return cudaError_t) -------------

@@ -56,6 +56,7 @@ def _load():
         "lc_schedule_check": ([vp, ctypes.c_int, lp, lp, vp], ctypes.c_int),
         "lc_set_tile": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "lc_launch_counts": ([vp, ip, ip], ctypes.c_int),
+        "lc_launch_counts_graphs": ([vp, ip, ip], ctypes.c_int),
         "lc_batch_create": ([ctypes.c_int32, dp, dp, lp, ctypes.c_int, ctx_pp], ctypes.c_int),
         "lc_batch_energies": ([vp, dp, dp, dp, lp, vp], ctypes.c_int),
         "lc_batch_info": ([vp, ip, lp, lp], ctypes.c_int),
@@ -328,6 +329,13 @@ class Box:
     def launch_counts(self):
         a, b = ctypes.c_int32(), ctypes.c_int32()
         _check(self._lib.lc_launch_counts(self._h, ctypes.byref(a), ctypes.byref(b)), "lc_launch_counts")
+        return a.value, b.value
+
+    def launch_counts_graphs(self):
+        """(kernels of the one-step graph, kernels of the two-step graph)."""
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.lc_launch_counts_graphs(self._h, ctypes.byref(a), ctypes.byref(b)),
+               "lc_launch_counts_graphs")
         return a.value, b.value
 
 
